@@ -1,0 +1,346 @@
+/*
+ * oracle.c -- plain, slow CPU oracle for the L1 Caputo time-marching schemes.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes or
+ * calls this file; only the test-suite, the smoke check and the CPU-baseline leg
+ * of the benchmark load it (through oracle/oracle.py).  It shares no code, no
+ * header and no table with the CUDA path.
+ *
+ * What it computes (Liu, Cheng, Li, Wang, "Fast procedures for Caputo fractional
+ * ordinary and partial differential equations"):
+ *
+ *   - L1 weights G_k = (k+1)^(1-g) - k^(1-g)          (Lemma 1; Sec. 3 definitions)
+ *     and M_k = (k+1)^(2-g) - k^(2-g)                  (Sec. 3 definitions)
+ *     evaluated in binary128 and rounded once to double (the paper does not state
+ *     a precision; the differences cancel catastrophically in double).
+ *   - Scheme 4 (Eq. 19) advanced by the direct time-marching procedure of Eq. 20:
+ *     for n = 1..N solve the tridiagonal system
+ *         (mu*G_0 + 2/h^2) u_j^n - (u_{j-1}^n + u_{j+1}^n)/h^2
+ *             = f_j^n + mu*[ sum_{k=1}^{n-1} (G_{n-k-1} - G_{n-k}) u_j^k + G_{n-1} u_j^0 ]
+ *     (mu = tau^-g / Gamma(2-g); the u^0 coefficient follows from expanding the L1
+ *     quotient, see the header of march_step()).
+ *   - The hyperbolic L1 scheme of Eq. 15 / Eq. 17 (1<g<2, c = tau^-g/Gamma(3-g)) with
+ *     the advection term replaced by the central second difference, spatial term at
+ *     level n and f at t_{n-1/2}:
+ *         c*M_0 u^n + c(M_1-2M_0) u^{n-1} + c sum_{k=1}^{n-2} W_{n-k} u^k
+ *             + c(M_{n-2}-M_{n-1}) u^0 - c*tau*M_{n-1} phi - (u_xx)_h^n = f^{n-1/2}
+ *     with W_j = M_{j-2} - 2M_{j-1} + M_j and M_{-1} = 0.
+ *   - the scalar problem D^g u = -lambda u + f on the same time grid (no space).
+ *   - the transposed (adjoint) system, marched backwards in time.
+ *   - the orthonormal sine projection of one spatial mode, and a dense Toeplitz
+ *     matrix-vector product, as plain sums.
+ *
+ * Layout of every field: [M][N] row-major, time index contiguous; entry (j, n-1)
+ * holds the value at x_j = j*h (j = 1..M) and time level n (n = 1..N).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#if defined(__aarch64__)
+/* AArch64 Linux: long double is IEEE binary128. */
+typedef long double qreal;
+#define QPOW(a, b) powl((a), (b))
+#define QLOG(a) logl(a)
+#define QEXP(a) expl(a)
+#define QTGAMMA(a) tgammal(a)
+#define QLIT(x) x##L
+#else
+#include <quadmath.h>
+typedef __float128 qreal;
+#define QPOW(a, b) powq((a), (b))
+#define QLOG(a) logq(a)
+#define QEXP(a) expq(a)
+#define QTGAMMA(a) tgammaq(a)
+#define QLIT(x) x##Q
+#endif
+
+#define OR_OK 0
+#define OR_EINVAL 1
+#define OR_ENOMEM 2
+
+/* kind: 0 = sub-diffusion L1 (0<g<1), 1 = hyperbolic L1 (1<g<2). */
+/* space: 0 = scalar (D^g u = -lambda u + f), 1 = Dirichlet Laplacian on (0, L). */
+
+/* k^beta in binary128, with 0^beta = 0 for beta > 0. */
+static qreal qpow_int(int64_t k, qreal beta) {
+  if (k <= 0) return QLIT(0.0);
+  return QPOW((qreal)k, beta);
+}
+
+/* G_k = (k+1)^(1-g) - k^(1-g), k >= 0 (Lemma 1). */
+static qreal q_G(int64_t k, qreal g) {
+  qreal b = QLIT(1.0) - g;
+  return qpow_int(k + 1, b) - qpow_int(k, b);
+}
+
+/* M_k = (k+1)^(2-g) - k^(2-g), k >= 0; M_{-1} = M_{-2} = 0 (Sec. 3 definitions). */
+static qreal q_M(int64_t k, qreal g) {
+  if (k < 0) return QLIT(0.0);
+  qreal b = QLIT(2.0) - g;
+  return qpow_int(k + 1, b) - qpow_int(k, b);
+}
+
+/* Scale of the time stencil: mu = tau^-g/Gamma(2-g) (Lemma 2) or
+ * c = tau^-g/Gamma(3-g) (Eq. 17), in binary128. */
+static qreal q_scale(int kind, qreal g, qreal tau) {
+  qreal p = QEXP(-g * QLOG(tau));
+  return kind == 0 ? p / QTGAMMA(QLIT(2.0) - g) : p / QTGAMMA(QLIT(3.0) - g);
+}
+
+static int check_kind(int kind, double g) {
+  if (kind == 0) return (g > 0.0 && g < 1.0) ? OR_OK : OR_EINVAL;
+  if (kind == 1) return (g > 1.0 && g < 2.0) ? OR_OK : OR_EINVAL;
+  return OR_EINVAL;
+}
+
+/* G_k for k = 0..K-1, rounded to double. */
+int or_G(double g, int64_t K, double* out) {
+  if (!(g > 0.0 && g < 1.0) || K < 0 || (K > 0 && !out)) return OR_EINVAL;
+  for (int64_t k = 0; k < K; ++k) out[k] = (double)q_G(k, (qreal)g);
+  return OR_OK;
+}
+
+/* M_k for k = 0..K-1, rounded to double. */
+int or_M(double g, int64_t K, double* out) {
+  if (!(g > 1.0 && g < 2.0) || K < 0 || (K > 0 && !out)) return OR_EINVAL;
+  for (int64_t k = 0; k < K; ++k) out[k] = (double)q_M(k, (qreal)g);
+  return OR_OK;
+}
+
+/* Unscaled coefficient of u^{n-j} on the left-hand side at level n, for j = 0..N-1,
+ * each formed in binary128 from the paper's weights and rounded once:
+ *   kind 0 (Eq. 4/19):  j = 0: G_0;          j >= 1: -(G_{j-1} - G_j)
+ *   kind 1 (Eq. 17):    j = 0: M_0;  j = 1: M_1 - 2 M_0;  j >= 2: W_j = M_{j-2} - 2M_{j-1} + M_j
+ * The full left-hand coefficient is scale * coef[j]. */
+static qreal q_coef(int kind, int64_t j, qreal g) {
+  if (kind == 0) {
+    if (j == 0) return q_G(0, g);
+    return -(q_G(j - 1, g) - q_G(j, g));
+  }
+  if (j == 0) return q_M(0, g);
+  if (j == 1) return q_M(1, g) - QLIT(2.0) * q_M(0, g);
+  return q_M(j - 2, g) - QLIT(2.0) * q_M(j - 1, g) + q_M(j, g);
+}
+
+int or_time_coeffs(int kind, double g, int64_t N, double* coef) {
+  if (check_kind(kind, g) != OR_OK || N < 1 || !coef) return OR_EINVAL;
+  for (int64_t j = 0; j < N; ++j) coef[j] = (double)q_coef(kind, j, (qreal)g);
+  return OR_OK;
+}
+
+/* Scale mu (kind 0) or c (kind 1) for step tau, rounded to double. */
+double or_scale(int kind, double g, double tau) { return (double)q_scale(kind, (qreal)g, (qreal)tau); }
+
+/* d/dg of the full coefficients scale(g) * coef_j(g), j = 0..N-1, by a central
+ * difference of the binary128 definitions (step 1e-10: truncation ~1e-20 and
+ * rounding ~1e-24 relative, both far below double precision). */
+int or_time_coeffs_dgamma(int kind, double g, double tau, int64_t N, double* out) {
+  if (check_kind(kind, g) != OR_OK || N < 1 || !out) return OR_EINVAL;
+  const qreal d = QLIT(1e-10);
+  qreal gp = (qreal)g + d, gm = (qreal)g - d;
+  qreal sp = q_scale(kind, gp, (qreal)tau), sm = q_scale(kind, gm, (qreal)tau);
+  for (int64_t j = 0; j < N; ++j) {
+    qreal vp = sp * q_coef(kind, j, gp), vm = sm * q_coef(kind, j, gm);
+    out[j] = (double)((vp - vm) / (QLIT(2.0) * d));
+  }
+  return OR_OK;
+}
+
+/* Right-hand-side weights of the initial data at level n = 1..N (index n-1), from
+ * expanding the stencils:
+ *   kind 0: L1 quotient mu*sum_{k=1}^{n} G_{n-k}(u^k - u^{k-1}) leaves -mu*G_{n-1} u^0
+ *           on the left, i.e. +mu*G_{n-1} u^0 on the right.  (Eq. 4 prints "+G_n u_0";
+ *           the expansion gives G_{n-1}, which is what is used here.)
+ *   kind 1: Eq. 17 leaves c(M_{n-2} - M_{n-1}) u^0 - c*tau*M_{n-1} phi on the left, with
+ *           M_{-1} = 0 (at n = 1 the u^0 weight is -c*M_0, which the expansion of Eq. 15
+ *           gives directly), i.e. +c(M_{n-1} - M_{n-2}) u^0 + c*tau*M_{n-1} phi on the right.
+ * w_u0[n-1] and w_phi[n-1] include the scale; w_phi is zero for kind 0. */
+int or_initial_weights(int kind, double g, double tau, int64_t N, double* w_u0, double* w_phi) {
+  if (check_kind(kind, g) != OR_OK || N < 1 || !w_u0 || !w_phi) return OR_EINVAL;
+  qreal s = q_scale(kind, (qreal)g, (qreal)tau);
+  for (int64_t n = 1; n <= N; ++n) {
+    if (kind == 0) {
+      w_u0[n - 1] = (double)(s * q_G(n - 1, (qreal)g));
+      w_phi[n - 1] = 0.0;
+    } else {
+      w_u0[n - 1] = (double)(s * (q_M(n - 1, (qreal)g) - q_M(n - 2, (qreal)g)));
+      w_phi[n - 1] = (double)(s * (qreal)tau * q_M(n - 1, (qreal)g));
+    }
+  }
+  return OR_OK;
+}
+
+/* Thomas algorithm for the constant tridiagonal system
+ *   diag*x_j + off*(x_{j-1} + x_{j+1}) = r_j,  j = 0..M-1, x_{-1} = x_M = 0.
+ * cp is scratch of length M.  Overwrites r with x. */
+static void thomas_const(int64_t M, double diag, double off, double* r, double* cp) {
+  cp[0] = off / diag;
+  r[0] = r[0] / diag;
+  for (int64_t j = 1; j < M; ++j) {
+    double den = diag - off * cp[j - 1];
+    cp[j] = off / den;
+    r[j] = (r[j] - off * r[j - 1]) / den;
+  }
+  for (int64_t j = M - 2; j >= 0; --j) r[j] -= cp[j] * r[j + 1];
+}
+
+/*
+ * Direct time marching (Eq. 20 for kind 0, the direct procedure of Eq. 17 for kind 1,
+ * and the scalar analogue for space 0).  Cost O(M N^2).
+ *
+ * f, u: [M][N] (time contiguous).  u0, phi: length M or NULL (= 0).  For space 0 every
+ * row j is an independent scalar problem with the same lambda.
+ * T: final time (tau = T/N).  Lx: length of the space interval (h = Lx/(M+1)).
+ */
+int or_march(int kind, int space, double g, double T, double Lx, double lambda, int64_t N, int64_t M,
+             const double* f, const double* u0, const double* phi, double* u, int nthreads) {
+  if (check_kind(kind, g) != OR_OK || (space != 0 && space != 1) || N < 1 || M < 1 || !f || !u)
+    return OR_EINVAL;
+  if (!(T > 0.0) || (space == 1 && !(Lx > 0.0))) return OR_EINVAL;
+  const double tau = T / (double)N;
+  const double scale = or_scale(kind, g, tau);
+  double* coef = (double*)malloc(sizeof(double) * (size_t)N);
+  double* wu0 = (double*)malloc(sizeof(double) * (size_t)N);
+  double* wphi = (double*)malloc(sizeof(double) * (size_t)N);
+  double* rhs = (double*)malloc(sizeof(double) * (size_t)M);
+  double* cp = (double*)malloc(sizeof(double) * (size_t)M);
+  if (!coef || !wu0 || !wphi || !rhs || !cp) {
+    free(coef); free(wu0); free(wphi); free(rhs); free(cp);
+    return OR_ENOMEM;
+  }
+  or_time_coeffs(kind, g, N, coef);
+  or_initial_weights(kind, g, tau, N, wu0, wphi);
+  /* history weights h_j = -scale*coef_j for j >= 1: the right-hand side collects
+   * sum_{k=1}^{n-1} h_{n-k} u^k, which for kind 0 is mu*(G_{n-k-1} - G_{n-k}). */
+  double h = 0.0, diag, off;
+  if (space == 1) {
+    h = Lx / (double)(M + 1);
+    diag = scale * coef[0] + 2.0 / (h * h);
+    off = -1.0 / (h * h);
+  } else {
+    diag = scale * coef[0] + lambda;
+    off = 0.0;
+  }
+  if (nthreads < 1) nthreads = 1;
+  for (int64_t n = 1; n <= N; ++n) {
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+    for (int64_t j = 0; j < M; ++j) {
+      const double* uj = u + j * N;
+      double s = 0.0;
+      for (int64_t k = 1; k <= n - 1; ++k) s += coef[n - k] * uj[k - 1];
+      double r = f[j * N + (n - 1)] - scale * s;
+      if (u0) r += wu0[n - 1] * u0[j];
+      if (phi) r += wphi[n - 1] * phi[j];
+      rhs[j] = r;
+    }
+    if (space == 1) {
+      thomas_const(M, diag, off, rhs, cp);
+    } else {
+      for (int64_t j = 0; j < M; ++j) rhs[j] /= diag;
+    }
+    for (int64_t j = 0; j < M; ++j) u[j * N + (n - 1)] = rhs[j];
+  }
+  free(coef); free(wu0); free(wphi); free(rhs); free(cp);
+  return OR_OK;
+}
+
+/*
+ * Transposed system A^T lam = g, A the left-hand operator of or_march (zero initial
+ * data).  The time part of A is lower-triangular Toeplitz with first column
+ * scale*coef; its transpose is upper triangular, so the march runs n = N..1:
+ *   diag*lam_j^n + off*(lam_{j-1}^n + lam_{j+1}^n) = g_j^n - scale*sum_{k=n+1}^{N} coef_{k-n} lam_j^k
+ */
+int or_adjoint_march(int kind, int space, double g, double T, double Lx, double lambda, int64_t N,
+                     int64_t M, const double* gin, double* lam, int nthreads) {
+  if (check_kind(kind, g) != OR_OK || (space != 0 && space != 1) || N < 1 || M < 1 || !gin || !lam)
+    return OR_EINVAL;
+  const double tau = T / (double)N;
+  const double scale = or_scale(kind, g, tau);
+  double* coef = (double*)malloc(sizeof(double) * (size_t)N);
+  double* rhs = (double*)malloc(sizeof(double) * (size_t)M);
+  double* cp = (double*)malloc(sizeof(double) * (size_t)M);
+  if (!coef || !rhs || !cp) {
+    free(coef); free(rhs); free(cp);
+    return OR_ENOMEM;
+  }
+  or_time_coeffs(kind, g, N, coef);
+  double diag, off;
+  if (space == 1) {
+    double h = Lx / (double)(M + 1);
+    diag = scale * coef[0] + 2.0 / (h * h);
+    off = -1.0 / (h * h);
+  } else {
+    diag = scale * coef[0] + lambda;
+    off = 0.0;
+  }
+  if (nthreads < 1) nthreads = 1;
+  for (int64_t n = N; n >= 1; --n) {
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+    for (int64_t j = 0; j < M; ++j) {
+      const double* lj = lam + j * N;
+      double s = 0.0;
+      for (int64_t k = n + 1; k <= N; ++k) s += coef[k - n] * lj[k - 1];
+      rhs[j] = gin[j * N + (n - 1)] - scale * s;
+    }
+    if (space == 1) {
+      thomas_const(M, diag, off, rhs, cp);
+    } else {
+      for (int64_t j = 0; j < M; ++j) rhs[j] /= diag;
+    }
+    for (int64_t j = 0; j < M; ++j) lam[j * N + (n - 1)] = rhs[j];
+  }
+  free(coef); free(rhs); free(cp);
+  return OR_OK;
+}
+
+/* Orthonormal sine coefficient of mode m (1..M) of every time column:
+ *   out[n] = sqrt(2/(M+1)) * sum_{j=1}^{M} f_j^n sin(m*pi*j/(M+1)).
+ * The sine values are taken in binary128 and rounded; the sum is plain double. */
+int or_sine_project(int64_t M, int64_t N, const double* f, int64_t m, double* out) {
+  if (M < 1 || N < 1 || m < 1 || m > M || !f || !out) return OR_EINVAL;
+  double* sv = (double*)malloc(sizeof(double) * (size_t)M);
+  if (!sv) return OR_ENOMEM;
+#if defined(__aarch64__)
+  const qreal qpi = 3.141592653589793238462643383279502884L;
+#define QSIN(a) sinl(a)
+#else
+  const qreal qpi = M_PIq;
+#define QSIN(a) sinq(a)
+#endif
+  qreal nrm = QPOW((qreal)2.0 / (qreal)(M + 1), QLIT(0.5));
+  for (int64_t j = 1; j <= M; ++j) {
+    /* reduce m*j modulo 2(M+1) exactly before the sine */
+    int64_t r = (m * j) % (2 * (M + 1));
+    sv[j - 1] = (double)(nrm * QSIN(qpi * (qreal)r / (qreal)(M + 1)));
+  }
+  for (int64_t n = 0; n < N; ++n) out[n] = 0.0;
+  for (int64_t j = 0; j < M; ++j) {
+    const double* fj = f + j * N;
+    double s = sv[j];
+    for (int64_t n = 0; n < N; ++n) out[n] += s * fj[n];
+  }
+  free(sv);
+  return OR_OK;
+}
+
+/* Dense lower-triangular Toeplitz product, first column a (length N):
+ *   transpose = 0: y_n = sum_{k<=n} a_{n-k} x_k;  transpose = 1: y_n = sum_{k>=n} a_{k-n} x_k.
+ * Applied to nlines independent lines of length N (stride N). */
+int or_toeplitz_matvec(const double* a, int64_t N, const double* x, double* y, int64_t nlines, int transpose) {
+  if (N < 1 || nlines < 1 || !a || !x || !y) return OR_EINVAL;
+  for (int64_t l = 0; l < nlines; ++l) {
+    const double* xl = x + l * N;
+    double* yl = y + l * N;
+    for (int64_t n = 0; n < N; ++n) {
+      double s = 0.0;
+      if (!transpose)
+        for (int64_t k = 0; k <= n; ++k) s += a[n - k] * xl[k];
+      else
+        for (int64_t k = n; k < N; ++k) s += a[k - n] * xl[k];
+      yl[n] = s;
+    }
+  }
+  return OR_OK;
+}
