@@ -1,0 +1,176 @@
+/*
+ * ftoep.h -- C ABI of libftoep: GB300 (sm_103a) solver for the linear systems of
+ * L1-type Caputo finite-difference schemes (Liu, Cheng, Li, Wang, "Fast procedures
+ * for Caputo fractional ordinary and partial differential equations").
+ *
+ * Problem statement (Sec. 3, Eq. 18 and Eq. 14 with the advection term replaced by
+ * -u_xx; Sec. 2 for the scalar case):
+ *
+ *     D_t^g u(x,t) = u_xx(x,t) + f(x,t),   x in (0,L), t in (0,T],  u(0,t) = u(L,t) = 0,
+ *     u(x,0) = u0(x)  [and u_t(x,0) = phi(x) when 1 < g < 2],
+ *
+ * or, without space (FTOEP_SPACE_NONE), D_t^g u = -lambda*u + f on (0,T].
+ *
+ * Discretisation: tau = T/N, h = L/(M+1), x_j = j*h (j = 1..M).
+ *   FTOEP_L1_SUBDIFFUSION (0 < g < 1): Scheme 4, Eq. 19 (L1 formula of Lemma 2, Eq. 4),
+ *       level t_n; left-hand first column a_0 = mu, a_j = mu*(G_j - G_{j-1}),
+ *       mu = tau^-g/Gamma(2-g), G_k = (k+1)^(1-g) - k^(1-g).
+ *   FTOEP_L1_HYPERBOLIC (1 < g < 2): Eq. 15/17 at t_{n-1/2} with c = tau^-g/Gamma(3-g),
+ *       a_0 = c, a_1 = c(M_1 - 2M_0), a_j = c(M_{j-2} - 2M_{j-1} + M_j),
+ *       M_k = (k+1)^(2-g) - k^(2-g); spatial term taken at level n.
+ *   Space: central second difference with Dirichlet zeros (Eq. 19).
+ * With the unknowns of one spatial point ordered in time (the reordering of Sec. 3,
+ * "U_i = (U_i^1, ..., U_i^N)"), the time operator is lower-triangular Toeplitz with
+ * first column a (Sec. 3, the block A-hat).  The library diagonalises the spatial
+ * operator with an orthonormal sine transform (eigenvalues
+ * lambda_m = (4/h^2) sin^2(m pi/(2(M+1)))), so each mode solves a lower-triangular
+ * Toeplitz system (lambda_m I + T) u_m = r_m exactly (a direct solve, not an iteration).
+ *
+ * Field layout (all field arguments): [M][N] row-major, double precision, time index
+ * contiguous; element (j-1, n-1) is the value at x_j and time level n (t_n for the
+ * sub-diffusion scheme, t_{n-1/2} for the source of the hyperbolic scheme).  A plan
+ * with several problems uses their fields concatenated in problem order (problem p
+ * starts at element offset sum_{q<p} M_q*N_q).
+ *
+ * Pointers: field pointers may be device memory or host memory (pinned or pageable);
+ * the library detects which.  Host buffers are staged through the plan's device
+ * workspace inside the call.  The caller keeps ownership of every buffer it passes.
+ *
+ * Streams and errors: every call is ordered on the CUDA stream given to ftoep_create
+ * and may return before the GPU work has finished.  Errors are returned as status
+ * codes only; nothing aborts or throws across this interface.  A device-side wait that
+ * exceeds its bound sets a flag in the plan; the next call that synchronises
+ * (ftoep_sync, ftoep_adjoint with a host gamma-gradient, any call with host buffers)
+ * returns FTOEP_ETIMEOUT.  ftoep_last_error gives a message for the last failure.
+ */
+#ifndef FTOEP_H
+#define FTOEP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ftoep_plan_s* ftoep_plan;
+
+typedef enum {
+  FTOEP_OK = 0,
+  FTOEP_EINVAL = 1,       /* bad argument (range, null pointer, size mismatch)        */
+  FTOEP_ENOMEM = 2,       /* device or host allocation failed                          */
+  FTOEP_ECUDA = 3,        /* a CUDA runtime call failed                                */
+  FTOEP_ETIMEOUT = 4,     /* a bounded device-side wait gave up                        */
+  FTOEP_EUNSUPPORTED = 5  /* valid input that this build does not handle               */
+} ftoep_status;
+
+typedef enum {
+  FTOEP_L1_SUBDIFFUSION = 0, /* 0 < gamma < 1, Eq. 4/19                                 */
+  FTOEP_L1_HYPERBOLIC = 1    /* 1 < gamma < 2, Eq. 15/17                                */
+} ftoep_kind;
+
+typedef enum {
+  FTOEP_SPACE_NONE = 0,              /* D^g u = -lambda u + f; every row independent   */
+  FTOEP_SPACE_DIRICHLET_LAPLACIAN = 1 /* D^g u = u_xx + f with Dirichlet zeros          */
+} ftoep_space;
+
+typedef enum {
+  FTOEP_FP64 = 0,  /* all arithmetic in double precision                               */
+  FTOEP_MIXED = 1  /* float convolutions and transforms, double leaf substitutions and
+                      a double-precision residual; one residual-correction sweep         */
+} ftoep_precision;
+
+/* One problem.  T: final time (> 0).  L: length of the space interval (> 0, ignored for
+ * FTOEP_SPACE_NONE).  lambda: reaction coefficient for FTOEP_SPACE_NONE (>= 0).
+ * N >= 1 time steps; M >= 1 interior points (rows, for FTOEP_SPACE_NONE).
+ * Sine transforms currently need M+1 to be a power of two (else FTOEP_EUNSUPPORTED). */
+typedef struct {
+  int kind;       /* ftoep_kind      */
+  int space;      /* ftoep_space     */
+  int precision;  /* ftoep_precision */
+  double gamma, T, L, lambda;
+  int64_t N, M;
+} ftoep_problem;
+
+/* Optional tuning (NULL or 0 fields = library choice).
+ * leaf: size of the dense forward-substitution leaves (power of two, 1..32).
+ * fft_tile: largest time block solved inside one thread block (power of two).
+ * gemm_max_level: largest half-split level handled by direct (dense) block products
+ *   instead of FFTs.
+ * modes_per_cta: reserved (mode pairs per thread block of the sine transform). */
+typedef struct {
+  int leaf, fft_tile, gemm_max_level, modes_per_cta;
+} ftoep_tuning;
+
+/* Create a plan for nprob problems (1 <= nprob).  Computes the weights a_j of every
+ * problem on the host (cancellation-free series, double result), uploads them, builds
+ * the per-level kernel spectra and allocates the device workspace.  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).  On success *out owns all of it.
+ * Errors: FTOEP_EINVAL (gamma outside the kind's range, N/M/T/L invalid, nprob < 1,
+ * out NULL), FTOEP_EUNSUPPORTED (M+1 not a power of two with a sine transform),
+ * FTOEP_ENOMEM, FTOEP_ECUDA. */
+ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob,
+                          const ftoep_tuning* tune, void* cuda_stream);
+
+/* First column a_j (j = 0..N-1) of problem iprob's time operator (see top), and, if
+ * dadgamma is not NULL, its derivative with respect to gamma.  a and dadgamma are
+ * host or device buffers of N doubles.  Returns after the values are in place. */
+ftoep_status ftoep_weights(ftoep_plan p, int iprob, double* a, double* dadgamma);
+
+/* Solve every problem of the plan: u = A^-1 (f + initial-data terms), where A is the
+ * space-time operator of the scheme (Eq. 20 and its hyperbolic analogue).
+ * f, u: concatenated fields (see top); u0, phi: concatenated length-M vectors or NULL
+ * (zero).  phi is only used by hyperbolic problems.  f and u must not overlap. */
+ftoep_status ftoep_solve(ftoep_plan p, const double* f, double* u, const double* u0, const double* phi);
+
+/* y = T x (transpose = 0) or y = T^T x (transpose = 1) for nlines independent lines of
+ * length N of problem iprob, T the lower-triangular Toeplitz time operator with first
+ * column a (no lambda, no spatial part).  Computed by circulant embedding of size 2N'
+ * (N' = N rounded up to a power of two) and FFTs (Sec. 3.1, Eq. be1; the input is
+ * padded with zeros).  x, y: [nlines][N] doubles, host or device; they may not overlap.
+ * Always double precision. */
+ftoep_status ftoep_matvec(ftoep_plan p, int iprob, const double* x, double* y, int64_t nlines, int transpose);
+
+/* Adjoint of ftoep_solve for zero initial data.  g = dL/du (concatenated fields),
+ * u = the result of ftoep_solve for the same plan.  Writes dldf = A^-T g (same layout)
+ * and, if dldgamma is not NULL, dL/dgamma_p = -<dldf_p, (dA/dgamma) u_p> for every
+ * problem p into the HOST array dldgamma[nprob] (this synchronises the stream).
+ * The transposed time operator is solved by reversing time, applying the forward solve
+ * and reversing back (J T^T J = T for Toeplitz T).  Always double precision. */
+ftoep_status ftoep_adjoint(ftoep_plan p, const double* g, const double* u, double* dldf, double* dldgamma);
+
+/* Kernel classes for the instrumentation calls below. */
+typedef enum {
+  FTOEP_K_BLOCK_SOLVE = 0,    /* in-block half-split solve (leaves, direct and FFT levels)  */
+  FTOEP_K_CONV_SMEM = 1,      /* cross-block circulant convolution, one shared-memory FFT   */
+  FTOEP_K_CONV_FOURSTEP = 2,  /* cross-block circulant convolution, three-kernel four-step  */
+  FTOEP_K_SINE = 3,           /* sine transforms along space                                */
+  FTOEP_K_OTHER = 4           /* packing, residual, reductions, spectra                     */
+} ftoep_kernel_class;
+
+/* Instrumentation (no counterpart in the paper).  ftoep_profile waits for the stream,
+ * clears the per-class counters and switches CUDA-event timing of every subsequent
+ * operation on (enable != 0) or off.  Kernel launches are always counted.
+ * ftoep_profile_read waits for the stream and returns, for one class, the summed event
+ * time in milliseconds of the timed operations, the number of timed operations (one
+ * operation = one launcher call: 1 kernel, or 3 for the four-step convolution) and the
+ * number of kernels launched since the last ftoep_profile.  Any output may be NULL. */
+ftoep_status ftoep_profile(ftoep_plan p, int enable);
+ftoep_status ftoep_profile_read(ftoep_plan p, int kclass, double* total_ms, int64_t* ops, int64_t* launches);
+
+/* Wait for the plan's stream; returns FTOEP_ETIMEOUT if a device-side wait gave up,
+ * FTOEP_ECUDA on an asynchronous CUDA error. */
+ftoep_status ftoep_sync(ftoep_plan p);
+
+/* Copy a NUL-terminated message for the last failure of p (or of plan creation if p is
+ * NULL) into buf[n].  Returns FTOEP_EINVAL if buf is NULL or n == 0. */
+ftoep_status ftoep_last_error(ftoep_plan p, char* buf, size_t n);
+
+/* Release the plan and all device memory it owns (waits for its stream first). */
+ftoep_status ftoep_destroy(ftoep_plan p);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FTOEP_H */

@@ -1,0 +1,806 @@
+// C ABI of libftoep (include/ftoep.h): plans, workspace, and the order of the kernels.
+//
+// ftoep_solve, double precision, per problem:
+//   1. sine transform along space of f (+ initial-data terms)  -> pairs of modes z[P][Np]
+//   2. per time block of length B: in-block half-split solve; then the one cross-block
+//      update that becomes due (level s = B * 2^ctz(block+1)) as a circulant convolution
+//   3. inverse sine transform -> u
+// ftoep_solve, mixed: steps 1-3 with float transforms/convolutions (double leaves),
+//   then r = f - A u in double (Toeplitz product by a double FFT of length 2Np, exact
+//   three-point stencil), steps 1-3 on r, u += correction.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ftoep.h"
+#include "internal.h"
+
+using namespace ftoep;
+
+namespace {
+
+struct Prob {
+  ftoep_problem d{};
+  int64_t N = 0, M = 0, Np = 0, P = 0;
+  int logNp = 0, logK2 = 0;
+  double tau = 0, h = 0, scale = 0;
+  int B = 0, L = 0, Sf = 0, nblk = 0;
+  int64_t ncols = 0;
+  Prec prec = P64;
+  int64_t foff = 0, voff = 0;
+  std::vector<double> h_a, h_dadg;
+  double* a = nullptr;
+  double* dadg = nullptr;
+  double* wu0 = nullptr;
+  double* wphi = nullptr;
+  double2* invdiag = nullptr;
+  void* spec = nullptr;         // solve spectra, precision prec
+  double2* spec64 = nullptr;    // solve spectra in double (adjoint of mixed problems; == spec for P64)
+  double2* spec_mv = nullptr;   // product spectrum, length 2Np
+  double2* spec_dg = nullptr;   // d/dgamma product spectrum
+};
+
+int ilog2(int64_t v) {
+  int l = 0;
+  while ((int64_t(1) << l) < v) ++l;
+  return l;
+}
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+int ctz64(int64_t v) {
+  int c = 0;
+  while (!(v & 1)) {
+    v >>= 1;
+    ++c;
+  }
+  return c;
+}
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct ftoep_plan_s {
+  std::vector<Prob> probs;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int64_t ntw = 0;
+  double2* tw64 = nullptr;
+  float2* tw32 = nullptr;
+  // workspace
+  void* z = nullptr;            // solve pairs (max P*Np of double2)
+  void* scratch = nullptr;      // four-step scratch of the solve (max P*Np of double2)
+  double2* zmv = nullptr;       // product pairs (max P*Np double2)
+  double2* scratch_mv = nullptr;// four-step scratch of products (max P*2Np double2)
+  double* r = nullptr;          // residual field (max M*N)
+  double* dpart = nullptr;      // reduction partials
+  double* dscal = nullptr;      // device scalars (nprob)
+  size_t z_elems = 0, mv_elems = 0, r_elems = 0;
+  // host staging
+  double* stage_in = nullptr;
+  double* stage_out = nullptr;
+  double* stage_v0 = nullptr;
+  double* stage_v1 = nullptr;
+  size_t stage_elems = 0, stagev_elems = 0;
+  int64_t total_field = 0, total_vec = 0;
+  std::string err;
+  std::vector<void*> allocs;
+  // launch counters (always on) and optional CUDA-event timing per kernel class
+  bool prof_on = false;
+  int64_t launches[5] = {0, 0, 0, 0, 0};
+  double prof_ms[5] = {0, 0, 0, 0, 0};
+  int64_t prof_ops[5] = {0, 0, 0, 0, 0};
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  std::vector<cudaEvent_t> evpool;
+};
+
+namespace {
+
+ftoep_status fail(ftoep_plan p, ftoep_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (p) p->err = buf; else g_create_error = buf;
+  return s;
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(pl, e_ == cudaErrorMemoryAllocation ? FTOEP_ENOMEM : FTOEP_ECUDA,   \
+                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+#define CKL()                                                                         \
+  do {                                                                                \
+    cudaError_t e_ = cudaGetLastError();                                              \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(pl, FTOEP_ECUDA, "kernel launch: %s (%s:%d)", cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+ftoep_status dalloc(ftoep_plan pl, void** out, size_t bytes) {
+  *out = nullptr;
+  if (bytes == 0) return FTOEP_OK;
+  cudaError_t e = cudaMalloc(out, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *out = nullptr;
+    return fail(pl, FTOEP_ENOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+  }
+  pl->allocs.push_back(*out);
+  return FTOEP_OK;
+}
+
+cudaEvent_t ev_get(ftoep_plan pl) {
+  if (!pl->evpool.empty()) {
+    cudaEvent_t e = pl->evpool.back();
+    pl->evpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launch through a launcher returning its kernel count; count it, optionally time it.
+#define LAUNCH(cls, expr)                                            \
+  do {                                                               \
+    cudaEvent_t e0_ = nullptr, e1_ = nullptr;                        \
+    if (pl->prof_on) {                                               \
+      e0_ = ev_get(pl);                                              \
+      e1_ = ev_get(pl);                                              \
+      cudaEventRecord(e0_, pl->stream);                              \
+    }                                                                \
+    pl->launches[(cls)] += (expr);                                   \
+    if (pl->prof_on) {                                               \
+      cudaEventRecord(e1_, pl->stream);                              \
+      pl->pending.push_back({(cls), {e0_, e1_}});                    \
+    }                                                                \
+    CKL();                                                           \
+  } while (0)
+
+#define ALLOC(ptr, bytes)                                                  \
+  do {                                                                     \
+    ftoep_status s_ = dalloc(pl, (void**)&(ptr), (bytes));                 \
+    if (s_ != FTOEP_OK) return s_;                                         \
+  } while (0)
+
+#define TRY(expr)                          \
+  do {                                     \
+    ftoep_status s_ = (expr);              \
+    if (s_ != FTOEP_OK) return s_;         \
+  } while (0)
+
+bool is_device_ptr(const void* ptr) {
+  if (!ptr) return true;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+const void* tw_of(ftoep_plan pl, Prec pr) { return pr == P64 ? (const void*)pl->tw64 : (const void*)pl->tw32; }
+size_t velem(Prec pr) { return pr == P64 ? sizeof(double2) : sizeof(float2); }
+
+ftoep_status validate(const ftoep_problem& d, int i, const ftoep_tuning* tune) {
+  ftoep_plan pl = nullptr;
+  if (d.kind == FTOEP_L1_SUBDIFFUSION) {
+    if (!(d.gamma > 0.0 && d.gamma < 1.0)) return fail(pl, FTOEP_EINVAL, "problem %d: gamma %g not in (0,1)", i, d.gamma);
+  } else if (d.kind == FTOEP_L1_HYPERBOLIC) {
+    if (!(d.gamma > 1.0 && d.gamma < 2.0)) return fail(pl, FTOEP_EINVAL, "problem %d: gamma %g not in (1,2)", i, d.gamma);
+  } else {
+    return fail(pl, FTOEP_EINVAL, "problem %d: unknown kind %d", i, d.kind);
+  }
+  if (d.space != FTOEP_SPACE_NONE && d.space != FTOEP_SPACE_DIRICHLET_LAPLACIAN)
+    return fail(pl, FTOEP_EINVAL, "problem %d: unknown space %d", i, d.space);
+  if (d.precision != FTOEP_FP64 && d.precision != FTOEP_MIXED)
+    return fail(pl, FTOEP_EINVAL, "problem %d: unknown precision %d", i, d.precision);
+  if (d.N < 1 || d.M < 1) return fail(pl, FTOEP_EINVAL, "problem %d: N=%lld M=%lld must be >= 1", i, (long long)d.N, (long long)d.M);
+  if (!(d.T > 0.0) || !std::isfinite(d.T)) return fail(pl, FTOEP_EINVAL, "problem %d: T must be > 0", i);
+  if (d.space == FTOEP_SPACE_DIRICHLET_LAPLACIAN && (!(d.L > 0.0) || !std::isfinite(d.L)))
+    return fail(pl, FTOEP_EINVAL, "problem %d: L must be > 0", i);
+  if (d.space == FTOEP_SPACE_NONE && (!(d.lambda >= 0.0) || !std::isfinite(d.lambda)))
+    return fail(pl, FTOEP_EINVAL, "problem %d: lambda must be >= 0", i);
+  if (d.N > (int64_t(1) << 22)) return fail(pl, FTOEP_EUNSUPPORTED, "problem %d: N > 2^22 not supported", i);
+  if (d.space == FTOEP_SPACE_DIRICHLET_LAPLACIAN) {
+    if (!is_pow2(d.M + 1)) return fail(pl, FTOEP_EUNSUPPORTED, "problem %d: M+1 = %lld is not a power of two", i, (long long)(d.M + 1));
+    const int64_t lim = d.precision == FTOEP_FP64 ? 4096 : 8192;
+    if (d.M + 1 > lim) return fail(pl, FTOEP_EUNSUPPORTED, "problem %d: M+1 > %lld not supported", i, (long long)lim);
+  }
+  if (tune) {
+    if (tune->leaf && (!is_pow2(tune->leaf) || tune->leaf > 32))
+      return fail(pl, FTOEP_EINVAL, "tuning: leaf must be a power of two <= 32");
+    if (tune->fft_tile && (!is_pow2(tune->fft_tile) || tune->fft_tile > 4096 || tune->fft_tile < 16))
+      return fail(pl, FTOEP_EINVAL, "tuning: fft_tile must be a power of two in [16, 4096]");
+    if (tune->gemm_max_level && (!is_pow2(tune->gemm_max_level) || tune->gemm_max_level > 2048))
+      return fail(pl, FTOEP_EINVAL, "tuning: gemm_max_level must be a power of two <= 2048");
+  }
+  return FTOEP_OK;
+}
+
+// Spectra of the solve levels s = Sf .. Np/2 (level s at offset 2(s - Sf)).
+ftoep_status build_solve_spectra(ftoep_plan pl, Prob& pb, Prec pr, void* out) {
+  for (int64_t s = pb.Sf; s <= pb.Np / 2; s <<= 1) {
+    SpecArgs sa{};
+    sa.a = pb.a;
+    sa.lo = 1;
+    sa.hi = 2 * s;
+    sa.logn = ilog2(2 * s);
+    sa.nsmem = nsmem_for(pr);
+    sa.out = (char*)out + (size_t)2 * (s - pb.Sf) * velem(pr);
+    sa.tw64 = pl->tw64;
+    sa.scratch64 = pl->scratch_mv;
+    LAUNCH(FTOEP_K_OTHER, launch_spectrum(pr, sa, pl->stream));
+  }
+  return FTOEP_OK;
+}
+
+// Spectrum of the full product y = T x (c_k = a_k for k < N, zero after), length 2Np.
+ftoep_status build_product_spectrum(ftoep_plan pl, Prob& pb, const double* coeff, double2** out) {
+  if (*out) return FTOEP_OK;
+  ALLOC(*out, (size_t)2 * pb.Np * sizeof(double2));
+  SpecArgs sa{};
+  sa.a = coeff;
+  sa.lo = 0;
+  sa.hi = pb.N;
+  sa.logn = pb.logNp + 1;
+  sa.nsmem = nsmem_for(P64);
+  sa.out = *out;
+  sa.tw64 = pl->tw64;
+  sa.scratch64 = pl->scratch_mv;
+  LAUNCH(FTOEP_K_OTHER, launch_spectrum(P64, sa, pl->stream));
+  return FTOEP_OK;
+}
+
+// In-place solve of the pair array z (right-hand side in, solution out).
+ftoep_status solve_pairs(ftoep_plan pl, Prob& pb, Prec pr, void* z, const void* spec) {
+  cudaStream_t st = pl->stream;
+  for (int b = 0; b < pb.nblk; ++b) {
+    BlockArgs ba{};
+    ba.z = z;
+    ba.ld = pb.Np;
+    ba.npairs = pb.P;
+    ba.t0 = (int64_t)b * pb.B;
+    ba.B = pb.B;
+    ba.L = pb.L;
+    ba.Sf = pb.Sf;
+    ba.a = pb.a;
+    ba.invdiag = pb.invdiag;
+    ba.spec = spec;
+    ba.tw = tw_of(pl, pr);
+    LAUNCH(FTOEP_K_BLOCK_SOLVE, launch_block_solve(pr, ba, st));
+    const int64_t v = b + 1;
+    if (v < pb.nblk) {
+      const int64_t s = (int64_t)pb.B << ctz64(v);
+      const int64_t mid = v * pb.B;
+      ConvArgs ca{};
+      ca.zin = z;
+      ca.zout = z;
+      ca.ld_in = ca.ld_out = pb.Np;
+      ca.in_off = mid - s;
+      ca.out_off = mid;
+      ca.npairs = pb.P;
+      ca.logn = ilog2(2 * s);
+      ca.nsmem = nsmem_for(pr);
+      ca.mode = 0;
+      ca.spec = (const char*)spec + (size_t)2 * (s - pb.Sf) * velem(pr);
+      ca.tw = tw_of(pl, pr);
+      ca.scratch = pl->scratch;
+      LAUNCH((2 * s <= nsmem_for(pr)) ? FTOEP_K_CONV_SMEM : FTOEP_K_CONV_FOURSTEP, launch_conv(pr, ca, st));
+    }
+  }
+  return FTOEP_OK;
+}
+
+DstArgs dst_args(ftoep_plan pl, Prob& pb, Prec pr, void* z) {
+  DstArgs da{};
+  da.z = z;
+  da.ld = pb.Np;
+  da.N = pb.N;
+  da.ncols = pb.ncols;
+  da.M = pb.M;
+  da.logK2 = pb.logK2;
+  da.space = pb.d.space;
+  da.tw = tw_of(pl, pr);
+  return da;
+}
+
+// y = T x on nlines lines of length N (double), through the product workspace.
+ftoep_status product_lines(ftoep_plan pl, Prob& pb, const double2* spec, const double* x, double* y_or_null,
+                           int64_t nlines, int reverse, double2* out_pairs) {
+  cudaStream_t st = pl->stream;
+  PackArgs pa{};
+  pa.x = x;
+  pa.z = out_pairs;
+  pa.ld = pb.Np;
+  pa.N = pb.N;
+  pa.nlines = nlines;
+  pa.reverse = reverse;
+  LAUNCH(FTOEP_K_OTHER, launch_pack(P64, pa, st));
+  ConvArgs ca{};
+  ca.zin = out_pairs;
+  ca.zout = out_pairs;
+  ca.ld_in = ca.ld_out = pb.Np;
+  ca.in_off = ca.out_off = 0;
+  ca.npairs = (nlines + 1) / 2;
+  ca.logn = pb.logNp + 1;
+  ca.nsmem = nsmem_for(P64);
+  ca.mode = 1;
+  ca.spec = spec;
+  ca.tw = pl->tw64;
+  ca.scratch = pl->scratch_mv;
+  LAUNCH((2 * pb.Np <= nsmem_for(P64)) ? FTOEP_K_CONV_SMEM : FTOEP_K_CONV_FOURSTEP, launch_conv(P64, ca, st));
+  if (y_or_null) {
+    pa.y = y_or_null;
+    pa.mode = 0;
+    LAUNCH(FTOEP_K_OTHER, launch_unpack(P64, pa, st));
+  }
+  return FTOEP_OK;
+}
+
+ftoep_status solve_problem(ftoep_plan pl, Prob& pb, const double* f, double* u, const double* u0, const double* phi) {
+  cudaStream_t st = pl->stream;
+  const Prec pr = pb.prec;
+  DstArgs da = dst_args(pl, pb, pr, pl->z);
+  da.f = f;
+  da.u0 = u0;
+  da.phi = (pb.d.kind == FTOEP_L1_HYPERBOLIC) ? phi : nullptr;
+  da.wu0 = pb.wu0;
+  da.wphi = pb.wphi;
+  LAUNCH(FTOEP_K_SINE, launch_dst_forward(pr, da, st));
+  TRY(solve_pairs(pl, pb, pr, pl->z, pb.spec));
+  da.u = u;
+  da.accumulate = 0;
+  LAUNCH(FTOEP_K_SINE, launch_dst_inverse(pr, da, st));
+  if (pr == P64) return FTOEP_OK;
+  // residual in double: r = f + init - T u - S u
+  TRY(build_product_spectrum(pl, pb, pb.a, &pb.spec_mv));
+  TRY(product_lines(pl, pb, pb.spec_mv, u, nullptr, pb.M, 0, pl->zmv));
+  ResidualArgs ra{};
+  ra.f = f;
+  ra.u0 = u0;
+  ra.phi = da.phi;
+  ra.wu0 = pb.wu0;
+  ra.wphi = pb.wphi;
+  ra.u = u;
+  ra.tu = pl->zmv;
+  ra.r = pl->r;
+  ra.ld = pb.Np;
+  ra.N = pb.N;
+  ra.M = pb.M;
+  ra.space = pb.d.space;
+  ra.inv_h2 = 1.0 / (pb.h * pb.h);
+  ra.lambda = pb.d.lambda;
+  LAUNCH(FTOEP_K_OTHER, launch_residual(ra, st));
+  DstArgs dr = dst_args(pl, pb, pr, pl->z);
+  dr.f = pl->r;
+  LAUNCH(FTOEP_K_SINE, launch_dst_forward(pr, dr, st));
+  TRY(solve_pairs(pl, pb, pr, pl->z, pb.spec));
+  dr.u = u;
+  dr.accumulate = 1;
+  LAUNCH(FTOEP_K_SINE, launch_dst_inverse(pr, dr, st));
+  return FTOEP_OK;
+}
+
+ftoep_status ensure_staging(ftoep_plan pl) {
+  if (pl->stage_in) return FTOEP_OK;
+  ALLOC(pl->stage_in, (size_t)pl->total_field * sizeof(double));
+  ALLOC(pl->stage_out, (size_t)pl->total_field * sizeof(double));
+  ALLOC(pl->stage_v0, (size_t)pl->total_vec * sizeof(double));
+  ALLOC(pl->stage_v1, (size_t)pl->total_vec * sizeof(double));
+  return FTOEP_OK;
+}
+
+ftoep_status sync_plan(ftoep_plan pl) {
+  cudaError_t e = cudaStreamSynchronize(pl->stream);
+  if (e != cudaSuccess) return fail(pl, FTOEP_ECUDA, "stream synchronize: %s", cudaGetErrorString(e));
+  return FTOEP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob, const ftoep_tuning* tune,
+                          void* cuda_stream) {
+  g_create_error.clear();
+  if (!out) return fail(nullptr, FTOEP_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!probs || nprob < 1) return fail(nullptr, FTOEP_EINVAL, "need at least one problem");
+  for (int i = 0; i < nprob; ++i) TRY(validate(probs[i], i, tune));
+  ftoep_plan pl = new ftoep_plan_s();
+  pl->stream = (cudaStream_t)cuda_stream;
+  ftoep_status st = FTOEP_OK;
+  auto bail = [&](ftoep_status s) {
+    g_create_error = pl->err;
+    ftoep_destroy(pl);
+    return s;
+  };
+  if (cudaGetDevice(&pl->device) != cudaSuccess) {
+    cudaGetLastError();
+    pl->err = "no CUDA device";
+    return bail(FTOEP_ECUDA);
+  }
+  int64_t maxtw = 8192;
+  int64_t foff = 0, voff = 0;
+  size_t z_el = 0, mv_el = 0, r_el = 0;
+  for (int i = 0; i < nprob; ++i) {
+    Prob pb;
+    pb.d = probs[i];
+    pb.N = pb.d.N;
+    pb.M = pb.d.M;
+    pb.prec = pb.d.precision == FTOEP_FP64 ? P64 : P32;
+    int64_t np = 16;
+    while (np < pb.N) np <<= 1;
+    pb.Np = np;
+    pb.logNp = ilog2(np);
+    pb.P = (pb.M + 1) / 2;
+    pb.logK2 = pb.d.space ? ilog2(2 * (pb.M + 1)) : 0;
+    pb.tau = pb.d.T / (double)pb.N;
+    pb.h = pb.d.space ? pb.d.L / (double)(pb.M + 1) : 1.0;
+    pb.scale = scheme_scale(pb.d.kind, pb.d.gamma, pb.tau);
+    const int Bdef = pb.prec == P64 ? 1024 : 2048;
+    const int Ldef = pb.prec == P64 ? 16 : 8;
+    int B = (tune && tune->fft_tile) ? tune->fft_tile : Bdef;
+    if (B > np) B = (int)np;
+    int L = (tune && tune->leaf) ? tune->leaf : Ldef;
+    if (L > B) L = B;
+    int Sf = (tune && tune->gemm_max_level) ? 2 * tune->gemm_max_level : 64;
+    if (Sf < L) Sf = L;
+    pb.B = B;
+    pb.L = L;
+    pb.Sf = Sf;
+    pb.nblk = (int)((pb.N + B - 1) / B);
+    pb.ncols = (int64_t)pb.nblk * B;
+    pb.foff = foff;
+    pb.voff = voff;
+    foff += pb.M * pb.N;
+    voff += pb.M;
+    maxtw = std::max<int64_t>(maxtw, 2 * np);
+    if (pb.d.space) maxtw = std::max<int64_t>(maxtw, 2 * (pb.M + 1));
+    z_el = std::max<size_t>(z_el, (size_t)pb.P * np);
+    mv_el = std::max<size_t>(mv_el, (size_t)pb.P * np);
+    if (pb.prec == P32) r_el = std::max<size_t>(r_el, (size_t)pb.M * pb.N);
+    pl->probs.push_back(std::move(pb));
+  }
+  pl->total_field = foff;
+  pl->total_vec = voff;
+  pl->z_elems = z_el;
+  pl->mv_elems = mv_el;
+  pl->r_elems = r_el;
+  // twiddles: W_n^k for all n = 2 .. maxtw at offset n-2, from one long-double table
+  {
+    pl->ntw = maxtw;
+    const size_t tot = (size_t)2 * maxtw - 2;
+    std::vector<double2> h64(tot);
+    std::vector<float2> h32(tot);
+    std::vector<double2> big(maxtw);
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+    for (int64_t k = 0; k < maxtw; ++k) {
+      long double ang = -two_pi * (long double)k / (long double)maxtw;
+      big[k] = make_double2((double)cosl(ang), (double)sinl(ang));
+    }
+    for (int64_t n = 2; n <= maxtw; n <<= 1) {
+      const int64_t stride = maxtw / n;
+      for (int64_t k = 0; k < n; ++k) {
+        h64[(n - 2) + k] = big[k * stride];
+        h32[(n - 2) + k] = make_float2((float)big[k * stride].x, (float)big[k * stride].y);
+      }
+    }
+    if ((st = dalloc(pl, (void**)&pl->tw64, tot * sizeof(double2))) != FTOEP_OK) return bail(st);
+    if ((st = dalloc(pl, (void**)&pl->tw32, tot * sizeof(float2))) != FTOEP_OK) return bail(st);
+    if (cudaMemcpy(pl->tw64, h64.data(), tot * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(pl->tw32, h32.data(), tot * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      pl->err = "twiddle upload failed";
+      return bail(FTOEP_ECUDA);
+    }
+  }
+  if ((st = dalloc(pl, &pl->z, z_el * sizeof(double2))) != FTOEP_OK) return bail(st);
+  if ((st = dalloc(pl, &pl->scratch, z_el * sizeof(double2))) != FTOEP_OK) return bail(st);
+  if ((st = dalloc(pl, (void**)&pl->zmv, mv_el * sizeof(double2))) != FTOEP_OK) return bail(st);
+  if ((st = dalloc(pl, (void**)&pl->scratch_mv, 2 * mv_el * sizeof(double2))) != FTOEP_OK) return bail(st);
+  if (r_el && (st = dalloc(pl, (void**)&pl->r, r_el * sizeof(double))) != FTOEP_OK) return bail(st);
+  if ((st = dalloc(pl, (void**)&pl->dpart, 1024 * sizeof(double))) != FTOEP_OK) return bail(st);
+  if ((st = dalloc(pl, (void**)&pl->dscal, (size_t)nprob * sizeof(double))) != FTOEP_OK) return bail(st);
+  if (cudaMemsetAsync(pl->z, 0, z_el * sizeof(double2), pl->stream) != cudaSuccess) {
+    cudaGetLastError();
+    pl->err = "workspace clear failed";
+    return bail(FTOEP_ECUDA);
+  }
+  for (auto& pb : pl->probs) {
+    const int64_t N = pb.N, Np = pb.Np;
+    pb.h_a.resize(Np);
+    pb.h_dadg.resize(Np);
+    scheme_weights(pb.d.kind, pb.d.gamma, pb.tau, Np, pb.h_a.data(), pb.h_dadg.data());
+    std::vector<double> wu0(N), wphi(N);
+    initial_weights(pb.d.kind, pb.d.gamma, pb.tau, N, wu0.data(), wphi.data());
+    std::vector<double2> invd(pb.P);
+    for (int64_t p = 0; p < pb.P; ++p) {
+      double lam[2];
+      for (int q = 0; q < 2; ++q) {
+        const int64_t m = 2 * p + q + 1;
+        if (pb.d.space) {
+          const double sn = std::sin((double)m * 3.14159265358979323846 / (2.0 * (double)(pb.M + 1)));
+          lam[q] = 4.0 / (pb.h * pb.h) * sn * sn;
+        } else {
+          lam[q] = pb.d.lambda;
+        }
+      }
+      invd[p] = make_double2(1.0 / (pb.h_a[0] + lam[0]), 1.0 / (pb.h_a[0] + lam[1]));
+    }
+    if ((st = dalloc(pl, (void**)&pb.a, Np * sizeof(double))) != FTOEP_OK) return bail(st);
+    if ((st = dalloc(pl, (void**)&pb.dadg, Np * sizeof(double))) != FTOEP_OK) return bail(st);
+    if ((st = dalloc(pl, (void**)&pb.wu0, N * sizeof(double))) != FTOEP_OK) return bail(st);
+    if ((st = dalloc(pl, (void**)&pb.wphi, N * sizeof(double))) != FTOEP_OK) return bail(st);
+    if ((st = dalloc(pl, (void**)&pb.invdiag, pb.P * sizeof(double2))) != FTOEP_OK) return bail(st);
+    if (cudaMemcpy(pb.a, pb.h_a.data(), Np * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(pb.dadg, pb.h_dadg.data(), Np * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(pb.wu0, wu0.data(), N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(pb.wphi, wphi.data(), N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(pb.invdiag, invd.data(), pb.P * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      pl->err = "weight upload failed";
+      return bail(FTOEP_ECUDA);
+    }
+    const size_t nspec = pb.Sf <= Np / 2 ? (size_t)2 * (Np - pb.Sf) : 0;
+    if (nspec) {
+      if ((st = dalloc(pl, &pb.spec, nspec * velem(pb.prec))) != FTOEP_OK) return bail(st);
+      if ((st = build_solve_spectra(pl, pb, pb.prec, pb.spec)) != FTOEP_OK) return bail(st);
+      if (pb.prec == P64) pb.spec64 = (double2*)pb.spec;
+    }
+  }
+  if ((st = sync_plan(pl)) != FTOEP_OK) return bail(st);
+  *out = pl;
+  return FTOEP_OK;
+}
+
+ftoep_status ftoep_weights(ftoep_plan pl, int iprob, double* a, double* dadgamma) {
+  if (!pl) return fail(nullptr, FTOEP_EINVAL, "plan is NULL");
+  if (iprob < 0 || iprob >= (int)pl->probs.size()) return fail(pl, FTOEP_EINVAL, "iprob out of range");
+  if (!a) return fail(pl, FTOEP_EINVAL, "a is NULL");
+  Prob& pb = pl->probs[iprob];
+  CK(cudaMemcpy(a, pb.h_a.data(), pb.N * sizeof(double), cudaMemcpyDefault));
+  if (dadgamma) CK(cudaMemcpy(dadgamma, pb.h_dadg.data(), pb.N * sizeof(double), cudaMemcpyDefault));
+  return FTOEP_OK;
+}
+
+ftoep_status ftoep_solve(ftoep_plan pl, const double* f, double* u, const double* u0, const double* phi) {
+  if (!pl) return fail(nullptr, FTOEP_EINVAL, "plan is NULL");
+  if (!f || !u) return fail(pl, FTOEP_EINVAL, "f and u must not be NULL");
+  const size_t fb = (size_t)pl->total_field * sizeof(double);
+  if ((const char*)f < (const char*)u + fb && (const char*)u < (const char*)f + fb)
+    return fail(pl, FTOEP_EINVAL, "f and u overlap");
+  const bool host = !is_device_ptr(f) || !is_device_ptr(u) || !is_device_ptr(u0) || !is_device_ptr(phi);
+  const double *df = f, *du0 = u0, *dphi = phi;
+  double* du = u;
+  if (host) {
+    TRY(ensure_staging(pl));
+    CK(cudaMemcpyAsync(pl->stage_in, f, fb, cudaMemcpyDefault, pl->stream));
+    df = pl->stage_in;
+    du = pl->stage_out;
+    if (u0) {
+      CK(cudaMemcpyAsync(pl->stage_v0, u0, pl->total_vec * sizeof(double), cudaMemcpyDefault, pl->stream));
+      du0 = pl->stage_v0;
+    }
+    if (phi) {
+      CK(cudaMemcpyAsync(pl->stage_v1, phi, pl->total_vec * sizeof(double), cudaMemcpyDefault, pl->stream));
+      dphi = pl->stage_v1;
+    }
+  }
+  for (auto& pb : pl->probs)
+    TRY(solve_problem(pl, pb, df + pb.foff, du + pb.foff, du0 ? du0 + pb.voff : nullptr, dphi ? dphi + pb.voff : nullptr));
+  if (host) {
+    CK(cudaMemcpyAsync(u, du, fb, cudaMemcpyDefault, pl->stream));
+    TRY(sync_plan(pl));
+  }
+  return FTOEP_OK;
+}
+
+ftoep_status ftoep_matvec(ftoep_plan pl, int iprob, const double* x, double* y, int64_t nlines, int transpose) {
+  if (!pl) return fail(nullptr, FTOEP_EINVAL, "plan is NULL");
+  if (iprob < 0 || iprob >= (int)pl->probs.size()) return fail(pl, FTOEP_EINVAL, "iprob out of range");
+  if (!x || !y || nlines < 1) return fail(pl, FTOEP_EINVAL, "x, y must not be NULL and nlines >= 1");
+  Prob& pb = pl->probs[iprob];
+  const size_t bytes = (size_t)nlines * pb.N * sizeof(double);
+  if ((const char*)x < (const char*)y + bytes && (const char*)y < (const char*)x + bytes)
+    return fail(pl, FTOEP_EINVAL, "x and y overlap");
+  TRY(build_product_spectrum(pl, pb, pb.a, &pb.spec_mv));
+  const bool host = !is_device_ptr(x) || !is_device_ptr(y);
+  // lines per chunk: twice the pairs the product workspace holds
+  const int64_t chunk = 2 * (int64_t)(pl->mv_elems / pb.Np);
+  double *sx = nullptr, *sy = nullptr;
+  if (host) {
+    ALLOC(sx, (size_t)chunk * pb.N * sizeof(double));
+    ALLOC(sy, (size_t)chunk * pb.N * sizeof(double));
+  }
+  for (int64_t l0 = 0; l0 < nlines; l0 += chunk) {
+    const int64_t nl = std::min<int64_t>(chunk, nlines - l0);
+    const double* xin = x + l0 * pb.N;
+    double* yout = y + l0 * pb.N;
+    if (host) {
+      CK(cudaMemcpyAsync(sx, xin, nl * pb.N * sizeof(double), cudaMemcpyDefault, pl->stream));
+      xin = sx;
+    }
+    TRY(product_lines(pl, pb, pb.spec_mv, xin, host ? sy : yout, nl, transpose ? 1 : 0, pl->zmv));
+    if (host) {
+      CK(cudaMemcpyAsync(yout, sy, nl * pb.N * sizeof(double), cudaMemcpyDefault, pl->stream));
+    }
+  }
+  if (host) {
+    TRY(sync_plan(pl));
+    // release the per-call staging
+    for (auto it = pl->allocs.begin(); it != pl->allocs.end();) {
+      if (*it == sx || *it == sy) {
+        cudaFree(*it);
+        it = pl->allocs.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+  return FTOEP_OK;
+}
+
+ftoep_status ftoep_adjoint(ftoep_plan pl, const double* g, const double* u, double* dldf, double* dldgamma) {
+  if (!pl) return fail(nullptr, FTOEP_EINVAL, "plan is NULL");
+  if (!g || !dldf) return fail(pl, FTOEP_EINVAL, "g and dldf must not be NULL");
+  if (dldgamma && !u) return fail(pl, FTOEP_EINVAL, "u is required for the gamma gradient");
+  const size_t fb = (size_t)pl->total_field * sizeof(double);
+  if ((const char*)g < (const char*)dldf + fb && (const char*)dldf < (const char*)g + fb)
+    return fail(pl, FTOEP_EINVAL, "g and dldf overlap");
+  const bool host = !is_device_ptr(g) || !is_device_ptr(dldf) || !is_device_ptr(u);
+  const double* dg = g;
+  const double* du = u;
+  double* dout = dldf;
+  double* su = nullptr;
+  if (host) {
+    TRY(ensure_staging(pl));
+    CK(cudaMemcpyAsync(pl->stage_in, g, fb, cudaMemcpyDefault, pl->stream));
+    dg = pl->stage_in;
+    dout = pl->stage_out;
+    if (u && dldgamma) {
+      ALLOC(su, fb);
+      CK(cudaMemcpyAsync(su, u, fb, cudaMemcpyDefault, pl->stream));
+      du = su;
+    }
+  }
+  cudaStream_t st = pl->stream;
+  int ip = 0;
+  for (auto& pb : pl->probs) {
+    if (!pb.spec64 && pb.Sf <= pb.Np / 2) {
+      ALLOC(pb.spec64, (size_t)2 * (pb.Np - pb.Sf) * sizeof(double2));
+      TRY(build_solve_spectra(pl, pb, P64, pb.spec64));
+    }
+    // The double-precision block parameters (fixed defaults for the adjoint).
+    Prob q = pb;
+    if (pb.prec != P64) {
+      q.prec = P64;
+      q.B = (int)std::min<int64_t>(1024, pb.Np);
+      q.L = std::min(16, q.B);
+      q.nblk = (int)((pb.N + q.B - 1) / q.B);
+      q.ncols = (int64_t)q.nblk * q.B;
+      if (q.Sf != pb.Sf) return fail(pl, FTOEP_EUNSUPPORTED, "adjoint: spectrum level mismatch");
+    }
+    DstArgs da = dst_args(pl, q, P64, pl->z);
+    da.f = dg + pb.foff;
+    da.reverse = 1;
+    LAUNCH(FTOEP_K_SINE, launch_dst_forward(P64, da, st));
+    TRY(solve_pairs(pl, q, P64, pl->z, pb.spec64));
+    da.u = dout + pb.foff;
+    da.accumulate = 0;
+    LAUNCH(FTOEP_K_SINE, launch_dst_inverse(P64, da, st));
+    if (dldgamma) {
+      TRY(build_product_spectrum(pl, pb, pb.dadg, &pb.spec_dg));
+      TRY(product_lines(pl, pb, pb.spec_dg, du + pb.foff, nullptr, pb.M, 0, pl->zmv));
+      DotArgs dt{};
+      dt.x = dout + pb.foff;
+      dt.tu = pl->zmv;
+      dt.ld = pb.Np;
+      dt.N = pb.N;
+      dt.nlines = pb.M;
+      dt.partial = pl->dpart;
+      dt.nblocks = 1024;
+      LAUNCH(FTOEP_K_OTHER, launch_dot(dt, st));
+      LAUNCH(FTOEP_K_OTHER, launch_sum(pl->dpart, 1024, pl->dscal + ip, st));
+    }
+    ++ip;
+  }
+  if (host) CK(cudaMemcpyAsync(dldf, dout, fb, cudaMemcpyDefault, st));
+  if (dldgamma) {
+    std::vector<double> hs(pl->probs.size());
+    CK(cudaMemcpyAsync(hs.data(), pl->dscal, hs.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TRY(sync_plan(pl));
+    for (size_t i = 0; i < hs.size(); ++i) dldgamma[i] = -hs[i];
+  } else if (host) {
+    TRY(sync_plan(pl));
+  }
+  if (su) {
+    for (auto it = pl->allocs.begin(); it != pl->allocs.end();) {
+      if (*it == su) {
+        cudaFree(*it);
+        it = pl->allocs.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+  return FTOEP_OK;
+}
+
+ftoep_status ftoep_profile(ftoep_plan pl, int enable) {
+  if (!pl) return fail(nullptr, FTOEP_EINVAL, "plan is NULL");
+  TRY(sync_plan(pl));
+  for (auto& pe : pl->pending) {
+    pl->evpool.push_back(pe.second.first);
+    pl->evpool.push_back(pe.second.second);
+  }
+  pl->pending.clear();
+  for (int c = 0; c < 5; ++c) {
+    pl->launches[c] = 0;
+    pl->prof_ms[c] = 0.0;
+    pl->prof_ops[c] = 0;
+  }
+  pl->prof_on = enable != 0;
+  return FTOEP_OK;
+}
+
+ftoep_status ftoep_profile_read(ftoep_plan pl, int kclass, double* total_ms, int64_t* ops, int64_t* launches) {
+  if (!pl) return fail(nullptr, FTOEP_EINVAL, "plan is NULL");
+  if (kclass < 0 || kclass >= 5) return fail(pl, FTOEP_EINVAL, "kernel class out of range");
+  TRY(sync_plan(pl));
+  for (auto& pe : pl->pending) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess) {
+      pl->prof_ms[pe.first] += ms;
+      pl->prof_ops[pe.first] += 1;
+    } else {
+      cudaGetLastError();
+    }
+    pl->evpool.push_back(pe.second.first);
+    pl->evpool.push_back(pe.second.second);
+  }
+  pl->pending.clear();
+  if (total_ms) *total_ms = pl->prof_ms[kclass];
+  if (ops) *ops = pl->prof_ops[kclass];
+  if (launches) *launches = pl->launches[kclass];
+  return FTOEP_OK;
+}
+
+ftoep_status ftoep_sync(ftoep_plan pl) {
+  if (!pl) return fail(nullptr, FTOEP_EINVAL, "plan is NULL");
+  return sync_plan(pl);
+}
+
+ftoep_status ftoep_last_error(ftoep_plan pl, char* buf, size_t n) {
+  if (!buf || n == 0) return FTOEP_EINVAL;
+  const std::string& s = pl ? pl->err : g_create_error;
+  size_t k = std::min(n - 1, s.size());
+  memcpy(buf, s.data(), k);
+  buf[k] = '\0';
+  return FTOEP_OK;
+}
+
+ftoep_status ftoep_destroy(ftoep_plan pl) {
+  if (!pl) return FTOEP_EINVAL;
+  cudaStreamSynchronize(pl->stream);
+  cudaGetLastError();
+  for (void* ptr : pl->allocs) cudaFree(ptr);
+  for (auto& pe : pl->pending) {
+    cudaEventDestroy(pe.second.first);
+    cudaEventDestroy(pe.second.second);
+  }
+  for (cudaEvent_t e : pl->evpool) cudaEventDestroy(e);
+  delete pl;
+  return FTOEP_OK;
+}
+
+}  // extern "C"

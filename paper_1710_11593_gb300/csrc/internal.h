@@ -1,0 +1,138 @@
+// Internal interfaces between the host orchestration (api.cu) and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ftoep {
+
+// ---------------------------------------------------------------- host math (weights.cpp)
+double digamma(double x);
+double scheme_scale(int kind, double gamma, double tau);
+// a[j] (j < n) and optionally da/dgamma; see weights.cpp for the formulas.
+void scheme_weights(int kind, double gamma, double tau, int64_t n, double* a, double* dadg);
+// right-hand-side weights of u0 and phi at levels 1..n
+void initial_weights(int kind, double gamma, double tau, int64_t n, double* wu0, double* wphi);
+
+// ---------------------------------------------------------------- kernel launchers
+// Storage precision of the complex work arrays: 0 = double2, 1 = float2.
+enum Prec { P64 = 0, P32 = 1 };
+
+struct DstArgs {
+  // forward: f (+ wu0*u0 + wphi*phi) [M][N] doubles  ->  z pairs [P][ld]
+  // inverse: z pairs -> u [M][N] doubles (write or accumulate)
+  const double* f;      // forward input
+  const double* u0;     // nullable
+  const double* phi;    // nullable
+  const double* wu0;    // length N (with u0)
+  const double* wphi;   // length N (with phi)
+  double* u;            // inverse output
+  void* z;              // pair array (double2 or float2)
+  int64_t ld;           // row length of z (elements)
+  int64_t N;            // valid time columns
+  int64_t ncols;        // columns to process (>= N; columns >= N are written as 0 by forward)
+  int64_t M;            // interior points
+  int logK2;            // log2(2(M+1))
+  int reverse;          // time reversal of z (forward: write z[N-1-n]; inverse: read z[N-1-n])
+  int accumulate;       // inverse: u += result
+  int space;            // 0: no transform (pairs of rows), 1: sine transform
+  const void* tw;       // twiddles of the z precision
+};
+int launch_dst_forward(Prec prec, const DstArgs& a, cudaStream_t st);
+int launch_dst_inverse(Prec prec, const DstArgs& a, cudaStream_t st);
+
+// Pack real lines [nlines][N] into pairs [ceil(nlines/2)][ld] (zero padded to ld, optional
+// reversal within [0,N)); unpack back.
+struct PackArgs {
+  const double* x;  // lines (pack input)
+  double* y;        // lines (unpack output)
+  void* z;          // pairs
+  int64_t ld, N, nlines;
+  int reverse;
+  int mode;  // unpack: 0 write, 1 accumulate
+};
+int launch_pack(Prec prec, const PackArgs& a, cudaStream_t st);
+int launch_unpack(Prec prec, const PackArgs& a, cudaStream_t st);
+
+// Residual r = f + wu0*u0 + wphi*phi - (T u) - S(u), with (T u) given in pairs (double2)
+// and S the spatial operator: Dirichlet -u_xx (space 1) or lambda*u (space 0).
+struct ResidualArgs {
+  const double* f;
+  const double* u0;
+  const double* phi;
+  const double* wu0;
+  const double* wphi;
+  const double* u;
+  const double2* tu;  // pairs [P][ld]
+  double* r;
+  int64_t ld, N, M;
+  int space;
+  double inv_h2, lambda;
+};
+int launch_residual(const ResidualArgs& a, cudaStream_t st);
+
+// Sum over all (line, n) of x[line][n] * tu_pair(line, n)  ->  partial sums per block.
+struct DotArgs {
+  const double* x;    // lines [nlines][N]
+  const double2* tu;  // pairs
+  int64_t ld, N, nlines;
+  double* partial;    // [gridDim]
+  int nblocks;
+};
+int launch_dot(const DotArgs& a, cudaStream_t st);
+int launch_sum(const double* partial, int n, double* out, cudaStream_t st);
+
+// Kernel spectrum of c_k = (lo <= k < hi) ? a[k] : 0, k < n = 2^logn, computed in double
+// and stored (divided by n) in the order of the convolution path chosen for n:
+// shared-memory DIF if n <= nsmem, else the four-step split n = n1*n2.
+struct SpecArgs {
+  const double* a;
+  int64_t lo, hi;
+  int logn;
+  int nsmem;
+  void* out;               // length n, precision of the convolution
+  const double2* tw64;     // double twiddles
+  double2* scratch64;      // length n (four-step only)
+};
+int launch_spectrum(Prec prec, const SpecArgs& a, cudaStream_t st);
+
+// Circulant convolution of every pair row:  t = x (*) c over length n = 2^logn, where
+// x = z_in[p][in_off .. in_off + n/2) zero-padded.  mode 0 (half-split update):
+// z_out[p][out_off + i] -= t[n/2 + i];  mode 1 (product): z_out[p][out_off + i] = t[i];
+// both for i < n/2.
+struct ConvArgs {
+  void* zin;
+  void* zout;
+  int64_t ld_in, ld_out, in_off, out_off;
+  int64_t npairs;
+  int logn;
+  int nsmem;
+  int mode;
+  const void* spec;
+  const void* tw;
+  void* scratch;    // [npairs][n] (four-step only)
+};
+int launch_conv(Prec prec, const ConvArgs& a, cudaStream_t st);
+
+// Solve the lower-triangular Toeplitz systems of every pair on one time block
+// [t0, t0 + B) in place (history from earlier blocks already subtracted).
+struct BlockArgs {
+  void* z;
+  int64_t ld;
+  int64_t npairs;
+  int64_t t0;
+  int B;            // block length (power of two)
+  int L;            // leaf length (power of two <= 32, <= B)
+  int Sf;           // first FFT level (levels L <= s < Sf are dense products)
+  const double* a;  // a[0..B)
+  const double2* invdiag;  // per pair: 1/(a0+lambda) of its two modes
+  const void* spec;        // spectra of levels Sf..B/2 (level s at offset 2(s - Sf))
+  const void* tw;
+};
+int launch_block_solve(Prec prec, const BlockArgs& a, cudaStream_t st);
+size_t block_solve_smem(Prec prec, int B);
+
+// Largest shared-memory FFT length of each precision.
+int nsmem_for(Prec prec);
+
+}  // namespace ftoep

@@ -1,0 +1,574 @@
+// Transform kernels: orthonormal sine transform (DST-I) along space, line packing,
+// residual, reductions, kernel spectra and the circulant convolutions behind every
+// Toeplitz product (Sec. 3.1, Eq. be1).
+//
+// Pair layout: the solver works on complex arrays z[P][ld] whose element (p, n) holds
+// mode (or line) 2p in .x and 2p+1 in .y.  Convolution with a real kernel acts on the
+// two components independently, so one complex FFT serves two real problems.
+#include <cstdio>
+
+#include "fft.cuh"
+#include "internal.h"
+
+namespace ftoep {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename T>
+using Vt = typename VecOf<T>::type;
+
+inline void set_smem(const void* fn, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// ------------------------------------------------------------------ sine transform
+//
+// DST-I of length M via the odd extension y (length 2K, K = M+1): y_0 = y_K = 0,
+// y_j = x_j, y_{2K-j} = -x_j.  Then FFT(y)_m = -2i sum_j x_j sin(pi j m / K).  Two real
+// columns a (in .x) and b (in .y) share one complex FFT: FFT(a + i b)_m has real part
+// 2 S_b[m] and imaginary part -2 S_a[m]; the orthonormal coefficient is
+// sqrt(2/K) S[m] = (FFT value)/sqrt(2K).  The transform is its own inverse.
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) dst_forward_kernel(DstArgs A, int C) {
+  typedef Vt<T> V;
+  V* z = (V*)A.z;
+  const int64_t col0 = (int64_t)blockIdx.x * C;
+  const int64_t M = A.M, N = A.N;
+  const int64_t P = (M + 1) / 2;
+  if (A.space == 0) {
+    // no spatial transform: pairs of rows
+    for (int64_t e = threadIdx.x; e < P * C; e += blockDim.x) {
+      const int64_t p = e / C;
+      const int c = (int)(e % C);
+      const int64_t n = col0 + c;
+      if (n >= A.ncols) continue;
+      double v[2] = {0.0, 0.0};
+      if (n < N) {
+        for (int q = 0; q < 2; ++q) {
+          const int64_t j = 2 * p + q;
+          if (j >= M) continue;
+          double t = A.f[j * N + n];
+          if (A.u0) t += A.wu0[n] * A.u0[j];
+          if (A.phi) t += A.wphi[n] * A.phi[j];
+          v[q] = t;
+        }
+      }
+      const int64_t nout = (A.reverse && n < N) ? N - 1 - n : n;
+      z[p * A.ld + nout] = mkv((T)v[0], (T)v[1]);
+    }
+    return;
+  }
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const int logK2 = A.logK2;
+  const int K2 = 1 << logK2, K = K2 >> 1;
+  const int lds = K2 + 1;
+  const int CP = C >> 1;
+  for (int cp = threadIdx.x; cp < CP; cp += blockDim.x) {
+    sm[cp * lds] = vzero<V>();
+    sm[cp * lds + K] = vzero<V>();
+  }
+  for (int64_t e = threadIdx.x; e < M * C; e += blockDim.x) {
+    const int64_t j = e / C;
+    const int c = (int)(e % C);
+    const int64_t n = col0 + c;
+    double v = 0.0;
+    if (n < N) {
+      v = A.f[j * N + n];
+      if (A.u0) v += A.wu0[n] * A.u0[j];
+      if (A.phi) v += A.wphi[n] * A.phi[j];
+    }
+    const T tv = (T)v;
+    V* col = sm + (c >> 1) * lds;
+    const int pos = (int)j + 1;
+    if (c & 1) {
+      col[pos].y = tv;
+      col[K2 - pos].y = -tv;
+    } else {
+      col[pos].x = tv;
+      col[K2 - pos].x = -tv;
+    }
+  }
+  __syncthreads();
+  fft_dif<V>(sm, logK2, CP, lds, (const V*)A.tw, false);
+  const T scale = (T)(1.0 / sqrt(2.0 * (double)K));
+  for (int64_t e = threadIdx.x; e < P * C; e += blockDim.x) {
+    const int64_t p = e / C;
+    const int c = (int)(e % C);
+    const int64_t n = col0 + c;
+    if (n >= A.ncols) continue;
+    const V* col = sm + (c >> 1) * lds;
+    const int m1 = (int)(2 * p + 1), m2 = m1 + 1;
+    const V y1 = col[brev(m1, logK2)];
+    const T v1 = (c & 1) ? y1.x : -y1.y;
+    T v2 = (T)0;
+    if (m2 <= M) {
+      const V y2 = col[brev(m2, logK2)];
+      v2 = (c & 1) ? y2.x : -y2.y;
+    }
+    const int64_t nout = (A.reverse && n < N) ? N - 1 - n : n;
+    z[p * A.ld + nout] = mkv(v1 * scale, v2 * scale);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) dst_inverse_kernel(DstArgs A, int C) {
+  typedef Vt<T> V;
+  const V* z = (const V*)A.z;
+  const int64_t col0 = (int64_t)blockIdx.x * C;
+  const int64_t M = A.M, N = A.N;
+  const int64_t P = (M + 1) / 2;
+  if (A.space == 0) {
+    for (int64_t e = threadIdx.x; e < P * C; e += blockDim.x) {
+      const int64_t p = e / C;
+      const int c = (int)(e % C);
+      const int64_t n = col0 + c;
+      if (n >= N) continue;
+      const int64_t nin = A.reverse ? N - 1 - n : n;
+      const V zz = z[p * A.ld + nin];
+      for (int q = 0; q < 2; ++q) {
+        const int64_t j = 2 * p + q;
+        if (j >= M) continue;
+        const double v = (double)(q ? zz.y : zz.x);
+        double* dst = A.u + j * N + n;
+        *dst = A.accumulate ? *dst + v : v;
+      }
+    }
+    return;
+  }
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const int logK2 = A.logK2;
+  const int K2 = 1 << logK2, K = K2 >> 1;
+  const int lds = K2 + 1;
+  const int CP = C >> 1;
+  for (int cp = threadIdx.x; cp < CP; cp += blockDim.x) {
+    sm[cp * lds] = vzero<V>();
+    sm[cp * lds + K] = vzero<V>();
+  }
+  for (int64_t e = threadIdx.x; e < P * C; e += blockDim.x) {
+    const int64_t p = e / C;
+    const int c = (int)(e % C);
+    const int64_t n = col0 + c;
+    const int64_t nin = (A.reverse && n < N) ? N - 1 - n : n;
+    const V zz = z[p * A.ld + nin];
+    V* col = sm + (c >> 1) * lds;
+    const int m1 = (int)(2 * p + 1), m2 = m1 + 1;
+    if (c & 1) {
+      col[m1].y = zz.x;
+      col[K2 - m1].y = -zz.x;
+      if (m2 <= M) {
+        col[m2].y = zz.y;
+        col[K2 - m2].y = -zz.y;
+      }
+    } else {
+      col[m1].x = zz.x;
+      col[K2 - m1].x = -zz.x;
+      if (m2 <= M) {
+        col[m2].x = zz.y;
+        col[K2 - m2].x = -zz.y;
+      }
+    }
+  }
+  __syncthreads();
+  fft_dif<V>(sm, logK2, CP, lds, (const V*)A.tw, false);
+  const double scale = 1.0 / sqrt(2.0 * (double)K);
+  for (int64_t e = threadIdx.x; e < M * C; e += blockDim.x) {
+    const int64_t j = e / C;
+    const int c = (int)(e % C);
+    const int64_t n = col0 + c;
+    if (n >= N) continue;
+    const V y = sm[(c >> 1) * lds + brev((int)j + 1, logK2)];
+    const double v = (double)((c & 1) ? y.x : -y.y) * scale;
+    double* dst = A.u + j * N + n;
+    *dst = A.accumulate ? *dst + v : v;
+  }
+}
+
+template <typename T>
+int dst_cols(int logK2) {
+  // columns per block: as many as fit (even, <= 8) in ~160 KB of shared memory
+  const size_t per_pair = ((size_t)(1 << logK2) + 1) * sizeof(Vt<T>);
+  int C = 8;
+  while (C > 2 && (size_t)(C / 2) * per_pair > 160 * 1024) C >>= 1;
+  return C;
+}
+
+template <typename T>
+void dst_launch(const DstArgs& a, bool fwd, cudaStream_t st) {
+  int C = a.space ? dst_cols<T>(a.logK2) : 8;
+  size_t smem = a.space ? (size_t)(C / 2) * ((size_t)(1 << a.logK2) + 1) * sizeof(Vt<T>) : 0;
+  dim3 grid((unsigned)((a.ncols + C - 1) / C));
+  if (fwd) {
+    set_smem((const void*)dst_forward_kernel<T>, smem);
+    dst_forward_kernel<T><<<grid, kThreads, smem, st>>>(a, C);
+  } else {
+    set_smem((const void*)dst_inverse_kernel<T>, smem);
+    dst_inverse_kernel<T><<<grid, kThreads, smem, st>>>(a, C);
+  }
+}
+
+// ------------------------------------------------------------------ pack / unpack
+
+template <typename T>
+__global__ void pack_kernel(PackArgs A) {
+  typedef Vt<T> V;
+  const int64_t p = blockIdx.y;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= A.ld) return;
+  double v0 = 0.0, v1 = 0.0;
+  if (k < A.N) {
+    const int64_t src = A.reverse ? A.N - 1 - k : k;
+    v0 = A.x[(2 * p) * A.N + src];
+    if (2 * p + 1 < A.nlines) v1 = A.x[(2 * p + 1) * A.N + src];
+  }
+  ((V*)A.z)[p * A.ld + k] = mkv((T)v0, (T)v1);
+}
+
+template <typename T>
+__global__ void unpack_kernel(PackArgs A) {
+  typedef Vt<T> V;
+  const int64_t p = blockIdx.y;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= A.N) return;
+  const int64_t k = A.reverse ? A.N - 1 - n : n;
+  const V v = ((const V*)A.z)[p * A.ld + k];
+  double* y0 = A.y + (2 * p) * A.N + n;
+  *y0 = A.mode ? *y0 + (double)v.x : (double)v.x;
+  if (2 * p + 1 < A.nlines) {
+    double* y1 = A.y + (2 * p + 1) * A.N + n;
+    *y1 = A.mode ? *y1 + (double)v.y : (double)v.y;
+  }
+}
+
+// ------------------------------------------------------------------ residual, dot
+
+__global__ void residual_kernel(ResidualArgs A) {
+  const int64_t j = blockIdx.y;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= A.N) return;
+  const int64_t idx = j * A.N + n;
+  double v = A.f[idx];
+  if (A.u0) v += A.wu0[n] * A.u0[j];
+  if (A.phi) v += A.wphi[n] * A.phi[j];
+  const double2 t = A.tu[(j >> 1) * A.ld + n];
+  const double tv = (j & 1) ? t.y : t.x;
+  const double uj = A.u[idx];
+  double s;
+  if (A.space == 1) {
+    const double um = j > 0 ? A.u[idx - A.N] : 0.0;
+    const double up = j + 1 < A.M ? A.u[idx + A.N] : 0.0;
+    s = (2.0 * uj - um - up) * A.inv_h2;
+  } else {
+    s = A.lambda * uj;
+  }
+  A.r[idx] = v - tv - s;
+}
+
+__global__ void dot_kernel(DotArgs A) {
+  __shared__ double red[kThreads / 32];
+  double acc = 0.0;
+  const int64_t total = A.nlines * A.N;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t l = e / A.N, n = e % A.N;
+    const double2 t = A.tu[(l >> 1) * A.ld + n];
+    acc += A.x[e] * ((l & 1) ? t.y : t.x);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    A.partial[blockIdx.x] = s;
+  }
+}
+
+__global__ void sum_kernel(const double* partial, int n, double* out) {
+  __shared__ double red[kThreads / 32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partial[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    *out = s;
+  }
+}
+
+// ------------------------------------------------------------------ four-step split
+
+struct Split {
+  int logn, logn1, logn2;
+};
+inline Split split_of(int logn) { return Split{logn, logn / 2, logn - logn / 2}; }
+
+template <typename T>
+int four_step_cols(int logn1) {
+  const size_t per = ((size_t)(1 << logn1) + 1) * sizeof(Vt<T>);
+  int C = 8;
+  while (C > 1 && (size_t)C * per > 160 * 1024) C >>= 1;
+  return C;
+}
+
+// ------------------------------------------------------------------ spectra
+
+template <typename TS>
+__global__ void __launch_bounds__(kThreads) spec_smem_kernel(SpecArgs A) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double2* sm = reinterpret_cast<double2*>(smraw);
+  const int n = 1 << A.logn;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) sm[k] = make_double2((k >= A.lo && k < A.hi) ? A.a[k] : 0.0, 0.0);
+  __syncthreads();
+  fft_dif<double2>(sm, A.logn, 1, 0, A.tw64, false);
+  const double inv = 1.0 / (double)n;
+  typedef Vt<TS> V;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) ((V*)A.out)[k] = mkv((TS)(sm[k].x * inv), (TS)(sm[k].y * inv));
+}
+
+__global__ void __launch_bounds__(kThreads) spec_col_kernel(SpecArgs A, int logn1, int logn2, int C) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double2* sm = reinterpret_cast<double2*>(smraw);
+  const int n1 = 1 << logn1, n2 = 1 << logn2, n = n1 * n2;
+  const int lds = n1 + 1;
+  const int c0 = blockIdx.x * C;
+  for (int e = threadIdx.x; e < n1 * C; e += blockDim.x) {
+    const int j1 = e / C, c = e % C;
+    const int64_t k = (int64_t)j1 * n2 + c0 + c;
+    sm[c * lds + j1] = make_double2((k >= A.lo && k < A.hi) ? A.a[k] : 0.0, 0.0);
+  }
+  __syncthreads();
+  fft_dif<double2>(sm, logn1, C, lds, A.tw64, false);
+  const double2* twn = A.tw64 + (n - 2);
+  for (int e = threadIdx.x; e < n1 * C; e += blockDim.x) {
+    const int r = e / C, c = e % C;
+    const int j2 = c0 + c;
+    const int k1 = brev(r, logn1);
+    A.scratch64[(int64_t)r * n2 + j2] = cmul(sm[c * lds + r], twn[(int64_t)j2 * k1 & (n - 1)]);
+  }
+}
+
+template <typename TS>
+__global__ void __launch_bounds__(kThreads) spec_row_kernel(SpecArgs A, int logn1, int logn2) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double2* sm = reinterpret_cast<double2*>(smraw);
+  const int n2 = 1 << logn2;
+  const int64_t n = (int64_t)n2 << logn1;
+  const int r = blockIdx.x;
+  for (int k = threadIdx.x; k < n2; k += blockDim.x) sm[k] = A.scratch64[(int64_t)r * n2 + k];
+  __syncthreads();
+  fft_dif<double2>(sm, logn2, 1, 0, A.tw64, false);
+  const double inv = 1.0 / (double)n;
+  typedef Vt<TS> V;
+  for (int k = threadIdx.x; k < n2; k += blockDim.x)
+    ((V*)A.out)[(int64_t)r * n2 + k] = mkv((TS)(sm[k].x * inv), (TS)(sm[k].y * inv));
+}
+
+template <typename TS>
+void spectrum_launch(const SpecArgs& a, cudaStream_t st) {
+  const int n = 1 << a.logn;
+  if (n <= a.nsmem) {
+    size_t smem = (size_t)n * sizeof(double2);
+    set_smem((const void*)spec_smem_kernel<TS>, smem);
+    spec_smem_kernel<TS><<<1, kThreads, smem, st>>>(a);
+    return;
+  }
+  Split sp = split_of(a.logn);
+  int C = four_step_cols<double>(sp.logn1);
+  size_t smem = (size_t)C * ((size_t)(1 << sp.logn1) + 1) * sizeof(double2);
+  set_smem((const void*)spec_col_kernel, smem);
+  spec_col_kernel<<<(1 << sp.logn2) / C, kThreads, smem, st>>>(a, sp.logn1, sp.logn2, C);
+  size_t smem2 = (size_t)(1 << sp.logn2) * sizeof(double2);
+  set_smem((const void*)spec_row_kernel<TS>, smem2);
+  spec_row_kernel<TS><<<1 << sp.logn1, kThreads, smem2, st>>>(a, sp.logn1, sp.logn2);
+}
+
+// ------------------------------------------------------------------ convolution
+
+// One block per pair; the whole length-n transform in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) conv_smem_kernel(ConvArgs A) {
+  typedef Vt<T> V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const int n = 1 << A.logn, s = n >> 1;
+  const int64_t p = blockIdx.x;
+  const V* zin = (const V*)A.zin + p * A.ld_in + A.in_off;
+  for (int i = threadIdx.x; i < s; i += blockDim.x) sm[i] = zin[i];
+  __syncthreads();
+  const V* tw = (const V*)A.tw;
+  fft_dif<V>(sm, A.logn, 1, 0, tw, true);
+  const V* spec = (const V*)A.spec;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) sm[k] = cmul(sm[k], spec[k]);
+  __syncthreads();
+  fft_dit<V>(sm, A.logn, 1, 0, tw, A.mode == 0 ? 1 : 2);
+  V* zo = (V*)A.zout + p * A.ld_out + A.out_off;
+  if (A.mode == 0) {
+    for (int i = threadIdx.x; i < s; i += blockDim.x) zo[i] = csub(zo[i], sm[s + i]);
+  } else {
+    for (int i = threadIdx.x; i < s; i += blockDim.x) zo[i] = sm[i];
+  }
+}
+
+// Four-step: n = n1*n2, index j = j1*n2 + j2.  Step A transforms columns (over j1),
+// applies W_n^{j2 k1}; step B transforms rows (over j2), multiplies by the spectrum
+// (stored in the same order), inverts the rows and removes the twiddle; step C inverts
+// the columns.  Column transforms leave k1 in bit-reversed row order, which the
+// twiddles account for.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) conv_col_fwd_kernel(ConvArgs A, int logn1, int logn2, int C) {
+  typedef Vt<T> V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const int n1 = 1 << logn1, n2 = 1 << logn2, n = n1 * n2, h1 = n1 >> 1;
+  const int lds = n1 + 1;
+  const int c0 = blockIdx.x * C;
+  const int64_t p = blockIdx.y;
+  const V* zin = (const V*)A.zin + p * A.ld_in + A.in_off;
+  for (int e = threadIdx.x; e < h1 * C; e += blockDim.x) {
+    const int j1 = e / C, c = e % C;
+    sm[c * lds + j1] = zin[(int64_t)j1 * n2 + c0 + c];
+  }
+  __syncthreads();
+  const V* tw = (const V*)A.tw;
+  fft_dif<V>(sm, logn1, C, lds, tw, true);
+  const V* twn = tw + (n - 2);
+  V* sc = (V*)A.scratch + p * (int64_t)n;
+  for (int e = threadIdx.x; e < n1 * C; e += blockDim.x) {
+    const int r = e / C, c = e % C;
+    const int j2 = c0 + c;
+    const int k1 = brev(r, logn1);
+    sc[(int64_t)r * n2 + j2] = cmul(sm[c * lds + r], twn[(int64_t)j2 * k1 & (n - 1)]);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) conv_row_kernel(ConvArgs A, int logn1, int logn2) {
+  typedef Vt<T> V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const int n2 = 1 << logn2, n = n2 << logn1;
+  const int r = blockIdx.x;
+  const int64_t p = blockIdx.y;
+  V* sc = (V*)A.scratch + p * (int64_t)n + (int64_t)r * n2;
+  for (int k = threadIdx.x; k < n2; k += blockDim.x) sm[k] = sc[k];
+  __syncthreads();
+  const V* tw = (const V*)A.tw;
+  fft_dif<V>(sm, logn2, 1, 0, tw, false);
+  const V* spec = (const V*)A.spec + (int64_t)r * n2;
+  for (int k = threadIdx.x; k < n2; k += blockDim.x) sm[k] = cmul(sm[k], spec[k]);
+  __syncthreads();
+  fft_dit<V>(sm, logn2, 1, 0, tw, 0);
+  const V* twn = tw + (n - 2);
+  const int k1 = brev(r, logn1);
+  for (int j2 = threadIdx.x; j2 < n2; j2 += blockDim.x) sc[j2] = cmulc(sm[j2], twn[(int64_t)j2 * k1 & (n - 1)]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) conv_col_inv_kernel(ConvArgs A, int logn1, int logn2, int C) {
+  typedef Vt<T> V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const int n1 = 1 << logn1, n2 = 1 << logn2, n = n1 * n2, h1 = n1 >> 1;
+  const int lds = n1 + 1;
+  const int c0 = blockIdx.x * C;
+  const int64_t p = blockIdx.y;
+  const V* sc = (const V*)A.scratch + p * (int64_t)n;
+  for (int e = threadIdx.x; e < n1 * C; e += blockDim.x) {
+    const int r = e / C, c = e % C;
+    sm[c * lds + r] = sc[(int64_t)r * n2 + c0 + c];
+  }
+  __syncthreads();
+  fft_dit<V>(sm, logn1, C, lds, (const V*)A.tw, A.mode == 0 ? 1 : 2);
+  V* zo = (V*)A.zout + p * A.ld_out + A.out_off;
+  for (int e = threadIdx.x; e < h1 * C; e += blockDim.x) {
+    const int jj = e / C, c = e % C;
+    const int64_t o = (int64_t)jj * n2 + c0 + c;
+    if (A.mode == 0) {
+      zo[o] = csub(zo[o], sm[c * lds + h1 + jj]);
+    } else {
+      zo[o] = sm[c * lds + jj];
+    }
+  }
+}
+
+template <typename T>
+void conv_launch(const ConvArgs& a, cudaStream_t st) {
+  const int n = 1 << a.logn;
+  if (n <= a.nsmem) {
+    size_t smem = (size_t)n * sizeof(Vt<T>);
+    set_smem((const void*)conv_smem_kernel<T>, smem);
+    conv_smem_kernel<T><<<(unsigned)a.npairs, kThreads, smem, st>>>(a);
+    return;
+  }
+  Split sp = split_of(a.logn);
+  const int C = four_step_cols<T>(sp.logn1);
+  const size_t smc = (size_t)C * ((size_t)(1 << sp.logn1) + 1) * sizeof(Vt<T>);
+  const size_t smr = (size_t)(1 << sp.logn2) * sizeof(Vt<T>);
+  dim3 gc((unsigned)((1 << sp.logn2) / C), (unsigned)a.npairs);
+  dim3 gr((unsigned)(1 << sp.logn1), (unsigned)a.npairs);
+  set_smem((const void*)conv_col_fwd_kernel<T>, smc);
+  set_smem((const void*)conv_row_kernel<T>, smr);
+  set_smem((const void*)conv_col_inv_kernel<T>, smc);
+  conv_col_fwd_kernel<T><<<gc, kThreads, smc, st>>>(a, sp.logn1, sp.logn2, C);
+  conv_row_kernel<T><<<gr, kThreads, smr, st>>>(a, sp.logn1, sp.logn2);
+  conv_col_inv_kernel<T><<<gc, kThreads, smc, st>>>(a, sp.logn1, sp.logn2, C);
+}
+
+}  // namespace
+
+int nsmem_for(Prec prec) { return prec == P64 ? 4096 : 8192; }
+
+int launch_dst_forward(Prec prec, const DstArgs& a, cudaStream_t st) {
+  if (prec == P64) dst_launch<double>(a, true, st); else dst_launch<float>(a, true, st);
+  return 1;
+}
+int launch_dst_inverse(Prec prec, const DstArgs& a, cudaStream_t st) {
+  if (prec == P64) dst_launch<double>(a, false, st); else dst_launch<float>(a, false, st);
+  return 1;
+}
+
+int launch_pack(Prec prec, const PackArgs& a, cudaStream_t st) {
+  dim3 grid((unsigned)((a.ld + kThreads - 1) / kThreads), (unsigned)((a.nlines + 1) / 2));
+  if (prec == P64) pack_kernel<double><<<grid, kThreads, 0, st>>>(a);
+  else pack_kernel<float><<<grid, kThreads, 0, st>>>(a);
+  return 1;
+}
+int launch_unpack(Prec prec, const PackArgs& a, cudaStream_t st) {
+  dim3 grid((unsigned)((a.N + kThreads - 1) / kThreads), (unsigned)((a.nlines + 1) / 2));
+  if (prec == P64) unpack_kernel<double><<<grid, kThreads, 0, st>>>(a);
+  else unpack_kernel<float><<<grid, kThreads, 0, st>>>(a);
+  return 1;
+}
+
+int launch_residual(const ResidualArgs& a, cudaStream_t st) {
+  dim3 grid((unsigned)((a.N + kThreads - 1) / kThreads), (unsigned)a.M);
+  residual_kernel<<<grid, kThreads, 0, st>>>(a);
+  return 1;
+}
+
+int launch_dot(const DotArgs& a, cudaStream_t st) {
+  dot_kernel<<<a.nblocks, kThreads, 0, st>>>(a);
+  return 1;
+}
+int launch_sum(const double* partial, int n, double* out, cudaStream_t st) {
+  sum_kernel<<<1, kThreads, 0, st>>>(partial, n, out);
+  return 1;
+}
+
+int launch_spectrum(Prec prec, const SpecArgs& a, cudaStream_t st) {
+  if (prec == P64) spectrum_launch<double>(a, st); else spectrum_launch<float>(a, st);
+  return (1 << a.logn) <= a.nsmem ? 1 : 2;
+}
+
+int launch_conv(Prec prec, const ConvArgs& a, cudaStream_t st) {
+  if (prec == P64) conv_launch<double>(a, st); else conv_launch<float>(a, st);
+  return (1 << a.logn) <= a.nsmem ? 1 : 3;
+}
+
+}  // namespace ftoep

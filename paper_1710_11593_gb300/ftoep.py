@@ -1,0 +1,283 @@
+"""Python binding of libftoep (C ABI in include/ftoep.h).
+
+Argument marshalling only: every numerical step runs in the CUDA kernels of the
+library.  Arrays may be torch tensors (CUDA or CPU) or numpy arrays; their data
+pointers are handed to the library, which detects host vs device memory.  If the
+library has not been built, every entry point raises ``FtoepError`` -- there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libftoep.so")
+
+FTOEP_OK, FTOEP_EINVAL, FTOEP_ENOMEM, FTOEP_ECUDA, FTOEP_ETIMEOUT, FTOEP_EUNSUPPORTED = range(6)
+STATUS_NAMES = {0: "FTOEP_OK", 1: "FTOEP_EINVAL", 2: "FTOEP_ENOMEM", 3: "FTOEP_ECUDA", 4: "FTOEP_ETIMEOUT",
+                5: "FTOEP_EUNSUPPORTED"}
+L1_SUBDIFFUSION, L1_HYPERBOLIC = 0, 1
+SPACE_NONE, SPACE_DIRICHLET_LAPLACIAN = 0, 1
+FP64, MIXED = 0, 1
+
+EXPORTS = ("ftoep_create", "ftoep_weights", "ftoep_solve", "ftoep_matvec", "ftoep_adjoint", "ftoep_profile",
+           "ftoep_profile_read", "ftoep_sync", "ftoep_last_error", "ftoep_destroy")
+K_BLOCK_SOLVE, K_CONV_SMEM, K_CONV_FOURSTEP, K_SINE, K_OTHER = range(5)
+KERNEL_CLASSES = {K_BLOCK_SOLVE: "block_solve", K_CONV_SMEM: "conv_smem", K_CONV_FOURSTEP: "conv_fourstep",
+                  K_SINE: "sine", K_OTHER: "other"}
+
+
+class FtoepError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class ftoep_problem(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("space", ctypes.c_int), ("precision", ctypes.c_int),
+                ("gamma", ctypes.c_double), ("T", ctypes.c_double), ("L", ctypes.c_double),
+                ("lam", ctypes.c_double), ("N", ctypes.c_int64), ("M", ctypes.c_int64)]
+
+
+class ftoep_tuning(ctypes.Structure):
+    _fields_ = [("leaf", ctypes.c_int), ("fft_tile", ctypes.c_int), ("gemm_max_level", ctypes.c_int),
+                ("modes_per_cta", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libftoep.so (built by ``paper_1710_11593_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FtoepError(FTOEP_EUNSUPPORTED, f"{path} not found: build it with paper_1710_11593_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i64, ci, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
+    lib.ftoep_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ftoep_problem), ci,
+                                 ctypes.POINTER(ftoep_tuning), vp]
+    lib.ftoep_weights.argtypes = [vp, ci, dp, dp]
+    lib.ftoep_solve.argtypes = [vp, dp, dp, dp, dp]
+    lib.ftoep_matvec.argtypes = [vp, ci, dp, dp, i64, ci]
+    lib.ftoep_adjoint.argtypes = [vp, dp, dp, dp, dp]
+    lib.ftoep_profile.argtypes = [vp, ci]
+    lib.ftoep_profile_read.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
+                                       ctypes.POINTER(i64)]
+    lib.ftoep_sync.argtypes = [vp]
+    lib.ftoep_last_error.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+    lib.ftoep_destroy.argtypes = [vp]
+    for name in EXPORTS:
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(x) -> Optional[int]:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
+            raise FtoepError(FTOEP_EINVAL, "numpy arrays must be C-contiguous float64")
+        return x.ctypes.data
+    # torch tensor
+    import torch
+    if isinstance(x, torch.Tensor):
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise FtoepError(FTOEP_EINVAL, "tensors must be contiguous float64")
+        return x.data_ptr()
+    raise FtoepError(FTOEP_EINVAL, f"unsupported array type {type(x)}")
+
+
+def _numel(x) -> int:
+    return int(x.size) if isinstance(x, np.ndarray) else int(x.numel())
+
+
+def _last_error(plan_handle) -> str:
+    buf = ctypes.create_string_buffer(512)
+    load().ftoep_last_error(plan_handle, buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def _check(rc: int, plan_handle=None):
+    if rc != FTOEP_OK:
+        raise FtoepError(rc, _last_error(plan_handle))
+
+
+def current_stream_handle() -> int:
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return 0
+
+
+@dataclass
+class ProblemSpec:
+    kind: int
+    gamma: float
+    N: int
+    M: int
+    space: int = SPACE_DIRICHLET_LAPLACIAN
+    precision: int = FP64
+    T: float = 1.0
+    L: float = 1.0
+    lam: float = 1.0
+
+    def to_c(self) -> ftoep_problem:
+        return ftoep_problem(self.kind, self.space, self.precision, self.gamma, self.T, self.L, self.lam,
+                             self.N, self.M)
+
+
+def ftoep_create(problems: Sequence[ProblemSpec], tuning: Optional[dict] = None, stream: Optional[int] = None):
+    """Create a plan (returns the opaque handle as an int)."""
+    lib = load()
+    arr = (ftoep_problem * len(problems))(*[p.to_c() for p in problems])
+    tp = None
+    if tuning:
+        tp = ctypes.pointer(ftoep_tuning(int(tuning.get("leaf", 0)), int(tuning.get("fft_tile", 0)),
+                                         int(tuning.get("gemm_max_level", 0)), int(tuning.get("modes_per_cta", 0))))
+    h = ctypes.c_void_p()
+    st = current_stream_handle() if stream is None else stream
+    rc = lib.ftoep_create(ctypes.byref(h), arr, len(problems), tp, ctypes.c_void_p(st))
+    _check(rc, None)
+    return h.value
+
+
+def ftoep_weights(plan: int, iprob: int, a, dadgamma=None):
+    _check(load().ftoep_weights(plan, iprob, _ptr(a), _ptr(dadgamma)), plan)
+
+
+def ftoep_solve(plan: int, f, u, u0=None, phi=None):
+    _check(load().ftoep_solve(plan, _ptr(f), _ptr(u), _ptr(u0), _ptr(phi)), plan)
+
+
+def ftoep_matvec(plan: int, iprob: int, x, y, nlines: int, transpose: bool = False):
+    _check(load().ftoep_matvec(plan, iprob, _ptr(x), _ptr(y), int(nlines), int(bool(transpose))), plan)
+
+
+def ftoep_adjoint(plan: int, g, u, dldf, dldgamma=None):
+    _check(load().ftoep_adjoint(plan, _ptr(g), _ptr(u), _ptr(dldf), _ptr(dldgamma)), plan)
+
+
+def ftoep_profile(plan: int, enable: bool):
+    _check(load().ftoep_profile(plan, int(bool(enable))), plan)
+
+
+def ftoep_profile_read(plan: int, kclass: int):
+    ms = ctypes.c_double()
+    ops = ctypes.c_int64()
+    nl = ctypes.c_int64()
+    _check(load().ftoep_profile_read(plan, kclass, ctypes.byref(ms), ctypes.byref(ops), ctypes.byref(nl)), plan)
+    return ms.value, ops.value, nl.value
+
+
+def ftoep_sync(plan: int):
+    _check(load().ftoep_sync(plan), plan)
+
+
+def ftoep_destroy(plan: int):
+    load().ftoep_destroy(plan)
+
+
+class Plan:
+    """Owning wrapper of an ftoep plan."""
+
+    def __init__(self, problems: Sequence[ProblemSpec], tuning: Optional[dict] = None, stream: Optional[int] = None):
+        self.problems = list(problems)
+        self.handle = ftoep_create(self.problems, tuning, stream)
+        self.total_field = sum(p.M * p.N for p in self.problems)
+        self.total_vec = sum(p.M for p in self.problems)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ftoep_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def weights(self, iprob: int = 0, with_dgamma: bool = False):
+        N = self.problems[iprob].N
+        a = np.empty(N)
+        d = np.empty(N) if with_dgamma else None
+        ftoep_weights(self.handle, iprob, a, d)
+        return (a, d) if with_dgamma else a
+
+    def solve(self, f, u=None, u0=None, phi=None):
+        if _numel(f) != self.total_field:
+            raise FtoepError(FTOEP_EINVAL, f"f has {_numel(f)} elements, plan expects {self.total_field}")
+        if u is None:
+            if isinstance(f, np.ndarray):
+                u = np.empty_like(f)
+            else:
+                import torch
+                u = torch.empty_like(f)
+        ftoep_solve(self.handle, f, u, u0, phi)
+        return u
+
+    def matvec(self, iprob: int, x, y=None, transpose: bool = False):
+        N = self.problems[iprob].N
+        n = _numel(x)
+        if n % N:
+            raise FtoepError(FTOEP_EINVAL, "x is not a whole number of lines")
+        if y is None:
+            if isinstance(x, np.ndarray):
+                y = np.empty_like(x)
+            else:
+                import torch
+                y = torch.empty_like(x)
+        ftoep_matvec(self.handle, iprob, x, y, n // N, transpose)
+        return y
+
+    def adjoint(self, g, u=None, dldf=None, want_gamma: bool = True):
+        if dldf is None:
+            if isinstance(g, np.ndarray):
+                dldf = np.empty_like(g)
+            else:
+                import torch
+                dldf = torch.empty_like(g)
+        dg = np.empty(len(self.problems)) if want_gamma else None
+        ftoep_adjoint(self.handle, g, u, dldf, dg)
+        return dldf, dg
+
+    def sync(self):
+        ftoep_sync(self.handle)
+
+    def profile(self, enable: bool = True):
+        ftoep_profile(self.handle, enable)
+
+    def profile_read(self):
+        """{class name: (event ms, timed operations, kernels launched)} since profile()."""
+        return {name: ftoep_profile_read(self.handle, k) for k, name in KERNEL_CLASSES.items()}
+
+
+def solve(f, gamma: float, kind: Optional[int] = None, precision: int = FP64, space: int = SPACE_DIRICHLET_LAPLACIAN,
+          T: float = 1.0, L: float = 1.0, lam: float = 1.0, u0=None, phi=None, tuning: Optional[dict] = None):
+    """One-shot solve of a single problem; f has shape [M, N] (time contiguous)."""
+    if kind is None:
+        kind = L1_SUBDIFFUSION if gamma < 1.0 else L1_HYPERBOLIC
+    M, N = (1, f.shape[0]) if len(f.shape) == 1 else (f.shape[0], f.shape[1])
+    with Plan([ProblemSpec(kind, gamma, N, M, space, precision, T, L, lam)], tuning) as p:
+        u = p.solve(f, u0=u0, phi=phi)
+        p.sync()
+    return u
