@@ -158,6 +158,24 @@ typedef enum {
 ftoep_status ftoep_profile(ftoep_plan p, int enable);
 ftoep_status ftoep_profile_read(ftoep_plan p, int kclass, double* total_ms, int64_t* ops, int64_t* launches);
 
+/* Plan-free, allocation-free variant of ftoep_matvec (the paper has no counterpart:
+ * it exists for callers that cannot allocate device memory -- code running after its
+ * memory budget is frozen by a host framework's caching allocator, plugins that may not
+ * allocate, loops where cudaMalloc's blocking and device synchronisation are not
+ * acceptable).  y = T x (transpose = 0) or T^T x (transpose = 1) for nlines lines of
+ * length N, T lower-triangular Toeplitz with first column a (N doubles, e.g. from
+ * ftoep_weights).  a, x, y: device pointers, [nlines][N]; x and y may not overlap.
+ * Work is ordered on cuda_stream (a cudaStream_t, NULL = legacy default stream).
+ * All intermediates live in one static device array of 16.8 MB compiled into the
+ * library (held on every GPU that loads it until the process exits); hence N <= 32768,
+ * larger N returns FTOEP_EINVAL.  Nothing is allocated or freed, ever.  The first call
+ * on a device (with that device current) looks up the array's address and writes its
+ * twiddle tables, synchronising the device once: make that first call before any stream
+ * capture.  Calls share the array, so calls whose GPU work overlaps in time race and must
+ * not be issued.  Messages for failures: ftoep_last_error(NULL, ...). */
+ftoep_status ftoep_matvec_noalloc(const double* a, int64_t N, const double* x, double* y, int64_t nlines,
+                                  int transpose, void* cuda_stream);
+
 /* Wait for the plan's stream; returns FTOEP_ETIMEOUT if a device-side wait gave up,
  * FTOEP_ECUDA on an asynchronous CUDA error. */
 ftoep_status ftoep_sync(ftoep_plan p);

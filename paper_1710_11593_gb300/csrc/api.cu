@@ -63,6 +63,11 @@ thread_local std::string g_create_error;
 
 }  // namespace
 
+namespace ftoep {
+// Message for ftoep_last_error(NULL, ...) from entry points that have no plan.
+void set_global_error(const char* msg) { g_create_error = msg; }
+}  // namespace ftoep
+
 struct ftoep_plan_s {
   std::vector<Prob> probs;
   cudaStream_t stream = nullptr;

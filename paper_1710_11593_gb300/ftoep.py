@@ -182,6 +182,17 @@ def ftoep_profile_read(plan: int, kclass: int):
     return ms.value, ops.value, nl.value
 
 
+def ftoep_matvec_noalloc(a, N: int, x, y, nlines: int, transpose: bool = False, stream: Optional[int] = None):
+    """Allocation-free Toeplitz product (device pointers only, N <= 32768); see ftoep.h."""
+    lib = load()
+    fn = lib.ftoep_matvec_noalloc
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                   ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    st = current_stream_handle() if stream is None else stream
+    _check(fn(_ptr(a), int(N), _ptr(x), _ptr(y), int(nlines), int(bool(transpose)), ctypes.c_void_p(st)), None)
+
+
 def ftoep_sync(plan: int):
     _check(load().ftoep_sync(plan), plan)
 
