@@ -93,7 +93,7 @@ typedef struct {
 } ftoep_problem;
 
 /* Optional tuning (NULL or 0 fields = library choice).
- * leaf: size of the dense forward-substitution leaves (power of two, 1..32).
+ * leaf: size of the dense forward-substitution leaves (power of two, 1..16).
  * fft_tile: largest time block solved inside one thread block (power of two).
  * gemm_max_level: largest half-split level handled by direct (dense) block products
  *   instead of FFTs.

@@ -221,8 +221,8 @@ ftoep_status validate(const ftoep_problem& d, int i, const ftoep_tuning* tune) {
     if (d.M + 1 > lim) return fail(pl, FTOEP_EUNSUPPORTED, "problem %d: M+1 > %lld not supported", i, (long long)lim);
   }
   if (tune) {
-    if (tune->leaf && (!is_pow2(tune->leaf) || tune->leaf > 32))
-      return fail(pl, FTOEP_EINVAL, "tuning: leaf must be a power of two <= 32");
+    if (tune->leaf && (!is_pow2(tune->leaf) || tune->leaf > 16))
+      return fail(pl, FTOEP_EINVAL, "tuning: leaf must be a power of two <= 16");
     if (tune->fft_tile && (!is_pow2(tune->fft_tile) || tune->fft_tile > 4096 || tune->fft_tile < 16))
       return fail(pl, FTOEP_EINVAL, "tuning: fft_tile must be a power of two in [16, 4096]");
     if (tune->gemm_max_level && (!is_pow2(tune->gemm_max_level) || tune->gemm_max_level > 2048))

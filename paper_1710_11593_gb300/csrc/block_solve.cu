@@ -23,30 +23,30 @@ constexpr int kThreads = 256;
 template <typename T>
 using Vt = typename VecOf<T>::type;
 
-// One warp: lane i < L owns row i of both components (mode 2p in .x, 2p+1 in .y).
+// Leaf forward substitution in double precision, one warp, unit-diagonal form: with
+// d_c = a_0 + lambda of component c (c = 0: mode 2p in .x, c = 1: mode 2p+1 in .y),
+//     x_k = y'_k,   y'_i -= (a_{i-k}/d_c) x_k  (i > k),   y' = y/d_c,
+// so each of the L steps is one shuffle and one FMA.  Lane l = c*L + i (i < L <= 16)
+// owns row i of component c; asc[c*L + j] = a_j/d_c.
 template <typename T>
-__device__ __forceinline__ void leaf_solve(Vt<T>* zb, int L, const double* as, double2 inv) {
+__device__ __forceinline__ void leaf_solve(Vt<T>* zb, int L, const double* asc, double2 inv) {
   const int lane = threadIdx.x;
-  double yr = 0.0, yi = 0.0;
-  if (lane < L) {
-    const Vt<T> z = zb[lane];
-    yr = (double)z.x;
-    yi = (double)z.y;
+  const int c = lane >= L ? 1 : 0;
+  const int i = lane - c * L;
+  const bool act = lane < 2 * L;
+  double y = 0.0;
+  if (act) {
+    const Vt<T> z = zb[i];
+    y = c ? (double)z.y * inv.y : (double)z.x * inv.x;
   }
-  double xr = 0.0, xi = 0.0;
+  const double* ac = asc + c * L;
   for (int k = 0; k < L; ++k) {
-    const double cr = __shfl_sync(0xffffffffu, yr * inv.x, k);
-    const double ci = __shfl_sync(0xffffffffu, yi * inv.y, k);
-    if (lane == k) {
-      xr = cr;
-      xi = ci;
-    } else if (lane > k && lane < L) {
-      const double ak = as[lane - k];
-      yr = fma(-ak, cr, yr);
-      yi = fma(-ak, ci, yi);
-    }
+    const double xk = __shfl_sync(0xffffffffu, y, c * L + k);
+    if (act && i > k) y = fma(-ac[i - k], xk, y);
   }
-  if (lane < L) zb[lane] = mkv((T)xr, (T)xi);
+  if (act) {
+    if (c) zb[i].y = (T)y; else zb[i].x = (T)y;
+  }
 }
 
 // y[mid + i] -= sum_{k<s} a_{s+i-k} x[mid - s + k], both components, direct sums.
@@ -99,23 +99,24 @@ __global__ void __launch_bounds__(kThreads) block_solve_kernel(BlockArgs A) {
   const int B = A.B, L = A.L, Sf = A.Sf;
   V* zb = reinterpret_cast<V*>(smraw);
   V* fb = zb + B;
-  double* as = reinterpret_cast<double*>(fb + B);
   const int nat = (2 * Sf < B) ? 2 * Sf : B;  // a_k needed by the dense levels: k < 2s <= 2*Sf
-  T* at = reinterpret_cast<T*>(as + B);
+  double* asc = reinterpret_cast<double*>(fb + B);  // 2L scaled leaf coefficients
+  T* at = reinterpret_cast<T*>(asc + 32);
   const int64_t p = blockIdx.x;
   V* zg = (V*)A.z + p * A.ld + A.t0;
-  for (int i = threadIdx.x; i < B; i += blockDim.x) {
-    zb[i] = zg[i];
-    as[i] = A.a[i];
-  }
+  for (int i = threadIdx.x; i < B; i += blockDim.x) zb[i] = zg[i];
   for (int i = threadIdx.x; i < nat; i += blockDim.x) at[i] = (T)A.a[i];
   const double2 inv = A.invdiag[p];
+  for (int i = threadIdx.x; i < 2 * L; i += blockDim.x) {
+    const int j = i % L;
+    asc[i] = j == 0 ? 0.0 : A.a[j] * (i < L ? inv.x : inv.y);
+  }
   const V* spec = (const V*)A.spec;
   const V* tw = (const V*)A.tw;
   __syncthreads();
   const int nleaf = B / L;
   for (int b = 0; b < nleaf; ++b) {
-    if (threadIdx.x < 32) leaf_solve<T>(zb + b * L, L, as, inv);
+    if (threadIdx.x < 32) leaf_solve<T>(zb + b * L, L, asc, inv);
     __syncthreads();
     const int v = b + 1;
     if (v < nleaf) {
@@ -133,13 +134,14 @@ __global__ void __launch_bounds__(kThreads) block_solve_kernel(BlockArgs A) {
 }
 
 template <typename T>
-size_t smem_bytes(int B) {
-  return (size_t)B * 2 * sizeof(Vt<T>) + (size_t)B * sizeof(double) + (size_t)B * sizeof(T);
+size_t smem_bytes(int B, int Sf) {
+  const int nat = (2 * Sf < B) ? 2 * Sf : B;
+  return (size_t)B * 2 * sizeof(Vt<T>) + 32 * sizeof(double) + (size_t)nat * sizeof(T);
 }
 
 template <typename T>
 void launch(const BlockArgs& a, cudaStream_t st) {
-  const size_t smem = smem_bytes<T>(a.B);
+  const size_t smem = smem_bytes<T>(a.B, a.Sf);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute((const void*)block_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   block_solve_kernel<T><<<(unsigned)a.npairs, kThreads, smem, st>>>(a);
@@ -147,7 +149,9 @@ void launch(const BlockArgs& a, cudaStream_t st) {
 
 }  // namespace
 
-size_t block_solve_smem(Prec prec, int B) { return prec == P64 ? smem_bytes<double>(B) : smem_bytes<float>(B); }
+size_t block_solve_smem(Prec prec, int B, int Sf) {
+  return prec == P64 ? smem_bytes<double>(B, Sf) : smem_bytes<float>(B, Sf);
+}
 
 int launch_block_solve(Prec prec, const BlockArgs& a, cudaStream_t st) {
   if (prec == P64) launch<double>(a, st); else launch<float>(a, st);

@@ -122,7 +122,7 @@ struct BlockArgs {
   int64_t npairs;
   int64_t t0;
   int B;            // block length (power of two)
-  int L;            // leaf length (power of two <= 32, <= B)
+  int L;            // leaf length (power of two <= 16, <= B)
   int Sf;           // first FFT level (levels L <= s < Sf are dense products)
   const double* a;  // a[0..B)
   const double2* invdiag;  // per pair: 1/(a0+lambda) of its two modes
@@ -130,7 +130,7 @@ struct BlockArgs {
   const void* tw;
 };
 int launch_block_solve(Prec prec, const BlockArgs& a, cudaStream_t st);
-size_t block_solve_smem(Prec prec, int B);
+size_t block_solve_smem(Prec prec, int B, int Sf);
 
 // Largest shared-memory FFT length of each precision.
 int nsmem_for(Prec prec);
