@@ -18,7 +18,8 @@
  *         (mu*G_0 + 2/h^2) u_j^n - (u_{j-1}^n + u_{j+1}^n)/h^2
  *             = f_j^n + mu*[ sum_{k=1}^{n-1} (G_{n-k-1} - G_{n-k}) u_j^k + G_{n-1} u_j^0 ]
  *     (mu = tau^-g / Gamma(2-g); the u^0 coefficient follows from expanding the L1
- *     quotient, see the header of march_step()).
+ *     quotient, see or_initial_weights()).  The history sum is plain double; the
+ *     tridiagonal level solve is done in binary128 (see thomas_const()).
  *   - The hyperbolic L1 scheme of Eq. 15 / Eq. 17 (1<g<2, c = tau^-g/Gamma(3-g)) with
  *     the advection term replaced by the central second difference, spatial term at
  *     level n and f at t_{n-1/2}:
@@ -173,17 +174,21 @@ int or_initial_weights(int kind, double g, double tau, int64_t N, double* w_u0, 
 }
 
 /* Thomas algorithm for the constant tridiagonal system
- *   diag*x_j + off*(x_{j-1} + x_{j+1}) = r_j,  j = 0..M-1, x_{-1} = x_M = 0.
- * cp is scratch of length M.  Overwrites r with x. */
-static void thomas_const(int64_t M, double diag, double off, double* r, double* cp) {
+ *   diag*x_j + off*(x_{j-1} + x_{j+1}) = r_j,  j = 0..M-1, x_{-1} = x_M = 0,
+ * carried out in binary128 (r and x rounded to double on the way in and out).  With
+ * diag ~ 2/h^2 >> mu the matrix has condition ~ (mu + 4/h^2)/(mu + pi^2), e.g. 1.6e3 at
+ * h = 1/1024, mu = 2.6e3: a double sweep loses that factor times eps at every level.
+ * cp, rq: scratch of length M.  Overwrites r with x. */
+static void thomas_const(int64_t M, qreal diag, qreal off, double* r, qreal* cp, qreal* rq) {
   cp[0] = off / diag;
-  r[0] = r[0] / diag;
+  rq[0] = (qreal)r[0] / diag;
   for (int64_t j = 1; j < M; ++j) {
-    double den = diag - off * cp[j - 1];
+    qreal den = diag - off * cp[j - 1];
     cp[j] = off / den;
-    r[j] = (r[j] - off * r[j - 1]) / den;
+    rq[j] = ((qreal)r[j] - off * rq[j - 1]) / den;
   }
-  for (int64_t j = M - 2; j >= 0; --j) r[j] -= cp[j] * r[j + 1];
+  for (int64_t j = M - 2; j >= 0; --j) rq[j] -= cp[j] * rq[j + 1];
+  for (int64_t j = 0; j < M; ++j) r[j] = (double)rq[j];
 }
 
 /*
@@ -205,23 +210,26 @@ int or_march(int kind, int space, double g, double T, double Lx, double lambda, 
   double* wu0 = (double*)malloc(sizeof(double) * (size_t)N);
   double* wphi = (double*)malloc(sizeof(double) * (size_t)N);
   double* rhs = (double*)malloc(sizeof(double) * (size_t)M);
-  double* cp = (double*)malloc(sizeof(double) * (size_t)M);
-  if (!coef || !wu0 || !wphi || !rhs || !cp) {
-    free(coef); free(wu0); free(wphi); free(rhs); free(cp);
+  qreal* cp = (qreal*)malloc(sizeof(qreal) * (size_t)M);
+  qreal* rq = (qreal*)malloc(sizeof(qreal) * (size_t)M);
+  if (!coef || !wu0 || !wphi || !rhs || !cp || !rq) {
+    free(coef); free(wu0); free(wphi); free(rhs); free(cp); free(rq);
     return OR_ENOMEM;
   }
   or_time_coeffs(kind, g, N, coef);
   or_initial_weights(kind, g, tau, N, wu0, wphi);
   /* history weights h_j = -scale*coef_j for j >= 1: the right-hand side collects
-   * sum_{k=1}^{n-1} h_{n-k} u^k, which for kind 0 is mu*(G_{n-k-1} - G_{n-k}). */
-  double h = 0.0, diag, off;
+   * sum_{k=1}^{n-1} h_{n-k} u^k, which for kind 0 is mu*(G_{n-k-1} - G_{n-k}).
+   * The level matrix is formed in binary128 from the binary128 scale. */
+  qreal diag, off;
+  const qreal qscale = q_scale(kind, (qreal)g, (qreal)tau) * q_coef(kind, 0, (qreal)g);
   if (space == 1) {
-    h = Lx / (double)(M + 1);
-    diag = scale * coef[0] + 2.0 / (h * h);
-    off = -1.0 / (h * h);
+    qreal h = (qreal)Lx / (qreal)(M + 1);
+    diag = qscale + QLIT(2.0) / (h * h);
+    off = QLIT(-1.0) / (h * h);
   } else {
-    diag = scale * coef[0] + lambda;
-    off = 0.0;
+    diag = qscale + (qreal)lambda;
+    off = QLIT(0.0);
   }
   if (nthreads < 1) nthreads = 1;
   for (int64_t n = 1; n <= N; ++n) {
@@ -236,13 +244,13 @@ int or_march(int kind, int space, double g, double T, double Lx, double lambda, 
       rhs[j] = r;
     }
     if (space == 1) {
-      thomas_const(M, diag, off, rhs, cp);
+      thomas_const(M, diag, off, rhs, cp, rq);
     } else {
-      for (int64_t j = 0; j < M; ++j) rhs[j] /= diag;
+      for (int64_t j = 0; j < M; ++j) rhs[j] = (double)((qreal)rhs[j] / diag);
     }
     for (int64_t j = 0; j < M; ++j) u[j * N + (n - 1)] = rhs[j];
   }
-  free(coef); free(wu0); free(wphi); free(rhs); free(cp);
+  free(coef); free(wu0); free(wphi); free(rhs); free(cp); free(rq);
   return OR_OK;
 }
 
@@ -260,20 +268,22 @@ int or_adjoint_march(int kind, int space, double g, double T, double Lx, double 
   const double scale = or_scale(kind, g, tau);
   double* coef = (double*)malloc(sizeof(double) * (size_t)N);
   double* rhs = (double*)malloc(sizeof(double) * (size_t)M);
-  double* cp = (double*)malloc(sizeof(double) * (size_t)M);
-  if (!coef || !rhs || !cp) {
-    free(coef); free(rhs); free(cp);
+  qreal* cp = (qreal*)malloc(sizeof(qreal) * (size_t)M);
+  qreal* rq = (qreal*)malloc(sizeof(qreal) * (size_t)M);
+  if (!coef || !rhs || !cp || !rq) {
+    free(coef); free(rhs); free(cp); free(rq);
     return OR_ENOMEM;
   }
   or_time_coeffs(kind, g, N, coef);
-  double diag, off;
+  qreal diag, off;
+  const qreal qscale = q_scale(kind, (qreal)g, (qreal)tau) * q_coef(kind, 0, (qreal)g);
   if (space == 1) {
-    double h = Lx / (double)(M + 1);
-    diag = scale * coef[0] + 2.0 / (h * h);
-    off = -1.0 / (h * h);
+    qreal h = (qreal)Lx / (qreal)(M + 1);
+    diag = qscale + QLIT(2.0) / (h * h);
+    off = QLIT(-1.0) / (h * h);
   } else {
-    diag = scale * coef[0] + lambda;
-    off = 0.0;
+    diag = qscale + (qreal)lambda;
+    off = QLIT(0.0);
   }
   if (nthreads < 1) nthreads = 1;
   for (int64_t n = N; n >= 1; --n) {
@@ -285,13 +295,13 @@ int or_adjoint_march(int kind, int space, double g, double T, double Lx, double 
       rhs[j] = gin[j * N + (n - 1)] - scale * s;
     }
     if (space == 1) {
-      thomas_const(M, diag, off, rhs, cp);
+      thomas_const(M, diag, off, rhs, cp, rq);
     } else {
-      for (int64_t j = 0; j < M; ++j) rhs[j] /= diag;
+      for (int64_t j = 0; j < M; ++j) rhs[j] = (double)((qreal)rhs[j] / diag);
     }
     for (int64_t j = 0; j < M; ++j) lam[j * N + (n - 1)] = rhs[j];
   }
-  free(coef); free(rhs); free(cp);
+  free(coef); free(rhs); free(cp); free(rq);
   return OR_OK;
 }
 
