@@ -23,8 +23,13 @@
  * "U_i = (U_i^1, ..., U_i^N)"), the time operator is lower-triangular Toeplitz with
  * first column a (Sec. 3, the block A-hat).  The library diagonalises the spatial
  * operator with an orthonormal sine transform (eigenvalues
- * lambda_m = (4/h^2) sin^2(m pi/(2(M+1)))), so each mode solves a lower-triangular
- * Toeplitz system (lambda_m I + T) u_m = r_m exactly (a direct solve, not an iteration).
+ * lambda_m = (4/h^2) sin^2(m pi/(2(M+1)))), so each mode solves (lambda_m I + T) u_m = r_m
+ * exactly (a direct solve, not an iteration).  Internally the rows are solved for the
+ * difference quotients v^n = (u^n - u^{n-1})/tau, the variables in which Eq. 4 and Eq. 15
+ * are written: per mode the operator becomes E + lambda_m tau 1 (E lower-triangular
+ * Toeplitz with first column scale*tau*G_j, resp. scale*tau*(M_j - M_{j-1}); 1 the
+ * all-ones lower triangle), and u = u0 + tau * cumsum(v).  Same equations, same
+ * solution; the history terms carry tau^(1-g) instead of tau^-g.
  *
  * Field layout (all field arguments): [M][N] row-major, double precision, time index
  * contiguous; element (j-1, n-1) is the value at x_j and time level n (t_n for the

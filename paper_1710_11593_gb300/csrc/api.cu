@@ -33,11 +33,13 @@ struct Prob {
   Prec prec = P64;
   int64_t foff = 0, voff = 0;
   std::vector<double> h_a, h_dadg;
-  double* a = nullptr;
-  double* dadg = nullptr;
+  double* a = nullptr;          // first column of the time operator (original form)
+  double* dadg = nullptr;       // its derivative in gamma
+  double* e = nullptr;          // first column in the difference form (solve kernel)
   double* wu0 = nullptr;
   double* wphi = nullptr;
-  double2* invdiag = nullptr;
+  double2* invdiag = nullptr;   // per pair 1/(e_0 + lambda tau)
+  double2* lamtau = nullptr;    // per pair lambda tau
   void* spec = nullptr;         // solve spectra, precision prec
   double2* spec64 = nullptr;    // solve spectra in double (adjoint of mixed problems; == spec for P64)
   double2* spec_mv = nullptr;   // product spectrum, length 2Np
@@ -80,7 +82,9 @@ struct ftoep_plan_s {
   void* scratch = nullptr;      // four-step scratch of the solve (max P*Np of double2)
   double2* zmv = nullptr;       // product pairs (max P*Np double2)
   double2* scratch_mv = nullptr;// four-step scratch of products (max P*2Np double2)
-  double* r = nullptr;          // residual field (max M*N)
+  double* r = nullptr;          // residual / temporary field (max M*N)
+  double2* prefix = nullptr;    // running sums of the difference-form solve (max P)
+  size_t prefix_elems = 0;
   double* dpart = nullptr;      // reduction partials
   double* dscal = nullptr;      // device scalars (nprob)
   size_t z_elems = 0, mv_elems = 0, r_elems = 0;
@@ -235,7 +239,7 @@ ftoep_status validate(const ftoep_problem& d, int i, const ftoep_tuning* tune) {
 ftoep_status build_solve_spectra(ftoep_plan pl, Prob& pb, Prec pr, void* out) {
   for (int64_t s = pb.Sf; s <= pb.Np / 2; s <<= 1) {
     SpecArgs sa{};
-    sa.a = pb.a;
+    sa.a = pb.e;
     sa.lo = 1;
     sa.hi = 2 * s;
     sa.logn = ilog2(2 * s);
@@ -268,6 +272,7 @@ ftoep_status build_product_spectrum(ftoep_plan pl, Prob& pb, const double* coeff
 // In-place solve of the pair array z (right-hand side in, solution out).
 ftoep_status solve_pairs(ftoep_plan pl, Prob& pb, Prec pr, void* z, const void* spec) {
   cudaStream_t st = pl->stream;
+  CK(cudaMemsetAsync(pl->prefix, 0, (size_t)pb.P * sizeof(double2), st));
   for (int b = 0; b < pb.nblk; ++b) {
     BlockArgs ba{};
     ba.z = z;
@@ -277,8 +282,10 @@ ftoep_status solve_pairs(ftoep_plan pl, Prob& pb, Prec pr, void* z, const void* 
     ba.B = pb.B;
     ba.L = pb.L;
     ba.Sf = pb.Sf;
-    ba.a = pb.a;
+    ba.a = pb.e;
     ba.invdiag = pb.invdiag;
+    ba.lamtau = pb.lamtau;
+    ba.prefix = pl->prefix;
     ba.spec = spec;
     ba.tw = tw_of(pl, pr);
     LAUNCH(FTOEP_K_BLOCK_SOLVE, launch_block_solve(pr, ba, st));
@@ -314,6 +321,8 @@ DstArgs dst_args(ftoep_plan pl, Prob& pb, Prec pr, void* z) {
   da.M = pb.M;
   da.logK2 = pb.logK2;
   da.space = pb.d.space;
+  da.inv_h2 = 1.0 / (pb.h * pb.h);
+  da.lambda = pb.d.lambda;
   da.tw = tw_of(pl, pr);
   return da;
 }
@@ -351,6 +360,27 @@ ftoep_status product_lines(ftoep_plan pl, Prob& pb, const double2* spec, const d
   return FTOEP_OK;
 }
 
+// Scan of the solved difference quotients into u (u = u0 + tau * cumsum(v)).
+ftoep_status scan_lines(ftoep_plan pl, Prob& pb, const double* in, double* out, const double* u0, int accumulate,
+                        int reverse) {
+  ScanArgs sc{};
+  sc.in = in;
+  sc.out = out;
+  sc.u0 = u0;
+  sc.N = pb.N;
+  sc.M = pb.M;
+  sc.tau = pb.tau;
+  sc.accumulate = accumulate;
+  sc.reverse = reverse;
+  LAUNCH(FTOEP_K_OTHER, launch_scan(sc, pl->stream));
+  return FTOEP_OK;
+}
+
+// The solve runs on the difference quotients v_n = (u^n - u^{n-1})/tau: per mode the
+// operator is E + lambda_m tau 1 (E lower-triangular Toeplitz, shared; 1 the all-ones
+// lower triangle) with right-hand side f + [c tau M_{n-1} phi] - S u0, and
+// u = u0 + tau cumsum(v).  Written in v the history terms carry the scale tau^(1-g)
+// instead of tau^-g, which keeps float arithmetic usable at large N.
 ftoep_status solve_problem(ftoep_plan pl, Prob& pb, const double* f, double* u, const double* u0, const double* phi) {
   cudaStream_t st = pl->stream;
   const Prec pr = pb.prec;
@@ -360,13 +390,15 @@ ftoep_status solve_problem(ftoep_plan pl, Prob& pb, const double* f, double* u, 
   da.phi = (pb.d.kind == FTOEP_L1_HYPERBOLIC) ? phi : nullptr;
   da.wu0 = pb.wu0;
   da.wphi = pb.wphi;
+  da.diff_form = 1;
   LAUNCH(FTOEP_K_SINE, launch_dst_forward(pr, da, st));
   TRY(solve_pairs(pl, pb, pr, pl->z, pb.spec));
   da.u = u;
   da.accumulate = 0;
   LAUNCH(FTOEP_K_SINE, launch_dst_inverse(pr, da, st));
+  TRY(scan_lines(pl, pb, u, u, u0, 0, 0));
   if (pr == P64) return FTOEP_OK;
-  // residual in double: r = f + init - T u - S u
+  // residual of the original form in double: r = f + init - T u - S u
   TRY(build_product_spectrum(pl, pb, pb.a, &pb.spec_mv));
   TRY(product_lines(pl, pb, pb.spec_mv, u, nullptr, pb.M, 0, pl->zmv));
   ResidualArgs ra{};
@@ -385,13 +417,16 @@ ftoep_status solve_problem(ftoep_plan pl, Prob& pb, const double* f, double* u, 
   ra.inv_h2 = 1.0 / (pb.h * pb.h);
   ra.lambda = pb.d.lambda;
   LAUNCH(FTOEP_K_OTHER, launch_residual(ra, st));
+  // correction: same rows, zero initial data; v-correction lands in r, then u += tau cumsum
   DstArgs dr = dst_args(pl, pb, pr, pl->z);
   dr.f = pl->r;
+  dr.diff_form = 1;
   LAUNCH(FTOEP_K_SINE, launch_dst_forward(pr, dr, st));
   TRY(solve_pairs(pl, pb, pr, pl->z, pb.spec));
-  dr.u = u;
-  dr.accumulate = 1;
+  dr.u = pl->r;
+  dr.accumulate = 0;
   LAUNCH(FTOEP_K_SINE, launch_dst_inverse(pr, dr, st));
+  TRY(scan_lines(pl, pb, pl->r, u, nullptr, 1, 0));
   return FTOEP_OK;
 }
 
@@ -473,7 +508,8 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
     if (pb.d.space) maxtw = std::max<int64_t>(maxtw, 2 * (pb.M + 1));
     z_el = std::max<size_t>(z_el, (size_t)pb.P * np);
     mv_el = std::max<size_t>(mv_el, (size_t)pb.P * np);
-    if (pb.prec == P32) r_el = std::max<size_t>(r_el, (size_t)pb.M * pb.N);
+    r_el = std::max<size_t>(r_el, (size_t)pb.M * pb.N);
+    pl->prefix_elems = std::max<size_t>(pl->prefix_elems, (size_t)pb.P);
     pl->probs.push_back(std::move(pb));
   }
   pl->total_field = foff;
@@ -513,7 +549,8 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
   if ((st = dalloc(pl, &pl->scratch, z_el * sizeof(double2))) != FTOEP_OK) return bail(st);
   if ((st = dalloc(pl, (void**)&pl->zmv, mv_el * sizeof(double2))) != FTOEP_OK) return bail(st);
   if ((st = dalloc(pl, (void**)&pl->scratch_mv, 2 * mv_el * sizeof(double2))) != FTOEP_OK) return bail(st);
-  if (r_el && (st = dalloc(pl, (void**)&pl->r, r_el * sizeof(double))) != FTOEP_OK) return bail(st);
+  if ((st = dalloc(pl, (void**)&pl->r, r_el * sizeof(double))) != FTOEP_OK) return bail(st);
+  if ((st = dalloc(pl, (void**)&pl->prefix, pl->prefix_elems * sizeof(double2))) != FTOEP_OK) return bail(st);
   if ((st = dalloc(pl, (void**)&pl->dpart, 1024 * sizeof(double))) != FTOEP_OK) return bail(st);
   if ((st = dalloc(pl, (void**)&pl->dscal, (size_t)nprob * sizeof(double))) != FTOEP_OK) return bail(st);
   if (cudaMemsetAsync(pl->z, 0, z_el * sizeof(double2), pl->stream) != cudaSuccess) {
@@ -526,9 +563,10 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
     pb.h_a.resize(Np);
     pb.h_dadg.resize(Np);
     scheme_weights(pb.d.kind, pb.d.gamma, pb.tau, Np, pb.h_a.data(), pb.h_dadg.data());
-    std::vector<double> wu0(N), wphi(N);
+    std::vector<double> wu0(N), wphi(N), he(Np);
     initial_weights(pb.d.kind, pb.d.gamma, pb.tau, N, wu0.data(), wphi.data());
-    std::vector<double2> invd(pb.P);
+    difference_weights(pb.d.kind, pb.d.gamma, pb.tau, Np, he.data());
+    std::vector<double2> invd(pb.P), lt(pb.P);
     for (int64_t p = 0; p < pb.P; ++p) {
       double lam[2];
       for (int q = 0; q < 2; ++q) {
@@ -540,18 +578,23 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
           lam[q] = pb.d.lambda;
         }
       }
-      invd[p] = make_double2(1.0 / (pb.h_a[0] + lam[0]), 1.0 / (pb.h_a[0] + lam[1]));
+      invd[p] = make_double2(1.0 / (he[0] + lam[0] * pb.tau), 1.0 / (he[0] + lam[1] * pb.tau));
+      lt[p] = make_double2(lam[0] * pb.tau, lam[1] * pb.tau);
     }
     if ((st = dalloc(pl, (void**)&pb.a, Np * sizeof(double))) != FTOEP_OK) return bail(st);
     if ((st = dalloc(pl, (void**)&pb.dadg, Np * sizeof(double))) != FTOEP_OK) return bail(st);
     if ((st = dalloc(pl, (void**)&pb.wu0, N * sizeof(double))) != FTOEP_OK) return bail(st);
     if ((st = dalloc(pl, (void**)&pb.wphi, N * sizeof(double))) != FTOEP_OK) return bail(st);
     if ((st = dalloc(pl, (void**)&pb.invdiag, pb.P * sizeof(double2))) != FTOEP_OK) return bail(st);
+    if ((st = dalloc(pl, (void**)&pb.lamtau, pb.P * sizeof(double2))) != FTOEP_OK) return bail(st);
+    if ((st = dalloc(pl, (void**)&pb.e, Np * sizeof(double))) != FTOEP_OK) return bail(st);
     if (cudaMemcpy(pb.a, pb.h_a.data(), Np * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(pb.dadg, pb.h_dadg.data(), Np * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(pb.wu0, wu0.data(), N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(pb.wphi, wphi.data(), N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(pb.invdiag, invd.data(), pb.P * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(pb.invdiag, invd.data(), pb.P * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(pb.lamtau, lt.data(), pb.P * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(pb.e, he.data(), Np * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
       cudaGetLastError();
       pl->err = "weight upload failed";
       return bail(FTOEP_ECUDA);
@@ -695,8 +738,12 @@ ftoep_status ftoep_adjoint(ftoep_plan pl, const double* g, const double* u, doub
       q.ncols = (int64_t)q.nblk * q.B;
       if (q.Sf != pb.Sf) return fail(pl, FTOEP_EUNSUPPORTED, "adjoint: spectrum level mismatch");
     }
+    // With u = tau C v (C the all-ones lower triangle), A_u = A_v (tau C)^-1, so
+    // A_u^-T g = A_v^-T (tau C^T g): suffix sums of g, then the transposed difference-form
+    // solve, done as time reversal + forward solve + reversal (J A_v^T J = A_v per mode).
+    TRY(scan_lines(pl, pb, dg + pb.foff, pl->r, nullptr, 0, 1));
     DstArgs da = dst_args(pl, q, P64, pl->z);
-    da.f = dg + pb.foff;
+    da.f = pl->r;
     da.reverse = 1;
     LAUNCH(FTOEP_K_SINE, launch_dst_forward(P64, da, st));
     TRY(solve_pairs(pl, q, P64, pl->z, pb.spec64));

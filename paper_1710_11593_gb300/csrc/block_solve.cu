@@ -23,13 +23,18 @@ constexpr int kThreads = 256;
 template <typename T>
 using Vt = typename VecOf<T>::type;
 
-// Leaf forward substitution in double precision, one warp, unit-diagonal form: with
-// d_c = a_0 + lambda of component c (c = 0: mode 2p in .x, c = 1: mode 2p+1 in .y),
-//     x_k = y'_k,   y'_i -= (a_{i-k}/d_c) x_k  (i > k),   y' = y/d_c,
-// so each of the L steps is one shuffle and one FMA.  Lane l = c*L + i (i < L <= 16)
-// owns row i of component c; asc[c*L + j] = a_j/d_c.
+// Leaf forward substitution in double precision, one warp.  The operator of mode c is
+// T_c = E + (lambda_c tau) 1, with E the shared lower-triangular Toeplitz matrix (first
+// column e) and 1 the all-ones lower triangle.  The all-ones part couples a row to every
+// earlier unknown through their sum, so the leaf receives the running sum P_c of all
+// earlier unknowns and returns it advanced over its own L unknowns.  Unit-diagonal form,
+// with d_c = e_0 + lambda_c tau:
+//     y'_i = (y_i - lambda_c tau P_c)/d_c,  x_k = y'_k,  y'_i -= ((e_{i-k} + lambda_c tau)/d_c) x_k,
+// one shuffle and one FMA per step.  Lane l = c*L + i (i < L <= 16) owns row i of
+// component c (c = 0: mode 2p in .x, c = 1: mode 2p+1 in .y); asc[c*L + j] holds
+// (e_j + lambda_c tau)/d_c and P (per lane, for its component) stays in a register.
 template <typename T>
-__device__ __forceinline__ void leaf_solve(Vt<T>* zb, int L, const double* asc, double2 inv) {
+__device__ __forceinline__ void leaf_solve(Vt<T>* zb, int L, const double* asc, double inv, double lt, double& P) {
   const int lane = threadIdx.x;
   const int c = lane >= L ? 1 : 0;
   const int i = lane - c * L;
@@ -37,7 +42,7 @@ __device__ __forceinline__ void leaf_solve(Vt<T>* zb, int L, const double* asc, 
   double y = 0.0;
   if (act) {
     const Vt<T> z = zb[i];
-    y = c ? (double)z.y * inv.y : (double)z.x * inv.x;
+    y = ((c ? (double)z.y : (double)z.x) - lt * P) * inv;
   }
   const double* ac = asc + c * L;
   for (int k = 0; k < L; ++k) {
@@ -47,6 +52,10 @@ __device__ __forceinline__ void leaf_solve(Vt<T>* zb, int L, const double* asc, 
   if (act) {
     if (c) zb[i].y = (T)y; else zb[i].x = (T)y;
   }
+  // advance the running sum by this leaf's unknowns (segments of L lanes)
+  double t = act ? y : 0.0;
+  for (int w = 1; w < L; w <<= 1) t += __shfl_xor_sync(0xffffffffu, t, w);
+  P += t;
 }
 
 // y[mid + i] -= sum_{k<s} a_{s+i-k} x[mid - s + k], both components, direct sums.
@@ -107,16 +116,26 @@ __global__ void __launch_bounds__(kThreads) block_solve_kernel(BlockArgs A) {
   for (int i = threadIdx.x; i < B; i += blockDim.x) zb[i] = zg[i];
   for (int i = threadIdx.x; i < nat; i += blockDim.x) at[i] = (T)A.a[i];
   const double2 inv = A.invdiag[p];
+  const double2 lt = A.lamtau[p];
   for (int i = threadIdx.x; i < 2 * L; i += blockDim.x) {
     const int j = i % L;
-    asc[i] = j == 0 ? 0.0 : A.a[j] * (i < L ? inv.x : inv.y);
+    asc[i] = j == 0 ? 0.0 : (A.a[j] + (i < L ? lt.x : lt.y)) * (i < L ? inv.x : inv.y);
   }
+  // warp 0 carries the running sums: lanes of component 0 hold P.x, of component 1 P.y
+  const bool c1lane = threadIdx.x >= L && threadIdx.x < 2 * L;
+  double P = 0.0;
+  if (threadIdx.x < 32) {
+    const double2 p0 = A.prefix[p];
+    P = c1lane ? p0.y : p0.x;
+  }
+  const double my_inv = c1lane ? inv.y : inv.x;
+  const double my_lt = c1lane ? lt.y : lt.x;
   const V* spec = (const V*)A.spec;
   const V* tw = (const V*)A.tw;
   __syncthreads();
   const int nleaf = B / L;
   for (int b = 0; b < nleaf; ++b) {
-    if (threadIdx.x < 32) leaf_solve<T>(zb + b * L, L, asc, inv);
+    if (threadIdx.x < 32) leaf_solve<T>(zb + b * L, L, asc, my_inv, my_lt, P);
     __syncthreads();
     const int v = b + 1;
     if (v < nleaf) {
@@ -131,6 +150,10 @@ __global__ void __launch_bounds__(kThreads) block_solve_kernel(BlockArgs A) {
     }
   }
   for (int i = threadIdx.x; i < B; i += blockDim.x) zg[i] = zb[i];
+  if (threadIdx.x < 32) {
+    const double py = __shfl_sync(0xffffffffu, P, L);
+    if (threadIdx.x == 0) A.prefix[p] = make_double2(P, py);
+  }
 }
 
 template <typename T>

@@ -13,6 +13,8 @@ double scheme_scale(int kind, double gamma, double tau);
 void scheme_weights(int kind, double gamma, double tau, int64_t n, double* a, double* dadg);
 // right-hand-side weights of u0 and phi at levels 1..n
 void initial_weights(int kind, double gamma, double tau, int64_t n, double* wu0, double* wphi);
+// first column e_j (j < n) of the time operator acting on v_k = (u^k - u^{k-1})/tau
+void difference_weights(int kind, double gamma, double tau, int64_t n, double* e);
 
 // ---------------------------------------------------------------- kernel launchers
 // Storage precision of the complex work arrays: 0 = double2, 1 = float2.
@@ -36,6 +38,9 @@ struct DstArgs {
   int reverse;          // time reversal of z (forward: write z[N-1-n]; inverse: read z[N-1-n])
   int accumulate;       // inverse: u += result
   int space;            // 0: no transform (pairs of rows), 1: sine transform
+  int diff_form;        // forward: right-hand side of the difference form (-(S u0) instead of wu0*u0)
+  double inv_h2;        // 1/h^2 (space 1) for S u0
+  double lambda;        // lambda (space 0) for S u0
   const void* tw;       // twiddles of the z precision
 };
 int launch_dst_forward(Prec prec, const DstArgs& a, cudaStream_t st);
@@ -53,6 +58,22 @@ struct PackArgs {
 };
 int launch_pack(Prec prec, const PackArgs& a, cudaStream_t st);
 int launch_unpack(Prec prec, const PackArgs& a, cudaStream_t st);
+
+// Time prefix sums along every line of [M][N] doubles, in double precision:
+//   reverse = 0: out[j][n] = base + tau * sum_{k<=n} in[j][k], base = out[j][n] (accumulate)
+//                or u0[j] (u0 != NULL) or 0;
+//   reverse = 1: out[j][n] = tau * sum_{k>=n} in[j][k].
+// in may equal out.
+struct ScanArgs {
+  const double* in;
+  double* out;
+  const double* u0;
+  int64_t N, M;
+  double tau;
+  int accumulate;
+  int reverse;
+};
+int launch_scan(const ScanArgs& a, cudaStream_t st);
 
 // Residual r = f + wu0*u0 + wphi*phi - (T u) - S(u), with (T u) given in pairs (double2)
 // and S the spatial operator: Dirichlet -u_xx (space 1) or lambda*u (space 0).
@@ -124,8 +145,10 @@ struct BlockArgs {
   int B;            // block length (power of two)
   int L;            // leaf length (power of two <= 16, <= B)
   int Sf;           // first FFT level (levels L <= s < Sf are dense products)
-  const double* a;  // a[0..B)
-  const double2* invdiag;  // per pair: 1/(a0+lambda) of its two modes
+  const double* a;  // e[0..B): shared first column (difference form)
+  const double2* invdiag;  // per pair: 1/(e0 + lambda*tau) of its two modes
+  const double2* lamtau;   // per pair: lambda*tau of its two modes (all-ones part of the operator)
+  double2* prefix;         // per pair: running sums of the solved v (in: before t0, out: after)
   const void* spec;        // spectra of levels Sf..B/2 (level s at offset 2(s - Sf))
   const void* tw;
 };

@@ -31,6 +31,25 @@ inline void set_smem(const void* fn, size_t bytes) {
 // 2 S_b[m] and imaginary part -2 S_a[m]; the orthonormal coefficient is
 // sqrt(2/K) S[m] = (FFT value)/sqrt(2K).  The transform is its own inverse.
 
+// Right-hand side at (j, n): f plus the initial-data terms.  Original form: wu0[n]*u0[j];
+// difference form: -(S u0)_j with S the spatial operator (Dirichlet -u_xx or lambda).
+__device__ __forceinline__ double rhs_value(const DstArgs& A, int64_t j, int64_t n) {
+  double v = A.f[j * A.N + n];
+  if (A.u0) {
+    if (!A.diff_form) {
+      v += A.wu0[n] * A.u0[j];
+    } else if (A.space == 1) {
+      const double um = j > 0 ? A.u0[j - 1] : 0.0;
+      const double up = j + 1 < A.M ? A.u0[j + 1] : 0.0;
+      v -= (2.0 * A.u0[j] - um - up) * A.inv_h2;
+    } else {
+      v -= A.lambda * A.u0[j];
+    }
+  }
+  if (A.phi) v += A.wphi[n] * A.phi[j];
+  return v;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) dst_forward_kernel(DstArgs A, int C) {
   typedef Vt<T> V;
@@ -50,10 +69,7 @@ __global__ void __launch_bounds__(kThreads) dst_forward_kernel(DstArgs A, int C)
         for (int q = 0; q < 2; ++q) {
           const int64_t j = 2 * p + q;
           if (j >= M) continue;
-          double t = A.f[j * N + n];
-          if (A.u0) t += A.wu0[n] * A.u0[j];
-          if (A.phi) t += A.wphi[n] * A.phi[j];
-          v[q] = t;
+          v[q] = rhs_value(A, j, n);
         }
       }
       const int64_t nout = (A.reverse && n < N) ? N - 1 - n : n;
@@ -75,12 +91,7 @@ __global__ void __launch_bounds__(kThreads) dst_forward_kernel(DstArgs A, int C)
     const int64_t j = e / C;
     const int c = (int)(e % C);
     const int64_t n = col0 + c;
-    double v = 0.0;
-    if (n < N) {
-      v = A.f[j * N + n];
-      if (A.u0) v += A.wu0[n] * A.u0[j];
-      if (A.phi) v += A.wphi[n] * A.phi[j];
-    }
+    const double v = n < N ? rhs_value(A, j, n) : 0.0;
     const T tv = (T)v;
     V* col = sm + (c >> 1) * lds;
     const int pos = (int)j + 1;
@@ -241,6 +252,66 @@ __global__ void unpack_kernel(PackArgs A) {
   if (2 * p + 1 < A.nlines) {
     double* y1 = A.y + (2 * p + 1) * A.N + n;
     *y1 = A.mode ? *y1 + (double)v.y : (double)v.y;
+  }
+}
+
+// ------------------------------------------------------------------ time prefix sums
+
+// One block per line; chunks of 4*kThreads elements, each thread a run of 4, block-wide
+// exclusive scan of the run totals, carry between chunks.  Double precision throughout.
+__global__ void __launch_bounds__(kThreads) scan_kernel(ScanArgs A) {
+  __shared__ double wsum[kThreads / 32];
+  __shared__ double carry_s;
+  const int64_t j = blockIdx.x;
+  const double* in = A.in + j * A.N;
+  double* out = A.out + j * A.N;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t chunk = 4 * kThreads;
+  double carry = 0.0;
+  const int64_t nchunks = (A.N + chunk - 1) / chunk;
+  for (int64_t ci = 0; ci < nchunks; ++ci) {
+    // forward: chunks left to right, runs in order; reverse: mirror both
+    const int64_t c0 = A.reverse ? A.N - (ci + 1) * chunk : ci * chunk;
+    double v[4];
+    double run = 0.0;
+    for (int q = 0; q < 4; ++q) {
+      const int64_t pos = A.reverse ? c0 + (chunk - 1 - (4 * threadIdx.x + q)) : c0 + 4 * threadIdx.x + q;
+      v[q] = (pos >= 0 && pos < A.N) ? in[pos] : 0.0;
+      run += v[q];
+      v[q] = run;  // inclusive within the run
+    }
+    // exclusive scan of run totals across the block
+    double x = run;
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      double w = lane < kThreads / 32 ? wsum[lane] : 0.0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      if (lane < kThreads / 32) wsum[lane] = w;
+      if (lane == kThreads / 32 - 1) carry_s = w;
+    }
+    __syncthreads();
+    const double before = carry + (x - run) + (warp > 0 ? wsum[warp - 1] : 0.0);
+    for (int q = 0; q < 4; ++q) {
+      const int64_t pos = A.reverse ? c0 + (chunk - 1 - (4 * threadIdx.x + q)) : c0 + 4 * threadIdx.x + q;
+      if (pos < 0 || pos >= A.N) continue;
+      const double sum = A.tau * (before + v[q]);
+      if (A.reverse) {
+        out[pos] = sum;
+      } else {
+        const double base = A.accumulate ? out[pos] : (A.u0 ? A.u0[j] : 0.0);
+        out[pos] = base + sum;
+      }
+    }
+    carry += carry_s;
+    __syncthreads();
   }
 }
 
@@ -543,6 +614,11 @@ int launch_unpack(Prec prec, const PackArgs& a, cudaStream_t st) {
   dim3 grid((unsigned)((a.N + kThreads - 1) / kThreads), (unsigned)((a.nlines + 1) / 2));
   if (prec == P64) unpack_kernel<double><<<grid, kThreads, 0, st>>>(a);
   else unpack_kernel<float><<<grid, kThreads, 0, st>>>(a);
+  return 1;
+}
+
+int launch_scan(const ScanArgs& a, cudaStream_t st) {
+  scan_kernel<<<(unsigned)a.M, kThreads, 0, st>>>(a);
   return 1;
 }
 

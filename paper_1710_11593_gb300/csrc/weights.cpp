@@ -172,6 +172,26 @@ void scheme_weights(int kind, double gamma, double tau, int64_t n, double* a, do
   }
 }
 
+void difference_weights(int kind, double gamma, double tau, int64_t n, double* e) {
+  // e_j = c1 q_j: the scheme rewritten in the difference quotients v_k = (u^k - u^{k-1})/tau
+  // (the form in which the L1 quotient and Eq. 15 are written).  c1 = scale * tau.
+  //   kind 0: q_j = G_j = (j+1)^b - j^b,                b = 1 - g
+  //   kind 1: q_0 = M_0 = 1, q_j = M_j - M_{j-1},        b = 2 - g
+  const double c1 = scheme_scale(kind, gamma, tau) * tau;
+  const double b = kind == 0 ? 1.0 - gamma : 2.0 - gamma;
+  for (int64_t j = 0; j < n; ++j) {
+    double q;
+    if (j == 0) {
+      q = 1.0;
+    } else if (kind == 0) {
+      q = first_diff(b, j);
+    } else {
+      q = (j >= kSeriesFrom) ? second_diff_series(b, j, nullptr) : second_diff_direct(b, j, nullptr);
+    }
+    e[j] = c1 * q;
+  }
+}
+
 void initial_weights(int kind, double gamma, double tau, int64_t n, double* wu0, double* wphi) {
   const double s = scheme_scale(kind, gamma, tau);
   if (kind == 0) {
