@@ -1,0 +1,140 @@
+"""Differentiation workload: loss = ||u(., T) - u_obs||^2, gradients in f and gamma through
+torch.autograd (ftoep_adjoint underneath), against the oracle.
+
+Small case (M = 31, N = 512): oracle adjoint march and oracle gamma-gradient, plus
+central differences of the ORACLE forward solve (step 1e-6 in gamma; 1e-4 on f entries
+and along one random direction).  Full size (M = 1023, N = 65536): the adjoint is
+anti-causal, so its last n0 levels equal the oracle adjoint of the n0-level suffix
+problem; sampled modes are marched per mode; the gamma-gradient is the mode-1 term
+(u is a pure mode-1 field for this source, the other modes contribute at roundoff).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1710_11593_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_ft():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_11593_gb300 import autograd, ftoep
+    ftoep.load()
+    return torch, ftoep, autograd
+
+
+def _rel(a, b):
+    return float(max(np.linalg.norm(a - b) / np.linalg.norm(b), np.max(np.abs(a - b)) / np.max(np.abs(b))))
+
+
+@pytest.mark.parametrize("recompute", [False, True])
+def test_autograd_small_vs_oracle(torch_ft, oracle, recompute):
+    torch, ftoep, ag = torch_ft
+    M, N, g = 31, 512, 0.6
+    p = wl.config_adjoint(M=M, N=N, gamma=g)
+    f = wl.materialize(p.source, p.kind, N, M)
+    u_obs = oracle.march(0, 1, 0.55, f)[:, -1] + wl.noise(M, 1e-3, seed=8)
+
+    ft_ = torch.from_numpy(f).cuda().requires_grad_(True)
+    gt = torch.tensor(g, dtype=torch.float64, requires_grad=True)
+    u = ag.fractional_solve(ft_, gt, recompute=recompute)
+    loss = torch.sum((u[:, -1] - torch.from_numpy(u_obs).cuda()) ** 2)
+    loss.backward()
+    dldf = ft_.grad.cpu().numpy()
+    dldg = float(gt.grad)
+
+    def oloss(ff, gg):
+        uu = oracle.march(0, 1, gg, ff)
+        return float(np.sum((uu[:, -1] - u_obs) ** 2))
+
+    uo = oracle.march(0, 1, g, f)
+    dLdu = np.zeros_like(uo)
+    dLdu[:, -1] = 2 * (uo[:, -1] - u_obs)
+    lam = oracle.adjoint_march(0, 1, g, dLdu)
+    assert _rel(dldf, lam) < 1e-12
+    grad_ref = oracle.gamma_gradient(0, g, uo, lam)
+    assert abs(dldg - grad_ref) <= 1e-9 * abs(grad_ref)
+    # central differences of the oracle forward
+    fd = (oloss(f, g + 1e-6) - oloss(f, g - 1e-6)) / 2e-6
+    assert abs(dldg - fd) <= 1e-6 * abs(fd)
+    rng = np.random.default_rng(4)
+    for _ in range(8):
+        j, n = int(rng.integers(M)), int(rng.integers(N))
+        fp, fm = f.copy(), f.copy()
+        fp[j, n] += 1e-4
+        fm[j, n] -= 1e-4
+        fdj = (oloss(fp, g) - oloss(fm, g)) / 2e-4
+        assert abs(fdj - dldf[j, n]) <= 1e-6 * max(abs(fdj), 1e-3 * np.max(np.abs(dldf)))
+    d = rng.standard_normal(f.shape)
+    fdd = (oloss(f + 1e-5 * d, g) - oloss(f - 1e-5 * d, g)) / 2e-5
+    assert abs(fdd - float(np.sum(d * dldf))) <= 1e-6 * abs(fdd)
+
+
+def test_adjoint_hyperbolic_small(torch_ft, oracle):
+    torch, ftoep, ag = torch_ft
+    M, N, g = 15, 400, 1.4
+    rng = np.random.default_rng(12)
+    f = rng.standard_normal((M, N))
+    gg = rng.standard_normal((M, N))
+    with ftoep.Plan([ftoep.ProblemSpec(1, g, N, M)]) as plan:
+        u = plan.solve(torch.from_numpy(f).cuda())
+        dldf, dg = plan.adjoint(torch.from_numpy(gg).cuda(), u)
+    uo = oracle.march(1, 1, g, f)
+    lam = oracle.adjoint_march(1, 1, g, gg)
+    assert _rel(dldf.cpu().numpy(), lam) < 1e-11
+    ref = oracle.gamma_gradient(1, g, uo, lam)
+    assert abs(dg[0] - ref) <= 1e-8 * abs(ref)
+
+
+def test_config5_adjoint_full(torch_ft, oracle):
+    """gamma = 0.6, M = 1023, N = 65536; u_obs from the oracle's mode-1 march at 0.55 plus
+    N(0, 1e-3^2) noise."""
+    torch, ftoep, ag = torch_ft
+    p = wl.config_adjoint()
+    M, N, g = p.M, p.N, p.gamma
+    x = wl.space_points(M)
+    s1 = np.sqrt(2.0 / (M + 1)) * np.sin(math.pi * np.arange(1, M + 1) / (M + 1))
+    # the source is sin(pi x) times a time profile: mode 1 only
+    tpts = wl.time_points(0, N)
+    prof = sum(c * tpts ** pw for c, pw, k in p.source)
+    fhat1 = prof * float(np.dot(s1, np.sin(math.pi * x)))
+    lam1 = oracle.mode_eigenvalue(1, M)
+    uh55 = oracle.march_mode(0, 0.55, fhat1, lam1)
+    u_obs = uh55[-1] * s1 + wl.noise(M, 1e-3, seed=21)
+    uh = oracle.march_mode(0, g, fhat1, lam1)
+
+    f = wl.materialize_torch(p.source, p.kind, N, M, device="cuda")
+    gt = torch.tensor(g, dtype=torch.float64, requires_grad=True)
+    fr = f.clone().requires_grad_(True)
+    u = ag.fractional_solve(fr, gt)
+    loss = torch.sum((u[:, -1] - torch.from_numpy(u_obs).cuda()) ** 2)
+    loss.backward()
+    dldf = fr.grad
+    # oracle adjoint input: g = 2 (u(T) - u_obs) at the last level
+    gT = 2.0 * (uh[-1] * s1 - u_obs)
+    # suffix: last n0 levels, all points
+    n0 = 2048
+    gs = np.zeros((M, n0))
+    gs[:, -1] = gT
+    lam_suffix = oracle.adjoint_march(0, 1, g, gs, T=n0 / N)
+    assert _rel(dldf[:, N - n0:].cpu().numpy(), lam_suffix) < 1e-12
+    # sampled modes over the full length
+    jj = torch.arange(1, M + 1, dtype=torch.float64, device="cuda")
+    for m in (1, 2, 700):
+        sm = np.sqrt(2.0 / (M + 1)) * np.sin(math.pi * m * np.arange(1, M + 1) / (M + 1))
+        ghat = np.zeros(N)
+        ghat[-1] = float(np.dot(sm, gT))
+        lam_m = oracle.adjoint_march(0, 0, g, ghat[None, :], lam=oracle.mode_eigenvalue(m, M))[0]
+        smt = torch.sin(torch.remainder(m * jj, 2 * (M + 1)) * (math.pi / (M + 1))) * math.sqrt(2.0 / (M + 1))
+        got = (smt @ dldf).cpu().numpy()
+        assert _rel(got, lam_m) < 1e-11
+        if m == 1:
+            lam_1 = lam_m
+    # gamma-gradient: mode-1 term
+    grad_ref = oracle.gamma_gradient(0, g, uh[None, :], lam_1[None, :])
+    assert abs(float(gt.grad) - grad_ref) <= 1e-9 * abs(grad_ref)
