@@ -87,8 +87,9 @@ typedef enum {
 
 /* One problem.  T: final time (> 0).  L: length of the space interval (> 0, ignored for
  * FTOEP_SPACE_NONE).  lambda: reaction coefficient for FTOEP_SPACE_NONE (>= 0).
- * N >= 1 time steps; M >= 1 interior points (rows, for FTOEP_SPACE_NONE).
- * Sine transforms currently need M+1 to be a power of two (else FTOEP_EUNSUPPORTED). */
+ * N >= 1 time steps (N <= 2^22); M >= 1 interior points (rows, for FTOEP_SPACE_NONE).
+ * Sine transform sizes: M+1 a power of two up to 4096 (double) / 8192 (mixed); any other
+ * M+1 (Bluestein chirp-z) up to 2048 (double) / 4096 (mixed); beyond: FTOEP_EUNSUPPORTED. */
 typedef struct {
   int kind;       /* ftoep_kind      */
   int space;      /* ftoep_space     */
@@ -112,8 +113,7 @@ typedef struct {
  * the per-level kernel spectra and allocates the device workspace.  cuda_stream is a
  * cudaStream_t (NULL = legacy default stream).  On success *out owns all of it.
  * Errors: FTOEP_EINVAL (gamma outside the kind's range, N/M/T/L invalid, nprob < 1,
- * out NULL), FTOEP_EUNSUPPORTED (M+1 not a power of two with a sine transform),
- * FTOEP_ENOMEM, FTOEP_ECUDA. */
+ * out NULL), FTOEP_EUNSUPPORTED (sizes beyond the limits above), FTOEP_ENOMEM, FTOEP_ECUDA. */
 ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob,
                           const ftoep_tuning* tune, void* cuda_stream);
 

@@ -40,6 +40,13 @@ struct Prob {
   double* wphi = nullptr;
   double2* invdiag = nullptr;   // per pair 1/(e_0 + lambda tau)
   double2* lamtau = nullptr;    // per pair lambda tau
+  // sine transform for M+1 not a power of two (Bluestein tables, double and float)
+  bool bluestein = false;
+  int logP = 0;
+  double2* chirp64 = nullptr;
+  double2* bspec64 = nullptr;
+  float2* chirp32 = nullptr;
+  float2* bspec32 = nullptr;
   void* spec = nullptr;         // solve spectra, precision prec
   double2* spec64 = nullptr;    // solve spectra in double (adjoint of mixed problems; == spec for P64)
   double2* spec_mv = nullptr;   // product spectrum, length 2Np
@@ -220,9 +227,10 @@ ftoep_status validate(const ftoep_problem& d, int i, const ftoep_tuning* tune) {
     return fail(pl, FTOEP_EINVAL, "problem %d: lambda must be >= 0", i);
   if (d.N > (int64_t(1) << 22)) return fail(pl, FTOEP_EUNSUPPORTED, "problem %d: N > 2^22 not supported", i);
   if (d.space == FTOEP_SPACE_DIRICHLET_LAPLACIAN) {
-    if (!is_pow2(d.M + 1)) return fail(pl, FTOEP_EUNSUPPORTED, "problem %d: M+1 = %lld is not a power of two", i, (long long)(d.M + 1));
-    const int64_t lim = d.precision == FTOEP_FP64 ? 4096 : 8192;
-    if (d.M + 1 > lim) return fail(pl, FTOEP_EUNSUPPORTED, "problem %d: M+1 > %lld not supported", i, (long long)lim);
+    const Prec pr = d.precision == FTOEP_FP64 ? P64 : P32;
+    const int64_t lim = is_pow2(d.M + 1) ? (d.precision == FTOEP_FP64 ? 4096 : 8192) : bluestein_max_K(pr);
+    if (d.M + 1 > lim) return fail(pl, FTOEP_EUNSUPPORTED, "problem %d: M+1 = %lld > %lld not supported", i,
+                                   (long long)(d.M + 1), (long long)lim);
   }
   if (tune) {
     if (tune->leaf && (!is_pow2(tune->leaf) || tune->leaf > 16))
@@ -324,6 +332,13 @@ DstArgs dst_args(ftoep_plan pl, Prob& pb, Prec pr, void* z) {
   da.inv_h2 = 1.0 / (pb.h * pb.h);
   da.lambda = pb.d.lambda;
   da.tw = tw_of(pl, pr);
+  if (pb.bluestein) {
+    da.bluestein = 1;
+    da.K = (int)(pb.M + 1);
+    da.logP = pb.logP;
+    da.chirp = pr == P64 ? (const void*)pb.chirp64 : (const void*)pb.chirp32;
+    da.bspec = pr == P64 ? (const void*)pb.bspec64 : (const void*)pb.bspec32;
+  }
   return da;
 }
 
@@ -445,6 +460,72 @@ ftoep_status sync_plan(ftoep_plan pl) {
   return FTOEP_OK;
 }
 
+
+// Bluestein tables for the sine transform of a problem with K = M+1 not a power of two:
+// chirp c_n = exp(-i pi n^2 / L) (L = 2K, n^2 reduced mod 2L exactly) and the forward
+// transform of b_m = conj(c_|m|) wrapped to length P, in the bit-reversed order of the
+// device decimation-in-frequency FFT, divided by P.  Host long double.
+ftoep_status build_bluestein(ftoep_plan pl, Prob& pb) {
+  const int64_t K = pb.M + 1, L = 2 * K;
+  const int logP = ilog2(2 * L - 1);
+  const int64_t P = int64_t(1) << logP;
+  pb.logP = logP;
+  const long double pi = 3.141592653589793238462643383279502884L;
+  std::vector<long double> cr(L), ci(L);
+  for (int64_t n = 0; n < L; ++n) {
+    const int64_t r = (n * n) % (2 * L);
+    const long double ang = -pi * (long double)r / (long double)L;
+    cr[n] = cosl(ang);
+    ci[n] = sinl(ang);
+  }
+  std::vector<long double> br(P, 0.0L), bi(P, 0.0L);
+  for (int64_t m = 0; m < L; ++m) {
+    br[m] = cr[m];
+    bi[m] = -ci[m];
+    if (m > 0) {
+      br[P - m] = cr[m];
+      bi[P - m] = -ci[m];
+    }
+  }
+  // radix-2 decimation in frequency, natural in, bit-reversed out (same permutation as fft_dif)
+  for (int64_t len = P; len >= 2; len >>= 1) {
+    const int64_t half = len / 2;
+    for (int64_t i = 0; i < half; ++i) {
+      const long double a = -2.0L * pi * (long double)i / (long double)len;
+      const long double wr = cosl(a), wi = sinl(a);
+      for (int64_t st = 0; st < P; st += len) {
+        const int64_t x = st + i, y = st + i + half;
+        const long double ur = br[x], ui = bi[x], vr = br[y], vi = bi[y];
+        br[x] = ur + vr;
+        bi[x] = ui + vi;
+        const long double dr = ur - vr, di = ui - vi;
+        br[y] = dr * wr - di * wi;
+        bi[y] = dr * wi + di * wr;
+      }
+    }
+  }
+  std::vector<double2> c64(L), b64(P);
+  std::vector<float2> c32(L), b32(P);
+  for (int64_t n = 0; n < L; ++n) {
+    c64[n] = make_double2((double)cr[n], (double)ci[n]);
+    c32[n] = make_float2((float)cr[n], (float)ci[n]);
+  }
+  for (int64_t k = 0; k < P; ++k) {
+    b64[k] = make_double2((double)(br[k] / P), (double)(bi[k] / P));
+    b32[k] = make_float2((float)(br[k] / P), (float)(bi[k] / P));
+  }
+  ALLOC(pb.chirp64, L * sizeof(double2));
+  ALLOC(pb.bspec64, P * sizeof(double2));
+  ALLOC(pb.chirp32, L * sizeof(float2));
+  ALLOC(pb.bspec32, P * sizeof(float2));
+  CK(cudaMemcpy(pb.chirp64, c64.data(), L * sizeof(double2), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(pb.bspec64, b64.data(), P * sizeof(double2), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(pb.chirp32, c32.data(), L * sizeof(float2), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(pb.bspec32, b32.data(), P * sizeof(float2), cudaMemcpyHostToDevice));
+  pb.bluestein = true;
+  return FTOEP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -505,7 +586,10 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
     foff += pb.M * pb.N;
     voff += pb.M;
     maxtw = std::max<int64_t>(maxtw, 2 * np);
-    if (pb.d.space) maxtw = std::max<int64_t>(maxtw, 2 * (pb.M + 1));
+    if (pb.d.space) {
+      maxtw = std::max<int64_t>(maxtw, 2 * (pb.M + 1));
+      if (!is_pow2(pb.M + 1)) maxtw = std::max<int64_t>(maxtw, int64_t(1) << ilog2(4 * (pb.M + 1) - 1));
+    }
     z_el = std::max<size_t>(z_el, (size_t)pb.P * np);
     mv_el = std::max<size_t>(mv_el, (size_t)pb.P * np);
     r_el = std::max<size_t>(r_el, (size_t)pb.M * pb.N);
@@ -599,6 +683,7 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
       pl->err = "weight upload failed";
       return bail(FTOEP_ECUDA);
     }
+    if (pb.d.space && !is_pow2(pb.M + 1) && (st = build_bluestein(pl, pb)) != FTOEP_OK) return bail(st);
     const size_t nspec = pb.Sf <= Np / 2 ? (size_t)2 * (Np - pb.Sf) : 0;
     if (nspec) {
       if ((st = dalloc(pl, &pb.spec, nspec * velem(pb.prec))) != FTOEP_OK) return bail(st);
@@ -728,6 +813,9 @@ ftoep_status ftoep_adjoint(ftoep_plan pl, const double* g, const double* u, doub
       ALLOC(pb.spec64, (size_t)2 * (pb.Np - pb.Sf) * sizeof(double2));
       TRY(build_solve_spectra(pl, pb, P64, pb.spec64));
     }
+    if (pb.bluestein && pb.M + 1 > bluestein_max_K(P64))
+      return fail(pl, FTOEP_EUNSUPPORTED, "adjoint: M+1 = %lld > %d needs a double sine transform that is not built",
+                  (long long)(pb.M + 1), bluestein_max_K(P64));
     // The double-precision block parameters (fixed defaults for the adjoint).
     Prob q = pb;
     if (pb.prec != P64) {

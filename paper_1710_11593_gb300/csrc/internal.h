@@ -39,11 +39,20 @@ struct DstArgs {
   int accumulate;       // inverse: u += result
   int space;            // 0: no transform (pairs of rows), 1: sine transform
   int diff_form;        // forward: right-hand side of the difference form (-(S u0) instead of wu0*u0)
+  // Sine transform for M+1 not a power of two (Bluestein): the length-2K DFT of the odd
+  // extension as a cyclic convolution of length P = 2^logP >= 4K - 1 with the chirp.
+  int bluestein;
+  int K;                // M + 1
+  int logP;
+  const void* chirp;    // c_n = exp(-i pi n^2 / (2K)), n < 2K (z precision)
+  const void* bspec;    // forward transform (this library's order) of conj(chirp) wrapped to length P, / P
   double inv_h2;        // 1/h^2 (space 1) for S u0
   double lambda;        // lambda (space 0) for S u0
   const void* tw;       // twiddles of the z precision
 };
 int launch_dst_forward(Prec prec, const DstArgs& a, cudaStream_t st);
+// Largest M+1 the Bluestein sine transform handles in one block's shared memory.
+int bluestein_max_K(Prec prec);
 int launch_dst_inverse(Prec prec, const DstArgs& a, cudaStream_t st);
 
 // Pack real lines [nlines][N] into pairs [ceil(nlines/2)][ld] (zero padded to ld, optional

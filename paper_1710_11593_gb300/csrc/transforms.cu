@@ -199,6 +199,125 @@ __global__ void __launch_bounds__(kThreads) dst_inverse_kernel(DstArgs A, int C)
   }
 }
 
+// Sine transform for any K = M+1 (Bluestein / chirp-z).  With W = exp(-2 pi i / L),
+// L = 2K, and c_n = W^{n^2/2}: DFT(y)_k = c_k sum_n (y_n c_n) conj(c_{k-n}), a linear
+// convolution that a cyclic one of length P >= 2L-1 reproduces exactly.  One block
+// handles C time columns (C/2 complex column pairs, one P-buffer each).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) dst_bluestein_kernel(DstArgs A, int C, int fwd) {
+  typedef Vt<T> V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const int64_t col0 = (int64_t)blockIdx.x * C;
+  const int64_t M = A.M, N = A.N;
+  const int64_t P2 = (M + 1) / 2;
+  const int K = A.K, L = 2 * K;
+  const int P = 1 << A.logP, H = P >> 1;
+  const int lds = P + 1;
+  const int CP = C >> 1;
+  const V* chirp = (const V*)A.chirp;
+  for (int e = threadIdx.x; e < CP * H; e += blockDim.x) sm[(e / H) * lds + (e % H)] = vzero<V>();
+  __syncthreads();
+  if (fwd) {
+    for (int64_t e = threadIdx.x; e < M * C; e += blockDim.x) {
+      const int64_t j = e / C;
+      const int c = (int)(e % C);
+      const int64_t n = col0 + c;
+      const T tv = (T)(n < N ? rhs_value(A, j, n) : 0.0);
+      V* col = sm + (c >> 1) * lds;
+      const int pos = (int)j + 1;
+      if (c & 1) {
+        col[pos].y = tv;
+        col[L - pos].y = -tv;
+      } else {
+        col[pos].x = tv;
+        col[L - pos].x = -tv;
+      }
+    }
+  } else {
+    const V* z = (const V*)A.z;
+    for (int64_t e = threadIdx.x; e < P2 * C; e += blockDim.x) {
+      const int64_t p = e / C;
+      const int c = (int)(e % C);
+      const int64_t n = col0 + c;
+      const int64_t nin = (A.reverse && n < N) ? N - 1 - n : n;
+      const V zz = z[p * A.ld + nin];
+      V* col = sm + (c >> 1) * lds;
+      const int m1 = (int)(2 * p + 1), m2 = m1 + 1;
+      if (c & 1) {
+        col[m1].y = zz.x;
+        col[L - m1].y = -zz.x;
+        if (m2 <= M) {
+          col[m2].y = zz.y;
+          col[L - m2].y = -zz.y;
+        }
+      } else {
+        col[m1].x = zz.x;
+        col[L - m1].x = -zz.x;
+        if (m2 <= M) {
+          col[m2].x = zz.y;
+          col[L - m2].x = -zz.y;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < CP * L; e += blockDim.x) {
+    V* q = sm + (e / L) * lds + (e % L);
+    *q = cmul(*q, chirp[e % L]);
+  }
+  __syncthreads();
+  const V* tw = (const V*)A.tw;
+  fft_dif<V>(sm, A.logP, CP, lds, tw, true);
+  const V* bs = (const V*)A.bspec;
+  for (int e = threadIdx.x; e < CP * P; e += blockDim.x) {
+    V* q = sm + (e / P) * lds + (e % P);
+    *q = cmul(*q, bs[e % P]);
+  }
+  __syncthreads();
+  fft_dit<V>(sm, A.logP, CP, lds, tw, 2);
+  const double scale = 1.0 / sqrt(2.0 * (double)K);
+  if (fwd) {
+    V* z = (V*)A.z;
+    for (int64_t e = threadIdx.x; e < P2 * C; e += blockDim.x) {
+      const int64_t p = e / C;
+      const int c = (int)(e % C);
+      const int64_t n = col0 + c;
+      if (n >= A.ncols) continue;
+      const V* col = sm + (c >> 1) * lds;
+      const int m1 = (int)(2 * p + 1), m2 = m1 + 1;
+      const V y1 = cmul(col[m1], chirp[m1]);
+      const T v1 = (c & 1) ? y1.x : -y1.y;
+      T v2 = (T)0;
+      if (m2 <= M) {
+        const V y2 = cmul(col[m2], chirp[m2]);
+        v2 = (c & 1) ? y2.x : -y2.y;
+      }
+      const int64_t nout = (A.reverse && n < N) ? N - 1 - n : n;
+      z[p * A.ld + nout] = mkv((T)(v1 * (T)scale), (T)(v2 * (T)scale));
+    }
+  } else {
+    for (int64_t e = threadIdx.x; e < M * C; e += blockDim.x) {
+      const int64_t j = e / C;
+      const int c = (int)(e % C);
+      const int64_t n = col0 + c;
+      if (n >= N) continue;
+      const V y = cmul(sm[(c >> 1) * lds + (int)j + 1], chirp[j + 1]);
+      const double v = (double)((c & 1) ? y.x : -y.y) * scale;
+      double* dst = A.u + j * N + n;
+      *dst = A.accumulate ? *dst + v : v;
+    }
+  }
+}
+
+template <typename T>
+int bluestein_cols(int logP) {
+  const size_t per_pair = ((size_t)(1 << logP) + 1) * sizeof(Vt<T>);
+  int C = 4;
+  while (C > 2 && (size_t)(C / 2) * per_pair > 160 * 1024) C >>= 1;
+  return C;
+}
+
 template <typename T>
 int dst_cols(int logK2) {
   // columns per block: as many as fit (even, <= 8) in ~160 KB of shared memory
@@ -210,6 +329,13 @@ int dst_cols(int logK2) {
 
 template <typename T>
 void dst_launch(const DstArgs& a, bool fwd, cudaStream_t st) {
+  if (a.space && a.bluestein) {
+    const int C = bluestein_cols<T>(a.logP);
+    const size_t smem = (size_t)(C / 2) * ((size_t)(1 << a.logP) + 1) * sizeof(Vt<T>);
+    set_smem((const void*)dst_bluestein_kernel<T>, smem);
+    dst_bluestein_kernel<T><<<(unsigned)((a.ncols + C - 1) / C), kThreads, smem, st>>>(a, C, fwd ? 1 : 0);
+    return;
+  }
   int C = a.space ? dst_cols<T>(a.logK2) : 8;
   size_t smem = a.space ? (size_t)(C / 2) * ((size_t)(1 << a.logK2) + 1) * sizeof(Vt<T>) : 0;
   dim3 grid((unsigned)((a.ncols + C - 1) / C));
@@ -594,6 +720,7 @@ void conv_launch(const ConvArgs& a, cudaStream_t st) {
 }  // namespace
 
 int nsmem_for(Prec prec) { return prec == P64 ? 4096 : 8192; }
+int bluestein_max_K(Prec prec) { return prec == P64 ? 2048 : 4096; }
 
 int launch_dst_forward(Prec prec, const DstArgs& a, cudaStream_t st) {
   if (prec == P64) dst_launch<double>(a, true, st); else dst_launch<float>(a, true, st);

@@ -72,6 +72,20 @@ def test_fp64_random_rhs(ft, oracle, kind, gamma, M, N, tune):
     assert _rel(u, ref) < 1e-12
 
 
+@pytest.mark.parametrize("kind,gamma,M,N,prec", [
+    (0, 0.7, 100, 700, 0),    # M+1 = 101 (prime): chirp-z sine transform
+    (1, 1.5, 62, 500, 0),     # M+1 = 63
+    (0, 0.4, 2, 300, 0),      # M+1 = 3, smallest odd size
+    (0, 0.8, 200, 1200, 1),   # mixed, M+1 = 201
+    (1, 1.8, 2046, 150, 1),   # mixed, M+1 = 2047 = 23*89, P = 8192
+])
+def test_sine_transform_any_size(ft, oracle, kind, gamma, M, N, prec):
+    f = wl.random_field((M, N), seed=M + 7 * N)
+    ref = oracle.march(kind, 1, gamma, f)
+    u = _solve_gpu(ft, kind, gamma, f, precision=prec)
+    assert _rel(u, ref) < (1e-12 if prec == 0 else 1e-6)
+
+
 def test_fp64_four_step_levels(ft, oracle):
     """N = 9000 -> padded 16384: levels s = 4096 use the four-step convolution."""
     M, N = 3, 9000
