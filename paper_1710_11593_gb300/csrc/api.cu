@@ -1,13 +1,16 @@
-// C ABI of libftoep (include/ftoep.h): plans, workspace, and the order of the kernels.
+// C ABI of libftoep (include/ftoep.h): plans, workspaces, streams and the order of the
+// kernels.
 //
-// ftoep_solve, double precision, per problem:
-//   1. sine transform along space of f (+ initial-data terms)  -> pairs of modes z[P][Np]
+// ftoep_solve, per problem (difference form, see solve_problem):
+//   1. right-hand side + sine transform along space      -> mode pairs z[P][Np]
 //   2. per time block of length B: in-block half-split solve; then the one cross-block
 //      update that becomes due (level s = B * 2^ctz(block+1)) as a circulant convolution
-//   3. inverse sine transform -> u
-// ftoep_solve, mixed: steps 1-3 with float transforms/convolutions (double leaves),
-//   then r = f - A u in double (Toeplitz product by a double FFT of length 2Np, exact
-//   three-point stencil), steps 1-3 on r, u += correction.
+//   3. inverse sine transform, u = u0 + tau * cumsum(v)
+//   mixed precision: 1-3 in float (double leaves and running sums), then the residual of
+//   the original form in double, 1-3 on it, u += correction.
+// A plan with several problems runs them on up to kMaxStreams internal streams (longest
+// first, each onto the least-loaded stream), each stream with its own workspace; the
+// caller's stream forks to them and joins them again through events.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -23,6 +26,10 @@ using namespace ftoep;
 
 namespace {
 
+constexpr int kMaxStreams = 4;
+constexpr int kNumClasses = 5;
+constexpr int kDotBlocks = 1024;
+
 struct Prob {
   ftoep_problem d{};
   int64_t N = 0, M = 0, Np = 0, P = 0;
@@ -32,6 +39,8 @@ struct Prob {
   int64_t ncols = 0;
   Prec prec = P64;
   int64_t foff = 0, voff = 0;
+  int stream = 0;               // internal stream the problem runs on
+  double cost = 0;              // scheduling estimate
   std::vector<double> h_a, h_dadg;
   double* a = nullptr;          // first column of the time operator (original form)
   double* dadg = nullptr;       // its derivative in gamma
@@ -51,6 +60,26 @@ struct Prob {
   double2* spec64 = nullptr;    // solve spectra in double (adjoint of mixed problems; == spec for P64)
   double2* spec_mv = nullptr;   // product spectrum, length 2Np
   double2* spec_dg = nullptr;   // d/dgamma product spectrum
+};
+
+// One stream's workspace.
+struct Ws {
+  cudaStream_t st = nullptr;
+  bool own = false;
+  void* z = nullptr;             // solve pairs (max P*Np double2)
+  void* scratch = nullptr;       // four-step scratch of the solve (max P*Np double2)
+  double2* zmv = nullptr;        // product pairs (max P*Np double2)
+  double2* scratch_mv = nullptr; // four-step scratch of products (max P*2Np double2)
+  double* r = nullptr;           // residual / temporary field (max M*N)
+  double2* prefix = nullptr;     // running sums of the difference-form solve (max P)
+  double* dpart = nullptr;       // reduction partials
+  // host-pointer staging (per problem, allocated on first use)
+  double* stage_in = nullptr;
+  double* stage_out = nullptr;
+  double* stage_v0 = nullptr;
+  double* stage_v1 = nullptr;
+  double* stage_u = nullptr;
+  cudaEvent_t done = nullptr;
 };
 
 int ilog2(int64_t v) {
@@ -79,36 +108,23 @@ void set_global_error(const char* msg) { g_create_error = msg; }
 
 struct ftoep_plan_s {
   std::vector<Prob> probs;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;  // caller's stream
   int device = 0;
   int64_t ntw = 0;
   double2* tw64 = nullptr;
   float2* tw32 = nullptr;
-  // workspace
-  void* z = nullptr;            // solve pairs (max P*Np of double2)
-  void* scratch = nullptr;      // four-step scratch of the solve (max P*Np of double2)
-  double2* zmv = nullptr;       // product pairs (max P*Np double2)
-  double2* scratch_mv = nullptr;// four-step scratch of products (max P*2Np double2)
-  double* r = nullptr;          // residual / temporary field (max M*N)
-  double2* prefix = nullptr;    // running sums of the difference-form solve (max P)
-  size_t prefix_elems = 0;
-  double* dpart = nullptr;      // reduction partials
-  double* dscal = nullptr;      // device scalars (nprob)
-  size_t z_elems = 0, mv_elems = 0, r_elems = 0;
-  // host staging
-  double* stage_in = nullptr;
-  double* stage_out = nullptr;
-  double* stage_v0 = nullptr;
-  double* stage_v1 = nullptr;
-  size_t stage_elems = 0, stagev_elems = 0;
+  std::vector<Ws> ws;
+  size_t z_el = 0, mv_el = 0, r_el = 0, p_el = 0, v_el = 0;
+  double* dscal = nullptr;        // device scalars (nprob)
+  cudaEvent_t fork = nullptr;
   int64_t total_field = 0, total_vec = 0;
   std::string err;
   std::vector<void*> allocs;
   // launch counters (always on) and optional CUDA-event timing per kernel class
   bool prof_on = false;
-  int64_t launches[5] = {0, 0, 0, 0, 0};
-  double prof_ms[5] = {0, 0, 0, 0, 0};
-  int64_t prof_ops[5] = {0, 0, 0, 0, 0};
+  int64_t launches[kNumClasses] = {0, 0, 0, 0, 0};
+  double prof_ms[kNumClasses] = {0, 0, 0, 0, 0};
+  int64_t prof_ops[kNumClasses] = {0, 0, 0, 0, 0};
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
   std::vector<cudaEvent_t> evpool;
 };
@@ -164,18 +180,19 @@ cudaEvent_t ev_get(ftoep_plan pl) {
   return e;
 }
 
-// Launch through a launcher returning its kernel count; count it, optionally time it.
+// Launch on stream `st` (in scope) through a launcher that returns its kernel count;
+// count it, optionally time it with a pair of events on the same stream.
 #define LAUNCH(cls, expr)                                            \
   do {                                                               \
     cudaEvent_t e0_ = nullptr, e1_ = nullptr;                        \
     if (pl->prof_on) {                                               \
       e0_ = ev_get(pl);                                              \
       e1_ = ev_get(pl);                                              \
-      cudaEventRecord(e0_, pl->stream);                              \
+      cudaEventRecord(e0_, st);                                      \
     }                                                                \
     pl->launches[(cls)] += (expr);                                   \
     if (pl->prof_on) {                                               \
-      cudaEventRecord(e1_, pl->stream);                              \
+      cudaEventRecord(e1_, st);                                      \
       pl->pending.push_back({(cls), {e0_, e1_}});                    \
     }                                                                \
     CKL();                                                           \
@@ -205,6 +222,17 @@ bool is_device_ptr(const void* ptr) {
 
 const void* tw_of(ftoep_plan pl, Prec pr) { return pr == P64 ? (const void*)pl->tw64 : (const void*)pl->tw32; }
 size_t velem(Prec pr) { return pr == P64 ? sizeof(double2) : sizeof(float2); }
+
+void release(ftoep_plan pl, void* ptr) {
+  if (!ptr) return;
+  for (auto it = pl->allocs.begin(); it != pl->allocs.end(); ++it) {
+    if (*it == ptr) {
+      cudaFree(ptr);
+      pl->allocs.erase(it);
+      return;
+    }
+  }
+}
 
 ftoep_status validate(const ftoep_problem& d, int i, const ftoep_tuning* tune) {
   ftoep_plan pl = nullptr;
@@ -244,7 +272,8 @@ ftoep_status validate(const ftoep_problem& d, int i, const ftoep_tuning* tune) {
 }
 
 // Spectra of the solve levels s = Sf .. Np/2 (level s at offset 2(s - Sf)).
-ftoep_status build_solve_spectra(ftoep_plan pl, Prob& pb, Prec pr, void* out) {
+ftoep_status build_solve_spectra(ftoep_plan pl, Ws& w, Prob& pb, Prec pr, void* out) {
+  cudaStream_t st = w.st;
   for (int64_t s = pb.Sf; s <= pb.Np / 2; s <<= 1) {
     SpecArgs sa{};
     sa.a = pb.e;
@@ -254,15 +283,16 @@ ftoep_status build_solve_spectra(ftoep_plan pl, Prob& pb, Prec pr, void* out) {
     sa.nsmem = nsmem_for(pr);
     sa.out = (char*)out + (size_t)2 * (s - pb.Sf) * velem(pr);
     sa.tw64 = pl->tw64;
-    sa.scratch64 = pl->scratch_mv;
-    LAUNCH(FTOEP_K_OTHER, launch_spectrum(pr, sa, pl->stream));
+    sa.scratch64 = w.scratch_mv;
+    LAUNCH(FTOEP_K_OTHER, launch_spectrum(pr, sa, st));
   }
   return FTOEP_OK;
 }
 
-// Spectrum of the full product y = T x (c_k = a_k for k < N, zero after), length 2Np.
-ftoep_status build_product_spectrum(ftoep_plan pl, Prob& pb, const double* coeff, double2** out) {
+// Spectrum of the full product y = T x (c_k = coeff_k for k < N, zero after), length 2Np.
+ftoep_status build_product_spectrum(ftoep_plan pl, Ws& w, Prob& pb, const double* coeff, double2** out) {
   if (*out) return FTOEP_OK;
+  cudaStream_t st = w.st;
   ALLOC(*out, (size_t)2 * pb.Np * sizeof(double2));
   SpecArgs sa{};
   sa.a = coeff;
@@ -272,15 +302,15 @@ ftoep_status build_product_spectrum(ftoep_plan pl, Prob& pb, const double* coeff
   sa.nsmem = nsmem_for(P64);
   sa.out = *out;
   sa.tw64 = pl->tw64;
-  sa.scratch64 = pl->scratch_mv;
-  LAUNCH(FTOEP_K_OTHER, launch_spectrum(P64, sa, pl->stream));
+  sa.scratch64 = w.scratch_mv;
+  LAUNCH(FTOEP_K_OTHER, launch_spectrum(P64, sa, st));
   return FTOEP_OK;
 }
 
-// In-place solve of the pair array z (right-hand side in, solution out).
-ftoep_status solve_pairs(ftoep_plan pl, Prob& pb, Prec pr, void* z, const void* spec) {
-  cudaStream_t st = pl->stream;
-  CK(cudaMemsetAsync(pl->prefix, 0, (size_t)pb.P * sizeof(double2), st));
+// In-place difference-form solve of the pair array z (right-hand side in, v out).
+ftoep_status solve_pairs(ftoep_plan pl, Ws& w, Prob& pb, Prec pr, void* z, const void* spec) {
+  cudaStream_t st = w.st;
+  CK(cudaMemsetAsync(w.prefix, 0, (size_t)pb.P * sizeof(double2), st));
   for (int b = 0; b < pb.nblk; ++b) {
     BlockArgs ba{};
     ba.z = z;
@@ -293,7 +323,7 @@ ftoep_status solve_pairs(ftoep_plan pl, Prob& pb, Prec pr, void* z, const void* 
     ba.a = pb.e;
     ba.invdiag = pb.invdiag;
     ba.lamtau = pb.lamtau;
-    ba.prefix = pl->prefix;
+    ba.prefix = w.prefix;
     ba.spec = spec;
     ba.tw = tw_of(pl, pr);
     LAUNCH(FTOEP_K_BLOCK_SOLVE, launch_block_solve(pr, ba, st));
@@ -313,14 +343,14 @@ ftoep_status solve_pairs(ftoep_plan pl, Prob& pb, Prec pr, void* z, const void* 
       ca.mode = 0;
       ca.spec = (const char*)spec + (size_t)2 * (s - pb.Sf) * velem(pr);
       ca.tw = tw_of(pl, pr);
-      ca.scratch = pl->scratch;
+      ca.scratch = w.scratch;
       LAUNCH((2 * s <= nsmem_for(pr)) ? FTOEP_K_CONV_SMEM : FTOEP_K_CONV_FOURSTEP, launch_conv(pr, ca, st));
     }
   }
   return FTOEP_OK;
 }
 
-DstArgs dst_args(ftoep_plan pl, Prob& pb, Prec pr, void* z) {
+DstArgs dst_args(ftoep_plan pl, const Prob& pb, Prec pr, void* z) {
   DstArgs da{};
   da.z = z;
   da.ld = pb.Np;
@@ -343,20 +373,20 @@ DstArgs dst_args(ftoep_plan pl, Prob& pb, Prec pr, void* z) {
 }
 
 // y = T x on nlines lines of length N (double), through the product workspace.
-ftoep_status product_lines(ftoep_plan pl, Prob& pb, const double2* spec, const double* x, double* y_or_null,
-                           int64_t nlines, int reverse, double2* out_pairs) {
-  cudaStream_t st = pl->stream;
+ftoep_status product_lines(ftoep_plan pl, Ws& w, Prob& pb, const double2* spec, const double* x, double* y_or_null,
+                           int64_t nlines, int reverse) {
+  cudaStream_t st = w.st;
   PackArgs pa{};
   pa.x = x;
-  pa.z = out_pairs;
+  pa.z = w.zmv;
   pa.ld = pb.Np;
   pa.N = pb.N;
   pa.nlines = nlines;
   pa.reverse = reverse;
   LAUNCH(FTOEP_K_OTHER, launch_pack(P64, pa, st));
   ConvArgs ca{};
-  ca.zin = out_pairs;
-  ca.zout = out_pairs;
+  ca.zin = w.zmv;
+  ca.zout = w.zmv;
   ca.ld_in = ca.ld_out = pb.Np;
   ca.in_off = ca.out_off = 0;
   ca.npairs = (nlines + 1) / 2;
@@ -365,7 +395,7 @@ ftoep_status product_lines(ftoep_plan pl, Prob& pb, const double2* spec, const d
   ca.mode = 1;
   ca.spec = spec;
   ca.tw = pl->tw64;
-  ca.scratch = pl->scratch_mv;
+  ca.scratch = w.scratch_mv;
   LAUNCH((2 * pb.Np <= nsmem_for(P64)) ? FTOEP_K_CONV_SMEM : FTOEP_K_CONV_FOURSTEP, launch_conv(P64, ca, st));
   if (y_or_null) {
     pa.y = y_or_null;
@@ -375,9 +405,10 @@ ftoep_status product_lines(ftoep_plan pl, Prob& pb, const double2* spec, const d
   return FTOEP_OK;
 }
 
-// Scan of the solved difference quotients into u (u = u0 + tau * cumsum(v)).
-ftoep_status scan_lines(ftoep_plan pl, Prob& pb, const double* in, double* out, const double* u0, int accumulate,
+// Time sums along every line: u = base + tau * cumsum(in) (or tau * suffix sums).
+ftoep_status scan_lines(ftoep_plan pl, Ws& w, Prob& pb, const double* in, double* out, const double* u0, int accumulate,
                         int reverse) {
+  cudaStream_t st = w.st;
   ScanArgs sc{};
   sc.in = in;
   sc.out = out;
@@ -387,7 +418,7 @@ ftoep_status scan_lines(ftoep_plan pl, Prob& pb, const double* in, double* out, 
   sc.tau = pb.tau;
   sc.accumulate = accumulate;
   sc.reverse = reverse;
-  LAUNCH(FTOEP_K_OTHER, launch_scan(sc, pl->stream));
+  LAUNCH(FTOEP_K_OTHER, launch_scan(sc, st));
   return FTOEP_OK;
 }
 
@@ -396,10 +427,11 @@ ftoep_status scan_lines(ftoep_plan pl, Prob& pb, const double* in, double* out, 
 // lower triangle) with right-hand side f + [c tau M_{n-1} phi] - S u0, and
 // u = u0 + tau cumsum(v).  Written in v the history terms carry the scale tau^(1-g)
 // instead of tau^-g, which keeps float arithmetic usable at large N.
-ftoep_status solve_problem(ftoep_plan pl, Prob& pb, const double* f, double* u, const double* u0, const double* phi) {
-  cudaStream_t st = pl->stream;
+ftoep_status solve_problem(ftoep_plan pl, Ws& w, Prob& pb, const double* f, double* u, const double* u0,
+                           const double* phi) {
+  cudaStream_t st = w.st;
   const Prec pr = pb.prec;
-  DstArgs da = dst_args(pl, pb, pr, pl->z);
+  DstArgs da = dst_args(pl, pb, pr, w.z);
   da.f = f;
   da.u0 = u0;
   da.phi = (pb.d.kind == FTOEP_L1_HYPERBOLIC) ? phi : nullptr;
@@ -407,15 +439,14 @@ ftoep_status solve_problem(ftoep_plan pl, Prob& pb, const double* f, double* u, 
   da.wphi = pb.wphi;
   da.diff_form = 1;
   LAUNCH(FTOEP_K_SINE, launch_dst_forward(pr, da, st));
-  TRY(solve_pairs(pl, pb, pr, pl->z, pb.spec));
+  TRY(solve_pairs(pl, w, pb, pr, w.z, pb.spec));
   da.u = u;
   da.accumulate = 0;
   LAUNCH(FTOEP_K_SINE, launch_dst_inverse(pr, da, st));
-  TRY(scan_lines(pl, pb, u, u, u0, 0, 0));
+  TRY(scan_lines(pl, w, pb, u, u, u0, 0, 0));
   if (pr == P64) return FTOEP_OK;
   // residual of the original form in double: r = f + init - T u - S u
-  TRY(build_product_spectrum(pl, pb, pb.a, &pb.spec_mv));
-  TRY(product_lines(pl, pb, pb.spec_mv, u, nullptr, pb.M, 0, pl->zmv));
+  TRY(product_lines(pl, w, pb, pb.spec_mv, u, nullptr, pb.M, 0));
   ResidualArgs ra{};
   ra.f = f;
   ra.u0 = u0;
@@ -423,8 +454,8 @@ ftoep_status solve_problem(ftoep_plan pl, Prob& pb, const double* f, double* u, 
   ra.wu0 = pb.wu0;
   ra.wphi = pb.wphi;
   ra.u = u;
-  ra.tu = pl->zmv;
-  ra.r = pl->r;
+  ra.tu = w.zmv;
+  ra.r = w.r;
   ra.ld = pb.Np;
   ra.N = pb.N;
   ra.M = pb.M;
@@ -433,24 +464,70 @@ ftoep_status solve_problem(ftoep_plan pl, Prob& pb, const double* f, double* u, 
   ra.lambda = pb.d.lambda;
   LAUNCH(FTOEP_K_OTHER, launch_residual(ra, st));
   // correction: same rows, zero initial data; v-correction lands in r, then u += tau cumsum
-  DstArgs dr = dst_args(pl, pb, pr, pl->z);
-  dr.f = pl->r;
+  DstArgs dr = dst_args(pl, pb, pr, w.z);
+  dr.f = w.r;
   dr.diff_form = 1;
   LAUNCH(FTOEP_K_SINE, launch_dst_forward(pr, dr, st));
-  TRY(solve_pairs(pl, pb, pr, pl->z, pb.spec));
-  dr.u = pl->r;
+  TRY(solve_pairs(pl, w, pb, pr, w.z, pb.spec));
+  dr.u = w.r;
   dr.accumulate = 0;
   LAUNCH(FTOEP_K_SINE, launch_dst_inverse(pr, dr, st));
-  TRY(scan_lines(pl, pb, pl->r, u, nullptr, 1, 0));
+  TRY(scan_lines(pl, w, pb, w.r, u, nullptr, 1, 0));
   return FTOEP_OK;
 }
 
-ftoep_status ensure_staging(ftoep_plan pl) {
-  if (pl->stage_in) return FTOEP_OK;
-  ALLOC(pl->stage_in, (size_t)pl->total_field * sizeof(double));
-  ALLOC(pl->stage_out, (size_t)pl->total_field * sizeof(double));
-  ALLOC(pl->stage_v0, (size_t)pl->total_vec * sizeof(double));
-  ALLOC(pl->stage_v1, (size_t)pl->total_vec * sizeof(double));
+// Adjoint of one problem (double): dldf = A_u^-T g and, if dgamma_out, the partial
+// <dldf, (dA/dgamma) u> into *dgamma_out (device).
+ftoep_status adjoint_problem(ftoep_plan pl, Ws& w, Prob& pb, const double* g, const double* u, double* dldf,
+                             double* dgamma_out) {
+  cudaStream_t st = w.st;
+  if (pb.bluestein && pb.M + 1 > bluestein_max_K(P64))
+    return fail(pl, FTOEP_EUNSUPPORTED, "adjoint: M+1 = %lld > %d needs a double sine transform that is not built",
+                (long long)(pb.M + 1), bluestein_max_K(P64));
+  // The double-precision block parameters (fixed defaults for mixed problems).
+  Prob q = pb;
+  if (pb.prec != P64) {
+    q.prec = P64;
+    q.B = (int)std::min<int64_t>(1024, pb.Np);
+    q.L = std::min(16, q.B);
+    q.nblk = (int)((pb.N + q.B - 1) / q.B);
+    q.ncols = (int64_t)q.nblk * q.B;
+  }
+  // With u = tau C v (C the all-ones lower triangle), A_u = A_v (tau C)^-1, so
+  // A_u^-T g = A_v^-T (tau C^T g): suffix sums of g, then the transposed difference-form
+  // solve, done as time reversal + forward solve + reversal (J A_v^T J = A_v per mode).
+  TRY(scan_lines(pl, w, pb, g, w.r, nullptr, 0, 1));
+  DstArgs da = dst_args(pl, q, P64, w.z);
+  da.f = w.r;
+  da.reverse = 1;
+  LAUNCH(FTOEP_K_SINE, launch_dst_forward(P64, da, st));
+  TRY(solve_pairs(pl, w, q, P64, w.z, pb.spec64));
+  da.u = dldf;
+  da.accumulate = 0;
+  LAUNCH(FTOEP_K_SINE, launch_dst_inverse(P64, da, st));
+  if (dgamma_out) {
+    TRY(product_lines(pl, w, pb, pb.spec_dg, u, nullptr, pb.M, 0));
+    DotArgs dt{};
+    dt.x = dldf;
+    dt.tu = w.zmv;
+    dt.ld = pb.Np;
+    dt.N = pb.N;
+    dt.nlines = pb.M;
+    dt.partial = w.dpart;
+    dt.nblocks = kDotBlocks;
+    LAUNCH(FTOEP_K_OTHER, launch_dot(dt, st));
+    LAUNCH(FTOEP_K_OTHER, launch_sum(w.dpart, kDotBlocks, dgamma_out, st));
+  }
+  return FTOEP_OK;
+}
+
+ftoep_status ensure_staging(ftoep_plan pl, Ws& w) {
+  if (w.stage_in) return FTOEP_OK;
+  ALLOC(w.stage_in, pl->r_el * sizeof(double));
+  ALLOC(w.stage_out, pl->r_el * sizeof(double));
+  ALLOC(w.stage_u, pl->r_el * sizeof(double));
+  ALLOC(w.stage_v0, pl->v_el * sizeof(double));
+  ALLOC(w.stage_v1, pl->v_el * sizeof(double));
   return FTOEP_OK;
 }
 
@@ -460,6 +537,23 @@ ftoep_status sync_plan(ftoep_plan pl) {
   return FTOEP_OK;
 }
 
+// Make the internal streams wait for the caller's stream.
+ftoep_status fork_streams(ftoep_plan pl) {
+  if (pl->ws.size() == 1 && !pl->ws[0].own) return FTOEP_OK;
+  CK(cudaEventRecord(pl->fork, pl->stream));
+  for (auto& w : pl->ws) CK(cudaStreamWaitEvent(w.st, pl->fork, 0));
+  return FTOEP_OK;
+}
+
+// Make the caller's stream wait for the internal streams.
+ftoep_status join_streams(ftoep_plan pl) {
+  if (pl->ws.size() == 1 && !pl->ws[0].own) return FTOEP_OK;
+  for (auto& w : pl->ws) {
+    CK(cudaEventRecord(w.done, w.st));
+    CK(cudaStreamWaitEvent(pl->stream, w.done, 0));
+  }
+  return FTOEP_OK;
+}
 
 // Bluestein tables for the sine transform of a problem with K = M+1 not a power of two:
 // chirp c_n = exp(-i pi n^2 / L) (L = 2K, n^2 reduced mod 2L exactly) and the forward
@@ -493,8 +587,8 @@ ftoep_status build_bluestein(ftoep_plan pl, Prob& pb) {
     for (int64_t i = 0; i < half; ++i) {
       const long double a = -2.0L * pi * (long double)i / (long double)len;
       const long double wr = cosl(a), wi = sinl(a);
-      for (int64_t st = 0; st < P; st += len) {
-        const int64_t x = st + i, y = st + i + half;
+      for (int64_t s0 = 0; s0 < P; s0 += len) {
+        const int64_t x = s0 + i, y = s0 + i + half;
         const long double ur = br[x], ui = bi[x], vr = br[y], vi = bi[y];
         br[x] = ur + vr;
         bi[x] = ui + vi;
@@ -526,6 +620,55 @@ ftoep_status build_bluestein(ftoep_plan pl, Prob& pb) {
   return FTOEP_OK;
 }
 
+ftoep_status setup_problem(ftoep_plan pl, Prob& pb) {
+  const int64_t N = pb.N, Np = pb.Np;
+  pb.h_a.resize(Np);
+  pb.h_dadg.resize(Np);
+  scheme_weights(pb.d.kind, pb.d.gamma, pb.tau, Np, pb.h_a.data(), pb.h_dadg.data());
+  std::vector<double> wu0(N), wphi(N), he(Np);
+  initial_weights(pb.d.kind, pb.d.gamma, pb.tau, N, wu0.data(), wphi.data());
+  difference_weights(pb.d.kind, pb.d.gamma, pb.tau, Np, he.data());
+  std::vector<double2> invd(pb.P), lt(pb.P);
+  for (int64_t p = 0; p < pb.P; ++p) {
+    double lam[2];
+    for (int q = 0; q < 2; ++q) {
+      const int64_t m = 2 * p + q + 1;
+      if (pb.d.space) {
+        const double sn = std::sin((double)m * 3.14159265358979323846 / (2.0 * (double)(pb.M + 1)));
+        lam[q] = 4.0 / (pb.h * pb.h) * sn * sn;
+      } else {
+        lam[q] = pb.d.lambda;
+      }
+    }
+    invd[p] = make_double2(1.0 / (he[0] + lam[0] * pb.tau), 1.0 / (he[0] + lam[1] * pb.tau));
+    lt[p] = make_double2(lam[0] * pb.tau, lam[1] * pb.tau);
+  }
+  ALLOC(pb.a, Np * sizeof(double));
+  ALLOC(pb.dadg, Np * sizeof(double));
+  ALLOC(pb.e, Np * sizeof(double));
+  ALLOC(pb.wu0, N * sizeof(double));
+  ALLOC(pb.wphi, N * sizeof(double));
+  ALLOC(pb.invdiag, pb.P * sizeof(double2));
+  ALLOC(pb.lamtau, pb.P * sizeof(double2));
+  CK(cudaMemcpy(pb.a, pb.h_a.data(), Np * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(pb.dadg, pb.h_dadg.data(), Np * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(pb.e, he.data(), Np * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(pb.wu0, wu0.data(), N * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(pb.wphi, wphi.data(), N * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(pb.invdiag, invd.data(), pb.P * sizeof(double2), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(pb.lamtau, lt.data(), pb.P * sizeof(double2), cudaMemcpyHostToDevice));
+  if (pb.d.space && !is_pow2(pb.M + 1)) TRY(build_bluestein(pl, pb));
+  Ws& w = pl->ws[0];
+  const size_t nspec = pb.Sf <= Np / 2 ? (size_t)2 * (Np - pb.Sf) : 0;
+  if (nspec) {
+    ALLOC(pb.spec, nspec * velem(pb.prec));
+    TRY(build_solve_spectra(pl, w, pb, pb.prec, pb.spec));
+    if (pb.prec == P64) pb.spec64 = (double2*)pb.spec;
+  }
+  if (pb.prec == P32) TRY(build_product_spectrum(pl, w, pb, pb.a, &pb.spec_mv));
+  return FTOEP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -552,7 +695,6 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
   }
   int64_t maxtw = 8192;
   int64_t foff = 0, voff = 0;
-  size_t z_el = 0, mv_el = 0, r_el = 0;
   for (int i = 0; i < nprob; ++i) {
     Prob pb;
     pb.d = probs[i];
@@ -590,17 +732,55 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
       maxtw = std::max<int64_t>(maxtw, 2 * (pb.M + 1));
       if (!is_pow2(pb.M + 1)) maxtw = std::max<int64_t>(maxtw, int64_t(1) << ilog2(4 * (pb.M + 1) - 1));
     }
-    z_el = std::max<size_t>(z_el, (size_t)pb.P * np);
-    mv_el = std::max<size_t>(mv_el, (size_t)pb.P * np);
-    r_el = std::max<size_t>(r_el, (size_t)pb.M * pb.N);
-    pl->prefix_elems = std::max<size_t>(pl->prefix_elems, (size_t)pb.P);
+    pl->z_el = std::max<size_t>(pl->z_el, (size_t)pb.P * np);
+    pl->mv_el = std::max<size_t>(pl->mv_el, (size_t)pb.P * np);
+    pl->r_el = std::max<size_t>(pl->r_el, (size_t)pb.M * pb.N);
+    pl->p_el = std::max<size_t>(pl->p_el, (size_t)pb.P);
+    pl->v_el = std::max<size_t>(pl->v_el, (size_t)pb.M);
+    pb.cost = (double)pb.M * (double)np * (double)(pb.logNp + 1) * (double)(pb.logNp + 1);
     pl->probs.push_back(std::move(pb));
   }
   pl->total_field = foff;
   pl->total_vec = voff;
-  pl->z_elems = z_el;
-  pl->mv_elems = mv_el;
-  pl->r_elems = r_el;
+  // streams: the caller's stream for one problem, else up to kMaxStreams own streams,
+  // problems longest first onto the least-loaded one
+  const int nstreams = nprob == 1 ? 1 : std::min(nprob, kMaxStreams);
+  pl->ws.resize(nstreams);
+  for (int s = 0; s < nstreams; ++s) {
+    Ws& w = pl->ws[s];
+    if (nstreams == 1) {
+      w.st = pl->stream;
+    } else {
+      if (cudaStreamCreateWithFlags(&w.st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        pl->err = "stream creation failed";
+        return bail(FTOEP_ECUDA);
+      }
+      w.own = true;
+    }
+    if (cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      pl->err = "event creation failed";
+      return bail(FTOEP_ECUDA);
+    }
+  }
+  if (cudaEventCreateWithFlags(&pl->fork, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    pl->err = "event creation failed";
+    return bail(FTOEP_ECUDA);
+  }
+  {
+    std::vector<int> order(nprob);
+    for (int i = 0; i < nprob; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return pl->probs[x].cost > pl->probs[y].cost; });
+    std::vector<double> load(nstreams, 0.0);
+    for (int i : order) {
+      const int s = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      pl->probs[i].stream = s;
+      load[s] += pl->probs[i].cost;
+    }
+  }
   // twiddles: W_n^k for all n = 2 .. maxtw at offset n-2, from one long-double table
   {
     pl->ntw = maxtw;
@@ -629,69 +809,28 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
       return bail(FTOEP_ECUDA);
     }
   }
-  if ((st = dalloc(pl, &pl->z, z_el * sizeof(double2))) != FTOEP_OK) return bail(st);
-  if ((st = dalloc(pl, &pl->scratch, z_el * sizeof(double2))) != FTOEP_OK) return bail(st);
-  if ((st = dalloc(pl, (void**)&pl->zmv, mv_el * sizeof(double2))) != FTOEP_OK) return bail(st);
-  if ((st = dalloc(pl, (void**)&pl->scratch_mv, 2 * mv_el * sizeof(double2))) != FTOEP_OK) return bail(st);
-  if ((st = dalloc(pl, (void**)&pl->r, r_el * sizeof(double))) != FTOEP_OK) return bail(st);
-  if ((st = dalloc(pl, (void**)&pl->prefix, pl->prefix_elems * sizeof(double2))) != FTOEP_OK) return bail(st);
-  if ((st = dalloc(pl, (void**)&pl->dpart, 1024 * sizeof(double))) != FTOEP_OK) return bail(st);
-  if ((st = dalloc(pl, (void**)&pl->dscal, (size_t)nprob * sizeof(double))) != FTOEP_OK) return bail(st);
-  if (cudaMemsetAsync(pl->z, 0, z_el * sizeof(double2), pl->stream) != cudaSuccess) {
-    cudaGetLastError();
-    pl->err = "workspace clear failed";
-    return bail(FTOEP_ECUDA);
-  }
-  for (auto& pb : pl->probs) {
-    const int64_t N = pb.N, Np = pb.Np;
-    pb.h_a.resize(Np);
-    pb.h_dadg.resize(Np);
-    scheme_weights(pb.d.kind, pb.d.gamma, pb.tau, Np, pb.h_a.data(), pb.h_dadg.data());
-    std::vector<double> wu0(N), wphi(N), he(Np);
-    initial_weights(pb.d.kind, pb.d.gamma, pb.tau, N, wu0.data(), wphi.data());
-    difference_weights(pb.d.kind, pb.d.gamma, pb.tau, Np, he.data());
-    std::vector<double2> invd(pb.P), lt(pb.P);
-    for (int64_t p = 0; p < pb.P; ++p) {
-      double lam[2];
-      for (int q = 0; q < 2; ++q) {
-        const int64_t m = 2 * p + q + 1;
-        if (pb.d.space) {
-          const double sn = std::sin((double)m * 3.14159265358979323846 / (2.0 * (double)(pb.M + 1)));
-          lam[q] = 4.0 / (pb.h * pb.h) * sn * sn;
-        } else {
-          lam[q] = pb.d.lambda;
-        }
-      }
-      invd[p] = make_double2(1.0 / (he[0] + lam[0] * pb.tau), 1.0 / (he[0] + lam[1] * pb.tau));
-      lt[p] = make_double2(lam[0] * pb.tau, lam[1] * pb.tau);
-    }
-    if ((st = dalloc(pl, (void**)&pb.a, Np * sizeof(double))) != FTOEP_OK) return bail(st);
-    if ((st = dalloc(pl, (void**)&pb.dadg, Np * sizeof(double))) != FTOEP_OK) return bail(st);
-    if ((st = dalloc(pl, (void**)&pb.wu0, N * sizeof(double))) != FTOEP_OK) return bail(st);
-    if ((st = dalloc(pl, (void**)&pb.wphi, N * sizeof(double))) != FTOEP_OK) return bail(st);
-    if ((st = dalloc(pl, (void**)&pb.invdiag, pb.P * sizeof(double2))) != FTOEP_OK) return bail(st);
-    if ((st = dalloc(pl, (void**)&pb.lamtau, pb.P * sizeof(double2))) != FTOEP_OK) return bail(st);
-    if ((st = dalloc(pl, (void**)&pb.e, Np * sizeof(double))) != FTOEP_OK) return bail(st);
-    if (cudaMemcpy(pb.a, pb.h_a.data(), Np * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(pb.dadg, pb.h_dadg.data(), Np * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(pb.wu0, wu0.data(), N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(pb.wphi, wphi.data(), N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(pb.invdiag, invd.data(), pb.P * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(pb.lamtau, lt.data(), pb.P * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(pb.e, he.data(), Np * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+  for (auto& w : pl->ws) {
+    if ((st = dalloc(pl, &w.z, pl->z_el * sizeof(double2))) != FTOEP_OK) return bail(st);
+    if ((st = dalloc(pl, &w.scratch, pl->z_el * sizeof(double2))) != FTOEP_OK) return bail(st);
+    if ((st = dalloc(pl, (void**)&w.zmv, pl->mv_el * sizeof(double2))) != FTOEP_OK) return bail(st);
+    if ((st = dalloc(pl, (void**)&w.scratch_mv, 2 * pl->mv_el * sizeof(double2))) != FTOEP_OK) return bail(st);
+    if ((st = dalloc(pl, (void**)&w.r, pl->r_el * sizeof(double))) != FTOEP_OK) return bail(st);
+    if ((st = dalloc(pl, (void**)&w.prefix, pl->p_el * sizeof(double2))) != FTOEP_OK) return bail(st);
+    if ((st = dalloc(pl, (void**)&w.dpart, kDotBlocks * sizeof(double))) != FTOEP_OK) return bail(st);
+    if (cudaMemsetAsync(w.z, 0, pl->z_el * sizeof(double2), w.st) != cudaSuccess) {
       cudaGetLastError();
-      pl->err = "weight upload failed";
+      pl->err = "workspace clear failed";
       return bail(FTOEP_ECUDA);
     }
-    if (pb.d.space && !is_pow2(pb.M + 1) && (st = build_bluestein(pl, pb)) != FTOEP_OK) return bail(st);
-    const size_t nspec = pb.Sf <= Np / 2 ? (size_t)2 * (Np - pb.Sf) : 0;
-    if (nspec) {
-      if ((st = dalloc(pl, &pb.spec, nspec * velem(pb.prec))) != FTOEP_OK) return bail(st);
-      if ((st = build_solve_spectra(pl, pb, pb.prec, pb.spec)) != FTOEP_OK) return bail(st);
-      if (pb.prec == P64) pb.spec64 = (double2*)pb.spec;
-    }
   }
-  if ((st = sync_plan(pl)) != FTOEP_OK) return bail(st);
+  if ((st = dalloc(pl, (void**)&pl->dscal, (size_t)nprob * sizeof(double))) != FTOEP_OK) return bail(st);
+  for (auto& pb : pl->probs)
+    if ((st = setup_problem(pl, pb)) != FTOEP_OK) return bail(st);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    pl->err = "plan set-up failed";
+    return bail(FTOEP_ECUDA);
+  }
   *out = pl;
   return FTOEP_OK;
 }
@@ -713,28 +852,34 @@ ftoep_status ftoep_solve(ftoep_plan pl, const double* f, double* u, const double
   if ((const char*)f < (const char*)u + fb && (const char*)u < (const char*)f + fb)
     return fail(pl, FTOEP_EINVAL, "f and u overlap");
   const bool host = !is_device_ptr(f) || !is_device_ptr(u) || !is_device_ptr(u0) || !is_device_ptr(phi);
-  const double *df = f, *du0 = u0, *dphi = phi;
-  double* du = u;
-  if (host) {
-    TRY(ensure_staging(pl));
-    CK(cudaMemcpyAsync(pl->stage_in, f, fb, cudaMemcpyDefault, pl->stream));
-    df = pl->stage_in;
-    du = pl->stage_out;
-    if (u0) {
-      CK(cudaMemcpyAsync(pl->stage_v0, u0, pl->total_vec * sizeof(double), cudaMemcpyDefault, pl->stream));
-      du0 = pl->stage_v0;
-    }
-    if (phi) {
-      CK(cudaMemcpyAsync(pl->stage_v1, phi, pl->total_vec * sizeof(double), cudaMemcpyDefault, pl->stream));
-      dphi = pl->stage_v1;
+  TRY(fork_streams(pl));
+  for (auto& pb : pl->probs) {
+    Ws& w = pl->ws[pb.stream];
+    cudaStream_t st = w.st;
+    const double* pf = f + pb.foff;
+    double* pu = u + pb.foff;
+    const double* pu0 = u0 ? u0 + pb.voff : nullptr;
+    const double* pphi = phi ? phi + pb.voff : nullptr;
+    if (host) {
+      TRY(ensure_staging(pl, w));
+      const size_t bytes = (size_t)pb.M * pb.N * sizeof(double);
+      CK(cudaMemcpyAsync(w.stage_in, pf, bytes, cudaMemcpyDefault, st));
+      if (pu0) {
+        CK(cudaMemcpyAsync(w.stage_v0, pu0, pb.M * sizeof(double), cudaMemcpyDefault, st));
+        pu0 = w.stage_v0;
+      }
+      if (pphi) {
+        CK(cudaMemcpyAsync(w.stage_v1, pphi, pb.M * sizeof(double), cudaMemcpyDefault, st));
+        pphi = w.stage_v1;
+      }
+      TRY(solve_problem(pl, w, pb, w.stage_in, w.stage_out, pu0, pphi));
+      CK(cudaMemcpyAsync(pu, w.stage_out, bytes, cudaMemcpyDefault, st));
+    } else {
+      TRY(solve_problem(pl, w, pb, pf, pu, pu0, pphi));
     }
   }
-  for (auto& pb : pl->probs)
-    TRY(solve_problem(pl, pb, df + pb.foff, du + pb.foff, du0 ? du0 + pb.voff : nullptr, dphi ? dphi + pb.voff : nullptr));
-  if (host) {
-    CK(cudaMemcpyAsync(u, du, fb, cudaMemcpyDefault, pl->stream));
-    TRY(sync_plan(pl));
-  }
+  TRY(join_streams(pl));
+  if (host) TRY(sync_plan(pl));
   return FTOEP_OK;
 }
 
@@ -743,13 +888,16 @@ ftoep_status ftoep_matvec(ftoep_plan pl, int iprob, const double* x, double* y, 
   if (iprob < 0 || iprob >= (int)pl->probs.size()) return fail(pl, FTOEP_EINVAL, "iprob out of range");
   if (!x || !y || nlines < 1) return fail(pl, FTOEP_EINVAL, "x, y must not be NULL and nlines >= 1");
   Prob& pb = pl->probs[iprob];
+  Ws& w = pl->ws[0];
   const size_t bytes = (size_t)nlines * pb.N * sizeof(double);
   if ((const char*)x < (const char*)y + bytes && (const char*)y < (const char*)x + bytes)
     return fail(pl, FTOEP_EINVAL, "x and y overlap");
-  TRY(build_product_spectrum(pl, pb, pb.a, &pb.spec_mv));
+  TRY(fork_streams(pl));
+  cudaStream_t st = w.st;
+  TRY(build_product_spectrum(pl, w, pb, pb.a, &pb.spec_mv));
   const bool host = !is_device_ptr(x) || !is_device_ptr(y);
   // lines per chunk: twice the pairs the product workspace holds
-  const int64_t chunk = 2 * (int64_t)(pl->mv_elems / pb.Np);
+  const int64_t chunk = 2 * (int64_t)(pl->mv_el / pb.Np);
   double *sx = nullptr, *sy = nullptr;
   if (host) {
     ALLOC(sx, (size_t)chunk * pb.N * sizeof(double));
@@ -760,25 +908,17 @@ ftoep_status ftoep_matvec(ftoep_plan pl, int iprob, const double* x, double* y, 
     const double* xin = x + l0 * pb.N;
     double* yout = y + l0 * pb.N;
     if (host) {
-      CK(cudaMemcpyAsync(sx, xin, nl * pb.N * sizeof(double), cudaMemcpyDefault, pl->stream));
+      CK(cudaMemcpyAsync(sx, xin, nl * pb.N * sizeof(double), cudaMemcpyDefault, st));
       xin = sx;
     }
-    TRY(product_lines(pl, pb, pb.spec_mv, xin, host ? sy : yout, nl, transpose ? 1 : 0, pl->zmv));
-    if (host) {
-      CK(cudaMemcpyAsync(yout, sy, nl * pb.N * sizeof(double), cudaMemcpyDefault, pl->stream));
-    }
+    TRY(product_lines(pl, w, pb, pb.spec_mv, xin, host ? sy : yout, nl, transpose ? 1 : 0));
+    if (host) CK(cudaMemcpyAsync(yout, sy, nl * pb.N * sizeof(double), cudaMemcpyDefault, st));
   }
+  TRY(join_streams(pl));
   if (host) {
     TRY(sync_plan(pl));
-    // release the per-call staging
-    for (auto it = pl->allocs.begin(); it != pl->allocs.end();) {
-      if (*it == sx || *it == sy) {
-        cudaFree(*it);
-        it = pl->allocs.erase(it);
-      } else {
-        ++it;
-      }
-    }
+    release(pl, sx);
+    release(pl, sy);
   }
   return FTOEP_OK;
 }
@@ -791,100 +931,65 @@ ftoep_status ftoep_adjoint(ftoep_plan pl, const double* g, const double* u, doub
   if ((const char*)g < (const char*)dldf + fb && (const char*)dldf < (const char*)g + fb)
     return fail(pl, FTOEP_EINVAL, "g and dldf overlap");
   const bool host = !is_device_ptr(g) || !is_device_ptr(dldf) || !is_device_ptr(u);
-  const double* dg = g;
-  const double* du = u;
-  double* dout = dldf;
-  double* su = nullptr;
-  if (host) {
-    TRY(ensure_staging(pl));
-    CK(cudaMemcpyAsync(pl->stage_in, g, fb, cudaMemcpyDefault, pl->stream));
-    dg = pl->stage_in;
-    dout = pl->stage_out;
-    if (u && dldgamma) {
-      ALLOC(su, fb);
-      CK(cudaMemcpyAsync(su, u, fb, cudaMemcpyDefault, pl->stream));
-      du = su;
+  // spectra needed by the double adjoint (built once, ordered before the solves on the
+  // caller's stream through the fork below)
+  {
+    Ws& w0 = pl->ws[0];
+    TRY(fork_streams(pl));
+    for (auto& pb : pl->probs) {
+      if (!pb.spec64 && pb.Sf <= pb.Np / 2) {
+        ALLOC(pb.spec64, (size_t)2 * (pb.Np - pb.Sf) * sizeof(double2));
+        TRY(build_solve_spectra(pl, w0, pb, P64, pb.spec64));
+      }
+      if (dldgamma) TRY(build_product_spectrum(pl, w0, pb, pb.dadg, &pb.spec_dg));
     }
+    TRY(join_streams(pl));
   }
-  cudaStream_t st = pl->stream;
+  TRY(fork_streams(pl));
   int ip = 0;
   for (auto& pb : pl->probs) {
-    if (!pb.spec64 && pb.Sf <= pb.Np / 2) {
-      ALLOC(pb.spec64, (size_t)2 * (pb.Np - pb.Sf) * sizeof(double2));
-      TRY(build_solve_spectra(pl, pb, P64, pb.spec64));
-    }
-    if (pb.bluestein && pb.M + 1 > bluestein_max_K(P64))
-      return fail(pl, FTOEP_EUNSUPPORTED, "adjoint: M+1 = %lld > %d needs a double sine transform that is not built",
-                  (long long)(pb.M + 1), bluestein_max_K(P64));
-    // The double-precision block parameters (fixed defaults for the adjoint).
-    Prob q = pb;
-    if (pb.prec != P64) {
-      q.prec = P64;
-      q.B = (int)std::min<int64_t>(1024, pb.Np);
-      q.L = std::min(16, q.B);
-      q.nblk = (int)((pb.N + q.B - 1) / q.B);
-      q.ncols = (int64_t)q.nblk * q.B;
-      if (q.Sf != pb.Sf) return fail(pl, FTOEP_EUNSUPPORTED, "adjoint: spectrum level mismatch");
-    }
-    // With u = tau C v (C the all-ones lower triangle), A_u = A_v (tau C)^-1, so
-    // A_u^-T g = A_v^-T (tau C^T g): suffix sums of g, then the transposed difference-form
-    // solve, done as time reversal + forward solve + reversal (J A_v^T J = A_v per mode).
-    TRY(scan_lines(pl, pb, dg + pb.foff, pl->r, nullptr, 0, 1));
-    DstArgs da = dst_args(pl, q, P64, pl->z);
-    da.f = pl->r;
-    da.reverse = 1;
-    LAUNCH(FTOEP_K_SINE, launch_dst_forward(P64, da, st));
-    TRY(solve_pairs(pl, q, P64, pl->z, pb.spec64));
-    da.u = dout + pb.foff;
-    da.accumulate = 0;
-    LAUNCH(FTOEP_K_SINE, launch_dst_inverse(P64, da, st));
-    if (dldgamma) {
-      TRY(build_product_spectrum(pl, pb, pb.dadg, &pb.spec_dg));
-      TRY(product_lines(pl, pb, pb.spec_dg, du + pb.foff, nullptr, pb.M, 0, pl->zmv));
-      DotArgs dt{};
-      dt.x = dout + pb.foff;
-      dt.tu = pl->zmv;
-      dt.ld = pb.Np;
-      dt.N = pb.N;
-      dt.nlines = pb.M;
-      dt.partial = pl->dpart;
-      dt.nblocks = 1024;
-      LAUNCH(FTOEP_K_OTHER, launch_dot(dt, st));
-      LAUNCH(FTOEP_K_OTHER, launch_sum(pl->dpart, 1024, pl->dscal + ip, st));
+    Ws& w = pl->ws[pb.stream];
+    cudaStream_t st = w.st;
+    const double* pg = g + pb.foff;
+    const double* pu = u ? u + pb.foff : nullptr;
+    double* pd = dldf + pb.foff;
+    if (host) {
+      TRY(ensure_staging(pl, w));
+      const size_t bytes = (size_t)pb.M * pb.N * sizeof(double);
+      CK(cudaMemcpyAsync(w.stage_in, pg, bytes, cudaMemcpyDefault, st));
+      if (pu && dldgamma) {
+        CK(cudaMemcpyAsync(w.stage_u, pu, bytes, cudaMemcpyDefault, st));
+        pu = w.stage_u;
+      }
+      TRY(adjoint_problem(pl, w, pb, w.stage_in, pu, w.stage_out, dldgamma ? pl->dscal + ip : nullptr));
+      CK(cudaMemcpyAsync(pd, w.stage_out, bytes, cudaMemcpyDefault, st));
+    } else {
+      TRY(adjoint_problem(pl, w, pb, pg, pu, pd, dldgamma ? pl->dscal + ip : nullptr));
     }
     ++ip;
   }
-  if (host) CK(cudaMemcpyAsync(dldf, dout, fb, cudaMemcpyDefault, st));
+  TRY(join_streams(pl));
   if (dldgamma) {
     std::vector<double> hs(pl->probs.size());
+    cudaStream_t st = pl->stream;
     CK(cudaMemcpyAsync(hs.data(), pl->dscal, hs.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     TRY(sync_plan(pl));
     for (size_t i = 0; i < hs.size(); ++i) dldgamma[i] = -hs[i];
   } else if (host) {
     TRY(sync_plan(pl));
   }
-  if (su) {
-    for (auto it = pl->allocs.begin(); it != pl->allocs.end();) {
-      if (*it == su) {
-        cudaFree(*it);
-        it = pl->allocs.erase(it);
-      } else {
-        ++it;
-      }
-    }
-  }
   return FTOEP_OK;
 }
 
 ftoep_status ftoep_profile(ftoep_plan pl, int enable) {
   if (!pl) return fail(nullptr, FTOEP_EINVAL, "plan is NULL");
-  TRY(sync_plan(pl));
+  CK(cudaDeviceSynchronize());
   for (auto& pe : pl->pending) {
     pl->evpool.push_back(pe.second.first);
     pl->evpool.push_back(pe.second.second);
   }
   pl->pending.clear();
-  for (int c = 0; c < 5; ++c) {
+  for (int c = 0; c < kNumClasses; ++c) {
     pl->launches[c] = 0;
     pl->prof_ms[c] = 0.0;
     pl->prof_ops[c] = 0;
@@ -895,8 +1000,8 @@ ftoep_status ftoep_profile(ftoep_plan pl, int enable) {
 
 ftoep_status ftoep_profile_read(ftoep_plan pl, int kclass, double* total_ms, int64_t* ops, int64_t* launches) {
   if (!pl) return fail(nullptr, FTOEP_EINVAL, "plan is NULL");
-  if (kclass < 0 || kclass >= 5) return fail(pl, FTOEP_EINVAL, "kernel class out of range");
-  TRY(sync_plan(pl));
+  if (kclass < 0 || kclass >= kNumClasses) return fail(pl, FTOEP_EINVAL, "kernel class out of range");
+  CK(cudaDeviceSynchronize());
   for (auto& pe : pl->pending) {
     float ms = 0.0f;
     if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess) {
@@ -932,6 +1037,9 @@ ftoep_status ftoep_last_error(ftoep_plan pl, char* buf, size_t n) {
 ftoep_status ftoep_destroy(ftoep_plan pl) {
   if (!pl) return FTOEP_EINVAL;
   cudaStreamSynchronize(pl->stream);
+  for (auto& w : pl->ws) {
+    if (w.st) cudaStreamSynchronize(w.st);
+  }
   cudaGetLastError();
   for (void* ptr : pl->allocs) cudaFree(ptr);
   for (auto& pe : pl->pending) {
@@ -939,6 +1047,11 @@ ftoep_status ftoep_destroy(ftoep_plan pl) {
     cudaEventDestroy(pe.second.second);
   }
   for (cudaEvent_t e : pl->evpool) cudaEventDestroy(e);
+  for (auto& w : pl->ws) {
+    if (w.done) cudaEventDestroy(w.done);
+    if (w.own && w.st) cudaStreamDestroy(w.st);
+  }
+  if (pl->fork) cudaEventDestroy(pl->fork);
   delete pl;
   return FTOEP_OK;
 }
