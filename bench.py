@@ -72,8 +72,8 @@ def block_flops_per_unknown(B, L, Sf):
 
 
 def tuning_of(precision, Np):
-    B = min(1024 if precision == "fp64" else 2048, Np)
-    L = min(16 if precision == "fp64" else 8, B)
+    B = min(2048, Np)
+    L = min(16, B)
     return B, L, 64
 
 
@@ -88,7 +88,9 @@ def flop_model(p, precision):
     nblk = -(-p.N // B)
     ncols = nblk * B
     nsolve = 1 if precision == "fp64" else 2
-    block = nsolve * nblk * (2 * P * B) * block_flops_per_unknown(B, L, Sf)
+    # block solve = causal convolution with the block inverse: FFT and inverse FFT of length
+    # 2B per pair plus two complex products per point: 10 log2(2B) + 14 flops per unknown
+    block = nsolve * nblk * (2 * P * B) * (10 * math.log2(2 * B) + 14)
     conv_smem = conv_4 = 0.0
     nsmem = 4096 if precision == "fp64" else 8192
     for v in range(1, nblk):

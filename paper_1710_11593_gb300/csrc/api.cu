@@ -60,6 +60,11 @@ struct Prob {
   double2* spec64 = nullptr;    // solve spectra in double (adjoint of mixed problems; == spec for P64)
   double2* spec_mv = nullptr;   // product spectrum, length 2Np
   double2* spec_dg = nullptr;   // d/dgamma product spectrum
+  // block inverse spectra (block_inverse.cu): precision of the solve, and double (adjoint)
+  void* c1 = nullptr;
+  void* c2 = nullptr;
+  double2* c1_64 = nullptr;
+  double2* c2_64 = nullptr;
 };
 
 // One stream's workspace.
@@ -311,22 +316,22 @@ ftoep_status build_product_spectrum(ftoep_plan pl, Ws& w, Prob& pb, const double
 ftoep_status solve_pairs(ftoep_plan pl, Ws& w, Prob& pb, Prec pr, void* z, const void* spec) {
   cudaStream_t st = w.st;
   CK(cudaMemsetAsync(w.prefix, 0, (size_t)pb.P * sizeof(double2), st));
+  const void* c1 = pr == pb.prec ? pb.c1 : (const void*)pb.c1_64;
+  const void* c2 = pr == pb.prec ? pb.c2 : (const void*)pb.c2_64;
   for (int b = 0; b < pb.nblk; ++b) {
-    BlockArgs ba{};
-    ba.z = z;
-    ba.ld = pb.Np;
-    ba.npairs = pb.P;
-    ba.t0 = (int64_t)b * pb.B;
-    ba.B = pb.B;
-    ba.L = pb.L;
-    ba.Sf = pb.Sf;
-    ba.a = pb.e;
-    ba.invdiag = pb.invdiag;
-    ba.lamtau = pb.lamtau;
-    ba.prefix = w.prefix;
-    ba.spec = spec;
-    ba.tw = tw_of(pl, pr);
-    LAUNCH(FTOEP_K_BLOCK_SOLVE, launch_block_solve(pr, ba, st));
+    BlockInvArgs bi{};
+    bi.z = z;
+    bi.ld = pb.Np;
+    bi.npairs = pb.P;
+    bi.t0 = (int64_t)b * pb.B;
+    bi.B = pb.B;
+    bi.logB = ilog2(pb.B);
+    bi.c1 = c1;
+    bi.c2 = c2;
+    bi.lamtau = pb.lamtau;
+    bi.prefix = w.prefix;
+    bi.tw = tw_of(pl, pr);
+    LAUNCH(FTOEP_K_BLOCK_SOLVE, launch_block_inverse(pr, bi, st));
     const int64_t v = b + 1;
     if (v < pb.nblk) {
       const int64_t s = (int64_t)pb.B << ctz64(v);
@@ -484,15 +489,9 @@ ftoep_status adjoint_problem(ftoep_plan pl, Ws& w, Prob& pb, const double* g, co
   if (pb.bluestein && pb.M + 1 > bluestein_max_K(P64))
     return fail(pl, FTOEP_EUNSUPPORTED, "adjoint: M+1 = %lld > %d needs a double sine transform that is not built",
                 (long long)(pb.M + 1), bluestein_max_K(P64));
-  // The double-precision block parameters (fixed defaults for mixed problems).
+  // The adjoint runs in double with the problem's own block length.
   Prob q = pb;
-  if (pb.prec != P64) {
-    q.prec = P64;
-    q.B = (int)std::min<int64_t>(1024, pb.Np);
-    q.L = std::min(16, q.B);
-    q.nblk = (int)((pb.N + q.B - 1) / q.B);
-    q.ncols = (int64_t)q.nblk * q.B;
-  }
+  q.prec = P64;
   // With u = tau C v (C the all-ones lower triangle), A_u = A_v (tau C)^-1, so
   // A_u^-T g = A_v^-T (tau C^T g): suffix sums of g, then the transposed difference-form
   // solve, done as time reversal + forward solve + reversal (J A_v^T J = A_v per mode).
@@ -620,6 +619,44 @@ ftoep_status build_bluestein(ftoep_plan pl, Prob& pb) {
   return FTOEP_OK;
 }
 
+// h = first B entries of T_m^-1 e_1 for every mode (double substitution kernel on the
+// unit impulse), then the per-pair spectra C1, C2 in precision `pr`.
+ftoep_status build_block_inverse(ftoep_plan pl, Ws& w, Prob& pb, Prec pr, void** c1, void** c2) {
+  cudaStream_t st = w.st;
+  const int64_t n = 2 * (int64_t)pb.B;
+  ALLOC(*c1, (size_t)pb.P * n * velem(pr));
+  ALLOC(*c2, (size_t)pb.P * n * velem(pr));
+  double2* z = (double2*)w.z;
+  LAUNCH(FTOEP_K_OTHER, launch_unit_impulse(z, pb.Np, pb.P, pb.B, st));
+  CK(cudaMemsetAsync(w.prefix, 0, (size_t)pb.P * sizeof(double2), st));
+  BlockArgs ba{};
+  ba.z = z;
+  ba.ld = pb.Np;
+  ba.npairs = pb.P;
+  ba.t0 = 0;
+  ba.B = pb.B;
+  ba.L = pb.L;
+  ba.Sf = pb.Sf;
+  ba.a = pb.e;
+  ba.invdiag = pb.invdiag;
+  ba.lamtau = pb.lamtau;
+  ba.prefix = w.prefix;
+  ba.spec = pb.spec64;
+  ba.tw = pl->tw64;
+  LAUNCH(FTOEP_K_OTHER, launch_block_solve(P64, ba, st));
+  InvSpecArgs is{};
+  is.h = z;
+  is.ldh = pb.Np;
+  is.npairs = pb.P;
+  is.B = pb.B;
+  is.logB = ilog2(pb.B);
+  is.c1 = *c1;
+  is.c2 = *c2;
+  is.tw64 = pl->tw64;
+  LAUNCH(FTOEP_K_OTHER, launch_inverse_spectrum(pr, is, st));
+  return FTOEP_OK;
+}
+
 ftoep_status setup_problem(ftoep_plan pl, Prob& pb) {
   const int64_t N = pb.N, Np = pb.Np;
   pb.h_a.resize(Np);
@@ -663,7 +700,17 @@ ftoep_status setup_problem(ftoep_plan pl, Prob& pb) {
   if (nspec) {
     ALLOC(pb.spec, nspec * velem(pb.prec));
     TRY(build_solve_spectra(pl, w, pb, pb.prec, pb.spec));
-    if (pb.prec == P64) pb.spec64 = (double2*)pb.spec;
+    if (pb.prec == P64) {
+      pb.spec64 = (double2*)pb.spec;
+    } else {
+      ALLOC(pb.spec64, nspec * sizeof(double2));
+      TRY(build_solve_spectra(pl, w, pb, P64, pb.spec64));
+    }
+  }
+  TRY(build_block_inverse(pl, w, pb, pb.prec, &pb.c1, &pb.c2));
+  if (pb.prec == P64) {
+    pb.c1_64 = (double2*)pb.c1;
+    pb.c2_64 = (double2*)pb.c2;
   }
   if (pb.prec == P32) TRY(build_product_spectrum(pl, w, pb, pb.a, &pb.spec_mv));
   return FTOEP_OK;
@@ -710,8 +757,8 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
     pb.tau = pb.d.T / (double)pb.N;
     pb.h = pb.d.space ? pb.d.L / (double)(pb.M + 1) : 1.0;
     pb.scale = scheme_scale(pb.d.kind, pb.d.gamma, pb.tau);
-    const int Bdef = pb.prec == P64 ? 1024 : 2048;
-    const int Ldef = pb.prec == P64 ? 16 : 8;
+    const int Bdef = 2048;
+    const int Ldef = 16;
     int B = (tune && tune->fft_tile) ? tune->fft_tile : Bdef;
     if (B > np) B = (int)np;
     int L = (tune && tune->leaf) ? tune->leaf : Ldef;
@@ -941,6 +988,7 @@ ftoep_status ftoep_adjoint(ftoep_plan pl, const double* g, const double* u, doub
         ALLOC(pb.spec64, (size_t)2 * (pb.Np - pb.Sf) * sizeof(double2));
         TRY(build_solve_spectra(pl, w0, pb, P64, pb.spec64));
       }
+      if (!pb.c1_64) TRY(build_block_inverse(pl, w0, pb, P64, (void**)&pb.c1_64, (void**)&pb.c2_64));
       if (dldgamma) TRY(build_product_spectrum(pl, w0, pb, pb.dadg, &pb.spec_dg));
     }
     TRY(join_streams(pl));

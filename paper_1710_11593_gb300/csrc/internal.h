@@ -164,6 +164,33 @@ struct BlockArgs {
 int launch_block_solve(Prec prec, const BlockArgs& a, cudaStream_t st);
 size_t block_solve_smem(Prec prec, int B, int Sf);
 
+// Block solve by the inverse of the block operator (block_inverse.cu): per pair the
+// spectra C1, C2 (length 2B, this library's FFT order, divided by 2B) of the two modes'
+// inverse first columns h (first B entries of T_m^-1 e_1).
+struct InvSpecArgs {
+  const double2* h;   // [npairs][ldh]: h of mode 2p in .x, of mode 2p+1 in .y
+  int64_t ldh;
+  int64_t npairs;
+  int B, logB;
+  void* c1;           // [npairs][2B], precision of the solve
+  void* c2;
+  const double2* tw64;
+};
+int launch_inverse_spectrum(Prec prec, const InvSpecArgs& a, cudaStream_t st);
+int launch_unit_impulse(double2* z, int64_t ld, int64_t npairs, int B, cudaStream_t st);
+
+struct BlockInvArgs {
+  void* z;                 // pairs [npairs][ld]; block [t0, t0+B) in place
+  int64_t ld, npairs, t0;
+  int B, logB;
+  const void* c1;
+  const void* c2;
+  const double2* lamtau;   // per pair lambda*tau
+  double2* prefix;         // per pair running sums of the solved v (in and out)
+  const void* tw;
+};
+int launch_block_inverse(Prec prec, const BlockInvArgs& a, cudaStream_t st);
+
 // Largest shared-memory FFT length of each precision.
 int nsmem_for(Prec prec);
 
