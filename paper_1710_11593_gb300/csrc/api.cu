@@ -60,6 +60,7 @@ struct Prob {
   double2* spec64 = nullptr;    // solve spectra in double (adjoint of mixed problems; == spec for P64)
   double2* spec_mv = nullptr;   // product spectrum, length 2Np
   double2* spec_dg = nullptr;   // d/dgamma product spectrum
+  void* spec_res = nullptr;     // float-float spectrum of the difference-form kernel (mixed residual)
   // block inverse spectra (block_inverse.cu): precision of the solve, and double (adjoint)
   void* c1 = nullptr;
   void* c2 = nullptr;
@@ -118,6 +119,7 @@ struct ftoep_plan_s {
   int64_t ntw = 0;
   double2* tw64 = nullptr;
   float2* tw32 = nullptr;
+  void* twff = nullptr;           // float-float twiddles (ff2)
   std::vector<Ws> ws;
   size_t z_el = 0, mv_el = 0, r_el = 0, p_el = 0, v_el = 0;
   double* dscal = nullptr;        // device scalars (nprob)
@@ -225,8 +227,10 @@ bool is_device_ptr(const void* ptr) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-const void* tw_of(ftoep_plan pl, Prec pr) { return pr == P64 ? (const void*)pl->tw64 : (const void*)pl->tw32; }
-size_t velem(Prec pr) { return pr == P64 ? sizeof(double2) : sizeof(float2); }
+const void* tw_of(ftoep_plan pl, Prec pr) {
+  return pr == P64 ? (const void*)pl->tw64 : pr == P32 ? (const void*)pl->tw32 : (const void*)pl->twff;
+}
+size_t velem(Prec pr) { return pr == P32 ? sizeof(float2) : sizeof(double2); }
 
 void release(ftoep_plan pl, void* ptr) {
   if (!ptr) return;
@@ -294,21 +298,22 @@ ftoep_status build_solve_spectra(ftoep_plan pl, Ws& w, Prob& pb, Prec pr, void* 
   return FTOEP_OK;
 }
 
-// Spectrum of the full product y = T x (c_k = coeff_k for k < N, zero after), length 2Np.
-ftoep_status build_product_spectrum(ftoep_plan pl, Ws& w, Prob& pb, const double* coeff, double2** out) {
+// Spectrum of the full product y = T x (c_k = coeff_k for k < N, zero after), length
+// 2Np, in precision pr (double or float-float).
+ftoep_status build_product_spectrum(ftoep_plan pl, Ws& w, Prob& pb, const double* coeff, void** out, Prec pr) {
   if (*out) return FTOEP_OK;
   cudaStream_t st = w.st;
-  ALLOC(*out, (size_t)2 * pb.Np * sizeof(double2));
+  ALLOC(*out, (size_t)2 * pb.Np * velem(pr));
   SpecArgs sa{};
   sa.a = coeff;
   sa.lo = 0;
   sa.hi = pb.N;
   sa.logn = pb.logNp + 1;
-  sa.nsmem = nsmem_for(P64);
+  sa.nsmem = nsmem_for(pr);
   sa.out = *out;
   sa.tw64 = pl->tw64;
   sa.scratch64 = w.scratch_mv;
-  LAUNCH(FTOEP_K_OTHER, launch_spectrum(P64, sa, st));
+  LAUNCH(FTOEP_K_OTHER, launch_spectrum(pr, sa, st));
   return FTOEP_OK;
 }
 
@@ -377,9 +382,10 @@ DstArgs dst_args(ftoep_plan pl, const Prob& pb, Prec pr, void* z) {
   return da;
 }
 
-// y = T x on nlines lines of length N (double), through the product workspace.
-ftoep_status product_lines(ftoep_plan pl, Ws& w, Prob& pb, const double2* spec, const double* x, double* y_or_null,
-                           int64_t nlines, int reverse) {
+// y = T x on nlines lines of length N (double in and out, arithmetic in precision pr:
+// double or float-float), through the product workspace.
+ftoep_status product_lines(ftoep_plan pl, Ws& w, Prob& pb, Prec pr, const void* spec, const double* x,
+                           double* y_or_null, int64_t nlines, int reverse) {
   cudaStream_t st = w.st;
   PackArgs pa{};
   pa.x = x;
@@ -388,7 +394,7 @@ ftoep_status product_lines(ftoep_plan pl, Ws& w, Prob& pb, const double2* spec, 
   pa.N = pb.N;
   pa.nlines = nlines;
   pa.reverse = reverse;
-  LAUNCH(FTOEP_K_OTHER, launch_pack(P64, pa, st));
+  LAUNCH(FTOEP_K_OTHER, launch_pack(pr, pa, st));
   ConvArgs ca{};
   ca.zin = w.zmv;
   ca.zout = w.zmv;
@@ -396,16 +402,16 @@ ftoep_status product_lines(ftoep_plan pl, Ws& w, Prob& pb, const double2* spec, 
   ca.in_off = ca.out_off = 0;
   ca.npairs = (nlines + 1) / 2;
   ca.logn = pb.logNp + 1;
-  ca.nsmem = nsmem_for(P64);
+  ca.nsmem = nsmem_for(pr);
   ca.mode = 1;
   ca.spec = spec;
-  ca.tw = pl->tw64;
+  ca.tw = tw_of(pl, pr);
   ca.scratch = w.scratch_mv;
-  LAUNCH((2 * pb.Np <= nsmem_for(P64)) ? FTOEP_K_CONV_SMEM : FTOEP_K_CONV_FOURSTEP, launch_conv(P64, ca, st));
+  LAUNCH((2 * pb.Np <= nsmem_for(pr)) ? FTOEP_K_CONV_SMEM : FTOEP_K_CONV_FOURSTEP, launch_conv(pr, ca, st));
   if (y_or_null) {
     pa.y = y_or_null;
     pa.mode = 0;
-    LAUNCH(FTOEP_K_OTHER, launch_unpack(P64, pa, st));
+    LAUNCH(FTOEP_K_OTHER, launch_unpack(pr, pa, st));
   }
   return FTOEP_OK;
 }
@@ -445,21 +451,30 @@ ftoep_status solve_problem(ftoep_plan pl, Ws& w, Prob& pb, const double* f, doub
   da.diff_form = 1;
   LAUNCH(FTOEP_K_SINE, launch_dst_forward(pr, da, st));
   TRY(solve_pairs(pl, w, pb, pr, w.z, pb.spec));
-  da.u = u;
+  if (pr == P64) {
+    da.u = u;
+    da.accumulate = 0;
+    LAUNCH(FTOEP_K_SINE, launch_dst_inverse(pr, da, st));
+    TRY(scan_lines(pl, w, pb, u, u, u0, 0, 0));
+    return FTOEP_OK;
+  }
+  // mixed: keep the solved v (physical space) in r, u = u0 + tau cumsum(v)
+  da.u = w.r;
   da.accumulate = 0;
   LAUNCH(FTOEP_K_SINE, launch_dst_inverse(pr, da, st));
-  TRY(scan_lines(pl, w, pb, u, u, u0, 0, 0));
-  if (pr == P64) return FTOEP_OK;
-  // residual of the original form in double: r = f + init - T u - S u
-  TRY(product_lines(pl, w, pb, pb.spec_mv, u, nullptr, pb.M, 0));
+  TRY(scan_lines(pl, w, pb, w.r, u, u0, 0, 0));
+  // residual of the same rows in the difference form, r = f + c tau M phi - E v - S u,
+  // with the Toeplitz product E v in float-float (no tau^-g cancellation in this form)
+  TRY(product_lines(pl, w, pb, PFF, pb.spec_res, w.r, nullptr, pb.M, 0));
   ResidualArgs ra{};
   ra.f = f;
-  ra.u0 = u0;
+  ra.u0 = nullptr;
   ra.phi = da.phi;
   ra.wu0 = pb.wu0;
   ra.wphi = pb.wphi;
   ra.u = u;
   ra.tu = w.zmv;
+  ra.tu_ff = 1;
   ra.r = w.r;
   ra.ld = pb.Np;
   ra.N = pb.N;
@@ -505,7 +520,7 @@ ftoep_status adjoint_problem(ftoep_plan pl, Ws& w, Prob& pb, const double* g, co
   da.accumulate = 0;
   LAUNCH(FTOEP_K_SINE, launch_dst_inverse(P64, da, st));
   if (dgamma_out) {
-    TRY(product_lines(pl, w, pb, pb.spec_dg, u, nullptr, pb.M, 0));
+    TRY(product_lines(pl, w, pb, P64, pb.spec_dg, u, nullptr, pb.M, 0));
     DotArgs dt{};
     dt.x = dldf;
     dt.tu = w.zmv;
@@ -712,7 +727,7 @@ ftoep_status setup_problem(ftoep_plan pl, Prob& pb) {
     pb.c1_64 = (double2*)pb.c1;
     pb.c2_64 = (double2*)pb.c2;
   }
-  if (pb.prec == P32) TRY(build_product_spectrum(pl, w, pb, pb.a, &pb.spec_mv));
+  if (pb.prec == P32) TRY(build_product_spectrum(pl, w, pb, pb.e, &pb.spec_res, PFF));
   return FTOEP_OK;
 }
 
@@ -834,23 +849,31 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
     const size_t tot = (size_t)2 * maxtw - 2;
     std::vector<double2> h64(tot);
     std::vector<float2> h32(tot);
+    std::vector<float4> hff(tot);
     std::vector<double2> big(maxtw);
     const long double two_pi = 6.283185307179586476925286766559005768L;
+    std::vector<float4> bigff(maxtw);
     for (int64_t k = 0; k < maxtw; ++k) {
       long double ang = -two_pi * (long double)k / (long double)maxtw;
-      big[k] = make_double2((double)cosl(ang), (double)sinl(ang));
+      const long double c = cosl(ang), sn = sinl(ang);
+      big[k] = make_double2((double)c, (double)sn);
+      const float ch = (float)c, sh = (float)sn;
+      bigff[k] = make_float4(ch, (float)(c - (long double)ch), sh, (float)(sn - (long double)sh));
     }
     for (int64_t n = 2; n <= maxtw; n <<= 1) {
       const int64_t stride = maxtw / n;
       for (int64_t k = 0; k < n; ++k) {
         h64[(n - 2) + k] = big[k * stride];
         h32[(n - 2) + k] = make_float2((float)big[k * stride].x, (float)big[k * stride].y);
+        hff[(n - 2) + k] = bigff[k * stride];
       }
     }
     if ((st = dalloc(pl, (void**)&pl->tw64, tot * sizeof(double2))) != FTOEP_OK) return bail(st);
     if ((st = dalloc(pl, (void**)&pl->tw32, tot * sizeof(float2))) != FTOEP_OK) return bail(st);
+    if ((st = dalloc(pl, &pl->twff, tot * sizeof(float4))) != FTOEP_OK) return bail(st);
     if (cudaMemcpy(pl->tw64, h64.data(), tot * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(pl->tw32, h32.data(), tot * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(pl->tw32, h32.data(), tot * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(pl->twff, hff.data(), tot * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess) {
       cudaGetLastError();
       pl->err = "twiddle upload failed";
       return bail(FTOEP_ECUDA);
@@ -941,7 +964,7 @@ ftoep_status ftoep_matvec(ftoep_plan pl, int iprob, const double* x, double* y, 
     return fail(pl, FTOEP_EINVAL, "x and y overlap");
   TRY(fork_streams(pl));
   cudaStream_t st = w.st;
-  TRY(build_product_spectrum(pl, w, pb, pb.a, &pb.spec_mv));
+  TRY(build_product_spectrum(pl, w, pb, pb.a, (void**)&pb.spec_mv, P64));
   const bool host = !is_device_ptr(x) || !is_device_ptr(y);
   // lines per chunk: twice the pairs the product workspace holds
   const int64_t chunk = 2 * (int64_t)(pl->mv_el / pb.Np);
@@ -958,7 +981,7 @@ ftoep_status ftoep_matvec(ftoep_plan pl, int iprob, const double* x, double* y, 
       CK(cudaMemcpyAsync(sx, xin, nl * pb.N * sizeof(double), cudaMemcpyDefault, st));
       xin = sx;
     }
-    TRY(product_lines(pl, w, pb, pb.spec_mv, xin, host ? sy : yout, nl, transpose ? 1 : 0));
+    TRY(product_lines(pl, w, pb, P64, pb.spec_mv, xin, host ? sy : yout, nl, transpose ? 1 : 0));
     if (host) CK(cudaMemcpyAsync(yout, sy, nl * pb.N * sizeof(double), cudaMemcpyDefault, st));
   }
   TRY(join_streams(pl));
@@ -989,7 +1012,7 @@ ftoep_status ftoep_adjoint(ftoep_plan pl, const double* g, const double* u, doub
         TRY(build_solve_spectra(pl, w0, pb, P64, pb.spec64));
       }
       if (!pb.c1_64) TRY(build_block_inverse(pl, w0, pb, P64, (void**)&pb.c1_64, (void**)&pb.c2_64));
-      if (dldgamma) TRY(build_product_spectrum(pl, w0, pb, pb.dadg, &pb.spec_dg));
+      if (dldgamma) TRY(build_product_spectrum(pl, w0, pb, pb.dadg, (void**)&pb.spec_dg, P64));
     }
     TRY(join_streams(pl));
   }

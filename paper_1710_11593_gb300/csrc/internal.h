@@ -17,8 +17,9 @@ void initial_weights(int kind, double gamma, double tau, int64_t n, double* wu0,
 void difference_weights(int kind, double gamma, double tau, int64_t n, double* e);
 
 // ---------------------------------------------------------------- kernel launchers
-// Storage precision of the complex work arrays: 0 = double2, 1 = float2.
-enum Prec { P64 = 0, P32 = 1 };
+// Storage precision of the complex work arrays: 0 = double2, 1 = float2,
+// 2 = float-float pairs (ff2, products of the mixed path's residual).
+enum Prec { P64 = 0, P32 = 1, PFF = 2 };
 
 struct DstArgs {
   // forward: f (+ wu0*u0 + wphi*phi) [M][N] doubles  ->  z pairs [P][ld]
@@ -84,8 +85,9 @@ struct ScanArgs {
 };
 int launch_scan(const ScanArgs& a, cudaStream_t st);
 
-// Residual r = f + wu0*u0 + wphi*phi - (T u) - S(u), with (T u) given in pairs (double2)
-// and S the spatial operator: Dirichlet -u_xx (space 1) or lambda*u (space 0).
+// Residual r = f + wu0*u0 + wphi*phi - (T x) - S(u), with (T x) given in pairs (double2
+// or float-float, tu_ff) and S the spatial operator: Dirichlet -u_xx (space 1) or
+// lambda*u (space 0).  r may alias the input of the product (it is read per element).
 struct ResidualArgs {
   const double* f;
   const double* u0;
@@ -93,7 +95,8 @@ struct ResidualArgs {
   const double* wu0;
   const double* wphi;
   const double* u;
-  const double2* tu;  // pairs [P][ld]
+  const void* tu;     // pairs [P][ld]
+  int tu_ff;
   double* r;
   int64_t ld, N, M;
   int space;

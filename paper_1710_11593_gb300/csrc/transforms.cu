@@ -23,6 +23,18 @@ inline void set_smem(const void* fn, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Conversions between double pairs and the storage types.
+template <typename T> __device__ __forceinline__ typename VecOf<T>::type make_pair_of(double a, double b);
+template <> __device__ __forceinline__ double2 make_pair_of<double>(double a, double b) { return make_double2(a, b); }
+template <> __device__ __forceinline__ float2 make_pair_of<float>(double a, double b) { return make_float2((float)a, (float)b); }
+template <> __device__ __forceinline__ ff2 make_pair_of<FF>(double a, double b) { return ff2_from(a, b); }
+__device__ __forceinline__ double re_of(double2 v) { return v.x; }
+__device__ __forceinline__ double im_of(double2 v) { return v.y; }
+__device__ __forceinline__ double re_of(float2 v) { return (double)v.x; }
+__device__ __forceinline__ double im_of(float2 v) { return (double)v.y; }
+__device__ __forceinline__ double re_of(ff2 v) { return (double)v.xh + (double)v.xl; }
+__device__ __forceinline__ double im_of(ff2 v) { return (double)v.yh + (double)v.yl; }
+
 // ------------------------------------------------------------------ sine transform
 //
 // DST-I of length M via the odd extension y (length 2K, K = M+1): y_0 = y_K = 0,
@@ -362,7 +374,7 @@ __global__ void pack_kernel(PackArgs A) {
     v0 = A.x[(2 * p) * A.N + src];
     if (2 * p + 1 < A.nlines) v1 = A.x[(2 * p + 1) * A.N + src];
   }
-  ((V*)A.z)[p * A.ld + k] = mkv((T)v0, (T)v1);
+  ((V*)A.z)[p * A.ld + k] = make_pair_of<T>(v0, v1);
 }
 
 template <typename T>
@@ -374,10 +386,10 @@ __global__ void unpack_kernel(PackArgs A) {
   const int64_t k = A.reverse ? A.N - 1 - n : n;
   const V v = ((const V*)A.z)[p * A.ld + k];
   double* y0 = A.y + (2 * p) * A.N + n;
-  *y0 = A.mode ? *y0 + (double)v.x : (double)v.x;
+  *y0 = A.mode ? *y0 + re_of(v) : re_of(v);
   if (2 * p + 1 < A.nlines) {
     double* y1 = A.y + (2 * p + 1) * A.N + n;
-    *y1 = A.mode ? *y1 + (double)v.y : (double)v.y;
+    *y1 = A.mode ? *y1 + im_of(v) : im_of(v);
   }
 }
 
@@ -451,8 +463,14 @@ __global__ void residual_kernel(ResidualArgs A) {
   double v = A.f[idx];
   if (A.u0) v += A.wu0[n] * A.u0[j];
   if (A.phi) v += A.wphi[n] * A.phi[j];
-  const double2 t = A.tu[(j >> 1) * A.ld + n];
-  const double tv = (j & 1) ? t.y : t.x;
+  double tv;
+  if (A.tu_ff) {
+    const ff2 t = ((const ff2*)A.tu)[(j >> 1) * A.ld + n];
+    tv = (j & 1) ? im_of(t) : re_of(t);
+  } else {
+    const double2 t = ((const double2*)A.tu)[(j >> 1) * A.ld + n];
+    tv = (j & 1) ? t.y : t.x;
+  }
   const double uj = A.u[idx];
   double s;
   if (A.space == 1) {
@@ -525,7 +543,7 @@ __global__ void __launch_bounds__(kThreads) spec_smem_kernel(SpecArgs A) {
   fft_dif<double2>(sm, A.logn, 1, 0, A.tw64, false);
   const double inv = 1.0 / (double)n;
   typedef Vt<TS> V;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) ((V*)A.out)[k] = mkv((TS)(sm[k].x * inv), (TS)(sm[k].y * inv));
+  for (int k = threadIdx.x; k < n; k += blockDim.x) ((V*)A.out)[k] = make_pair_of<TS>(sm[k].x * inv, sm[k].y * inv);
 }
 
 __global__ void __launch_bounds__(kThreads) spec_col_kernel(SpecArgs A, int logn1, int logn2, int C) {
@@ -563,7 +581,7 @@ __global__ void __launch_bounds__(kThreads) spec_row_kernel(SpecArgs A, int logn
   const double inv = 1.0 / (double)n;
   typedef Vt<TS> V;
   for (int k = threadIdx.x; k < n2; k += blockDim.x)
-    ((V*)A.out)[(int64_t)r * n2 + k] = mkv((TS)(sm[k].x * inv), (TS)(sm[k].y * inv));
+    ((V*)A.out)[(int64_t)r * n2 + k] = make_pair_of<TS>(sm[k].x * inv, sm[k].y * inv);
 }
 
 template <typename TS>
@@ -719,7 +737,7 @@ void conv_launch(const ConvArgs& a, cudaStream_t st) {
 
 }  // namespace
 
-int nsmem_for(Prec prec) { return prec == P64 ? 4096 : 8192; }
+int nsmem_for(Prec prec) { return prec == P32 ? 8192 : 4096; }
 int bluestein_max_K(Prec prec) { return prec == P64 ? 2048 : 4096; }
 
 int launch_dst_forward(Prec prec, const DstArgs& a, cudaStream_t st) {
@@ -734,13 +752,15 @@ int launch_dst_inverse(Prec prec, const DstArgs& a, cudaStream_t st) {
 int launch_pack(Prec prec, const PackArgs& a, cudaStream_t st) {
   dim3 grid((unsigned)((a.ld + kThreads - 1) / kThreads), (unsigned)((a.nlines + 1) / 2));
   if (prec == P64) pack_kernel<double><<<grid, kThreads, 0, st>>>(a);
-  else pack_kernel<float><<<grid, kThreads, 0, st>>>(a);
+  else if (prec == P32) pack_kernel<float><<<grid, kThreads, 0, st>>>(a);
+  else pack_kernel<FF><<<grid, kThreads, 0, st>>>(a);
   return 1;
 }
 int launch_unpack(Prec prec, const PackArgs& a, cudaStream_t st) {
   dim3 grid((unsigned)((a.N + kThreads - 1) / kThreads), (unsigned)((a.nlines + 1) / 2));
   if (prec == P64) unpack_kernel<double><<<grid, kThreads, 0, st>>>(a);
-  else unpack_kernel<float><<<grid, kThreads, 0, st>>>(a);
+  else if (prec == P32) unpack_kernel<float><<<grid, kThreads, 0, st>>>(a);
+  else unpack_kernel<FF><<<grid, kThreads, 0, st>>>(a);
   return 1;
 }
 
@@ -765,12 +785,16 @@ int launch_sum(const double* partial, int n, double* out, cudaStream_t st) {
 }
 
 int launch_spectrum(Prec prec, const SpecArgs& a, cudaStream_t st) {
-  if (prec == P64) spectrum_launch<double>(a, st); else spectrum_launch<float>(a, st);
+  if (prec == P64) spectrum_launch<double>(a, st);
+  else if (prec == P32) spectrum_launch<float>(a, st);
+  else spectrum_launch<FF>(a, st);
   return (1 << a.logn) <= a.nsmem ? 1 : 2;
 }
 
 int launch_conv(Prec prec, const ConvArgs& a, cudaStream_t st) {
-  if (prec == P64) conv_launch<double>(a, st); else conv_launch<float>(a, st);
+  if (prec == P64) conv_launch<double>(a, st);
+  else if (prec == P32) conv_launch<float>(a, st);
+  else conv_launch<FF>(a, st);
   return (1 << a.logn) <= a.nsmem ? 1 : 3;
 }
 
