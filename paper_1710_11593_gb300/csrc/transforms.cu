@@ -62,8 +62,10 @@ __device__ __forceinline__ double rhs_value(const DstArgs& A, int64_t j, int64_t
   return v;
 }
 
+constexpr int kDstThreads = 512;
+
 template <typename T>
-__global__ void __launch_bounds__(kThreads) dst_forward_kernel(DstArgs A, int C) {
+__global__ void __launch_bounds__(kDstThreads) dst_forward_kernel(DstArgs A, int C) {
   typedef Vt<T> V;
   V* z = (V*)A.z;
   const int64_t col0 = (int64_t)blockIdx.x * C;
@@ -99,20 +101,31 @@ __global__ void __launch_bounds__(kThreads) dst_forward_kernel(DstArgs A, int C)
     sm[cp * lds] = vzero<V>();
     sm[cp * lds + K] = vzero<V>();
   }
-  for (int64_t e = threadIdx.x; e < M * C; e += blockDim.x) {
-    const int64_t j = e / C;
-    const int c = (int)(e % C);
-    const int64_t n = col0 + c;
-    const double v = n < N ? rhs_value(A, j, n) : 0.0;
-    const T tv = (T)v;
-    V* col = sm + (c >> 1) * lds;
-    const int pos = (int)j + 1;
-    if (c & 1) {
-      col[pos].y = tv;
-      col[K2 - pos].y = -tv;
-    } else {
-      col[pos].x = tv;
-      col[K2 - pos].x = -tv;
+  // four independent loads in flight per thread before the shared-memory stores
+  const int64_t tot = M * C;
+  for (int64_t e0 = threadIdx.x; e0 < tot; e0 += 4 * (int64_t)blockDim.x) {
+    double v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t e = e0 + q * (int64_t)blockDim.x;
+      const int64_t n = col0 + (e % C);
+      v[q] = (e < tot && n < N) ? rhs_value(A, e / C, n) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t e = e0 + q * (int64_t)blockDim.x;
+      if (e >= tot) break;
+      const int c = (int)(e % C);
+      const T tv = (T)v[q];
+      V* col = sm + (c >> 1) * lds;
+      const int pos = (int)(e / C) + 1;
+      if (c & 1) {
+        col[pos].y = tv;
+        col[K2 - pos].y = -tv;
+      } else {
+        col[pos].x = tv;
+        col[K2 - pos].x = -tv;
+      }
     }
   }
   __syncthreads();
@@ -138,7 +151,7 @@ __global__ void __launch_bounds__(kThreads) dst_forward_kernel(DstArgs A, int C)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) dst_inverse_kernel(DstArgs A, int C) {
+__global__ void __launch_bounds__(kDstThreads) dst_inverse_kernel(DstArgs A, int C) {
   typedef Vt<T> V;
   const V* z = (const V*)A.z;
   const int64_t col0 = (int64_t)blockIdx.x * C;
@@ -172,27 +185,41 @@ __global__ void __launch_bounds__(kThreads) dst_inverse_kernel(DstArgs A, int C)
     sm[cp * lds] = vzero<V>();
     sm[cp * lds + K] = vzero<V>();
   }
-  for (int64_t e = threadIdx.x; e < P * C; e += blockDim.x) {
-    const int64_t p = e / C;
-    const int c = (int)(e % C);
-    const int64_t n = col0 + c;
-    const int64_t nin = (A.reverse && n < N) ? N - 1 - n : n;
-    const V zz = z[p * A.ld + nin];
-    V* col = sm + (c >> 1) * lds;
-    const int m1 = (int)(2 * p + 1), m2 = m1 + 1;
-    if (c & 1) {
-      col[m1].y = zz.x;
-      col[K2 - m1].y = -zz.x;
-      if (m2 <= M) {
-        col[m2].y = zz.y;
-        col[K2 - m2].y = -zz.y;
+  const int64_t tot = P * C;
+  for (int64_t e0 = threadIdx.x; e0 < tot; e0 += 4 * (int64_t)blockDim.x) {
+    V zq[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t e = e0 + q * (int64_t)blockDim.x;
+      if (e < tot) {
+        const int64_t n = col0 + (e % C);
+        const int64_t nin = (A.reverse && n < N) ? N - 1 - n : n;
+        zq[q] = z[(e / C) * A.ld + nin];
       }
-    } else {
-      col[m1].x = zz.x;
-      col[K2 - m1].x = -zz.x;
-      if (m2 <= M) {
-        col[m2].x = zz.y;
-        col[K2 - m2].x = -zz.y;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t e = e0 + q * (int64_t)blockDim.x;
+      if (e >= tot) break;
+      const int64_t p = e / C;
+      const int c = (int)(e % C);
+      const V zz = zq[q];
+      V* col = sm + (c >> 1) * lds;
+      const int m1 = (int)(2 * p + 1), m2 = m1 + 1;
+      if (c & 1) {
+        col[m1].y = zz.x;
+        col[K2 - m1].y = -zz.x;
+        if (m2 <= M) {
+          col[m2].y = zz.y;
+          col[K2 - m2].y = -zz.y;
+        }
+      } else {
+        col[m1].x = zz.x;
+        col[K2 - m1].x = -zz.x;
+        if (m2 <= M) {
+          col[m2].x = zz.y;
+          col[K2 - m2].x = -zz.y;
+        }
       }
     }
   }
@@ -216,7 +243,7 @@ __global__ void __launch_bounds__(kThreads) dst_inverse_kernel(DstArgs A, int C)
 // convolution that a cyclic one of length P >= 2L-1 reproduces exactly.  One block
 // handles C time columns (C/2 complex column pairs, one P-buffer each).
 template <typename T>
-__global__ void __launch_bounds__(kThreads) dst_bluestein_kernel(DstArgs A, int C, int fwd) {
+__global__ void __launch_bounds__(kDstThreads) dst_bluestein_kernel(DstArgs A, int C, int fwd) {
   typedef Vt<T> V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
@@ -231,29 +258,53 @@ __global__ void __launch_bounds__(kThreads) dst_bluestein_kernel(DstArgs A, int 
   for (int e = threadIdx.x; e < CP * H; e += blockDim.x) sm[(e / H) * lds + (e % H)] = vzero<V>();
   __syncthreads();
   if (fwd) {
-    for (int64_t e = threadIdx.x; e < M * C; e += blockDim.x) {
-      const int64_t j = e / C;
-      const int c = (int)(e % C);
-      const int64_t n = col0 + c;
-      const T tv = (T)(n < N ? rhs_value(A, j, n) : 0.0);
-      V* col = sm + (c >> 1) * lds;
-      const int pos = (int)j + 1;
-      if (c & 1) {
-        col[pos].y = tv;
-        col[L - pos].y = -tv;
-      } else {
-        col[pos].x = tv;
-        col[L - pos].x = -tv;
+    const int64_t tot = M * C;
+    for (int64_t e0 = threadIdx.x; e0 < tot; e0 += 4 * (int64_t)blockDim.x) {
+      double vq[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t e = e0 + q * (int64_t)blockDim.x;
+        const int64_t n = col0 + (e % C);
+        vq[q] = (e < tot && n < N) ? rhs_value(A, e / C, n) : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t e = e0 + q * (int64_t)blockDim.x;
+        if (e >= tot) break;
+        const int c = (int)(e % C);
+        const T tv = (T)vq[q];
+        V* col = sm + (c >> 1) * lds;
+        const int pos = (int)(e / C) + 1;
+        if (c & 1) {
+          col[pos].y = tv;
+          col[L - pos].y = -tv;
+        } else {
+          col[pos].x = tv;
+          col[L - pos].x = -tv;
+        }
       }
     }
   } else {
     const V* z = (const V*)A.z;
-    for (int64_t e = threadIdx.x; e < P2 * C; e += blockDim.x) {
+    const int64_t tot = P2 * C;
+    for (int64_t e0 = threadIdx.x; e0 < tot; e0 += 4 * (int64_t)blockDim.x) {
+     V zq[4];
+#pragma unroll
+     for (int q = 0; q < 4; ++q) {
+      const int64_t e = e0 + q * (int64_t)blockDim.x;
+      if (e < tot) {
+        const int64_t n = col0 + (e % C);
+        const int64_t nin = (A.reverse && n < N) ? N - 1 - n : n;
+        zq[q] = z[(e / C) * A.ld + nin];
+      }
+     }
+#pragma unroll
+     for (int q = 0; q < 4; ++q) {
+      const int64_t e = e0 + q * (int64_t)blockDim.x;
+      if (e >= tot) break;
       const int64_t p = e / C;
       const int c = (int)(e % C);
-      const int64_t n = col0 + c;
-      const int64_t nin = (A.reverse && n < N) ? N - 1 - n : n;
-      const V zz = z[p * A.ld + nin];
+      const V zz = zq[q];
       V* col = sm + (c >> 1) * lds;
       const int m1 = (int)(2 * p + 1), m2 = m1 + 1;
       if (c & 1) {
@@ -271,6 +322,7 @@ __global__ void __launch_bounds__(kThreads) dst_bluestein_kernel(DstArgs A, int 
           col[L - m2].x = -zz.y;
         }
       }
+     }
     }
   }
   __syncthreads();
@@ -345,7 +397,7 @@ void dst_launch(const DstArgs& a, bool fwd, cudaStream_t st) {
     const int C = bluestein_cols<T>(a.logP);
     const size_t smem = (size_t)(C / 2) * ((size_t)(1 << a.logP) + 1) * sizeof(Vt<T>);
     set_smem((const void*)dst_bluestein_kernel<T>, smem);
-    dst_bluestein_kernel<T><<<(unsigned)((a.ncols + C - 1) / C), kThreads, smem, st>>>(a, C, fwd ? 1 : 0);
+    dst_bluestein_kernel<T><<<(unsigned)((a.ncols + C - 1) / C), kDstThreads, smem, st>>>(a, C, fwd ? 1 : 0);
     return;
   }
   int C = a.space ? dst_cols<T>(a.logK2) : 8;
@@ -353,10 +405,10 @@ void dst_launch(const DstArgs& a, bool fwd, cudaStream_t st) {
   dim3 grid((unsigned)((a.ncols + C - 1) / C));
   if (fwd) {
     set_smem((const void*)dst_forward_kernel<T>, smem);
-    dst_forward_kernel<T><<<grid, kThreads, smem, st>>>(a, C);
+    dst_forward_kernel<T><<<grid, kDstThreads, smem, st>>>(a, C);
   } else {
     set_smem((const void*)dst_inverse_kernel<T>, smem);
-    dst_inverse_kernel<T><<<grid, kThreads, smem, st>>>(a, C);
+    dst_inverse_kernel<T><<<grid, kDstThreads, smem, st>>>(a, C);
   }
 }
 
@@ -645,9 +697,18 @@ __global__ void __launch_bounds__(kThreads) conv_col_fwd_kernel(ConvArgs A, int 
   const int c0 = blockIdx.x * C;
   const int64_t p = blockIdx.y;
   const V* zin = (const V*)A.zin + p * A.ld_in + A.in_off;
-  for (int e = threadIdx.x; e < h1 * C; e += blockDim.x) {
-    const int j1 = e / C, c = e % C;
-    sm[c * lds + j1] = zin[(int64_t)j1 * n2 + c0 + c];
+  for (int e0 = threadIdx.x; e0 < h1 * C; e0 += 4 * blockDim.x) {
+    V v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = e0 + q * blockDim.x;
+      if (e < h1 * C) v[q] = zin[(int64_t)(e / C) * n2 + c0 + e % C];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = e0 + q * blockDim.x;
+      if (e < h1 * C) sm[(e % C) * lds + e / C] = v[q];
+    }
   }
   __syncthreads();
   const V* tw = (const V*)A.tw;
@@ -694,9 +755,18 @@ __global__ void __launch_bounds__(kThreads) conv_col_inv_kernel(ConvArgs A, int 
   const int c0 = blockIdx.x * C;
   const int64_t p = blockIdx.y;
   const V* sc = (const V*)A.scratch + p * (int64_t)n;
-  for (int e = threadIdx.x; e < n1 * C; e += blockDim.x) {
-    const int r = e / C, c = e % C;
-    sm[c * lds + r] = sc[(int64_t)r * n2 + c0 + c];
+  for (int e0 = threadIdx.x; e0 < n1 * C; e0 += 4 * blockDim.x) {
+    V v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = e0 + q * blockDim.x;
+      if (e < n1 * C) v[q] = sc[(int64_t)(e / C) * n2 + c0 + e % C];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = e0 + q * blockDim.x;
+      if (e < n1 * C) sm[(e % C) * lds + e / C] = v[q];
+    }
   }
   __syncthreads();
   fft_dit<V>(sm, logn1, C, lds, (const V*)A.tw, A.mode == 0 ? 1 : 2);
