@@ -26,6 +26,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "M·N unknowns/sec at ≤1e-6 rel err: mixed-precision batched vs plain FP64"
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (profiling recipe); probe measured 1.19 (DFMA loop)
+# FP32 from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def parse():
@@ -40,22 +42,24 @@ def parse():
                     help="default: fp64 for diffusion/scalar, mixed for wave")
     ap.add_argument("--no-compare", action="store_true", help="skip the mixed-precision comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--M", type=int, default=None, help="override the workload's interior points (profiling cases)")
+    ap.add_argument("--N", type=int, default=None, help="override the workload's time steps (profiling cases)")
     return ap.parse_args()
 
 
-def workload(name, nprob=512):
+def workload(name, nprob=512, M=None, N=None):
     from paper_1710_11593_gb300 import workloads as wl
     if name == "batched":
         probs = wl.config_batched(nprob=nprob)
         return probs, f"batched{nprob}_N2^10-2^17_M63-2047_seed1234"
     if name == "diffusion":
-        p = wl.config_diffusion()
-        return p, "diffusion_g0.7_M1023_N65536"
+        p = wl.config_diffusion(M=M or 1023, N=N or 65536)
+        return p, f"diffusion_g0.7_M{p.M}_N{p.N}"
     if name == "wave":
-        p = wl.config_wave()
-        return p, "wave_g1.5_M4095_N262144"
-    p = wl.config_scalar()
-    return p, "scalar_g0.5_N1024"
+        p = wl.config_wave(M=M or 4095, N=N or 262144)
+        return p, f"wave_g1.5_M{p.M}_N{p.N}"
+    p = wl.config_scalar(N=N or 1024)
+    return p, f"scalar_g0.5_N{p.N}"
 
 
 # ----------------------------------------------------------------------------- flops model
@@ -106,14 +110,11 @@ def flop_model(p, precision):
     if p.space == 1:
         K2 = 2 * (p.M + 1)
         sine = 2 * nsolve * (ncols / 2) * 5 * K2 * math.log2(K2)
-    if precision == "mixed":  # residual product of length 2Np in double
+    out = {"block_solve": block, "conv_smem": conv_smem, "conv_fourstep": conv_4, "sine": sine}
+    if precision == "mixed":  # residual product of length 2Np in float-float
         n = 2 * Np
-        fl = P * (10 * n * math.log2(n) + 6 * n)
-        if n <= 4096:
-            conv_smem += fl
-        else:
-            conv_4 += fl
-    return {"block_solve": block, "conv_smem": conv_smem, "conv_fourstep": conv_4, "sine": sine}
+        out["residual"] = P * (10 * n * math.log2(n) + 6 * n)
+    return out
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -190,7 +191,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    p, wname = workload(args.workload, args.nprob)
+    p, wname = workload(args.workload, args.nprob, M=args.M, N=args.N)
     if isinstance(p, list):
         p = p[0]
     nprefix = min(p.N, 1024 if p.M > 1 else p.N)
@@ -357,7 +358,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     ftoep.load()
 
-    p, wname = workload(args.workload)
+    p, wname = workload(args.workload, M=args.M, N=args.N)
     precision = args.precision or ("mixed" if args.workload == "wave" else "fp64")
     prec = ftoep.FP64 if precision == "fp64" else ftoep.MIXED
     spec = ftoep.ProblemSpec(p.kind, p.gamma, p.N, p.M, p.space, prec, lam=p.lam)
@@ -406,14 +407,14 @@ def run_ours(args):
     if dom[0] in model and dom[1][0] > 0 and model[dom[0]] > 0:
         flops = model[dom[0]] * args.steps
         ach = flops / (dom[1][0] * 1e-3) / 1e12
-        fp32_class = precision == "mixed" and dom[0] != "block_solve"
-        peak = FP64_PEAK_TFLOPS
+        if precision == "mixed" and dom[0] != "residual":
+            peak, what = FP32_PEAK_TFLOPS, "FP32 (152 SMs x 128 lanes x 2 x 2.07 GHz)"
+        else:
+            peak, what = FP64_PEAK_TFLOPS, "FP64 (recipe nominal 1.25; DFMA probe 1.19)"
         roof = {"bound": "alu", "kernel_class": dom[0], "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": None, "per_launch_ms": dom[1][0] / max(1, dom[1][1]),
-                "note": "FP64 ALU bound; nominal flops (5 n log2 n per complex FFT of length n, 6 per "
-                        "complex product); peak = recipe nominal FP64 (1.25), DFMA probe 1.19"}
-        if fp32_class:
-            roof["note"] += "; class mixes FP32 transforms with the FP64 residual product"
+                "note": "nominal flops (5 n log2 n per complex FFT of length n, 6 per complex product) of "
+                        "the class / its CUDA-event time; peak = " + what}
 
     # end to end: same solve through the C ABI with pinned HOST buffers (copies inside)
     fh = f.cpu().pin_memory()

@@ -150,7 +150,8 @@ typedef enum {
   FTOEP_K_CONV_SMEM = 1,      /* cross-block circulant convolution, one shared-memory FFT   */
   FTOEP_K_CONV_FOURSTEP = 2,  /* cross-block circulant convolution, three-kernel four-step  */
   FTOEP_K_SINE = 3,           /* sine transforms along space                                */
-  FTOEP_K_OTHER = 4           /* packing, residual, reductions, spectra                     */
+  FTOEP_K_OTHER = 4,          /* packing, time sums, reductions, spectra                    */
+  FTOEP_K_RESIDUAL = 5        /* mixed path: float-float residual product and residual      */
 } ftoep_kernel_class;
 
 /* Instrumentation (no counterpart in the paper).  ftoep_profile waits for the stream,

@@ -27,7 +27,7 @@ using namespace ftoep;
 namespace {
 
 constexpr int kMaxStreams = 4;
-constexpr int kNumClasses = 5;
+constexpr int kNumClasses = 6;
 constexpr int kDotBlocks = 1024;
 
 struct Prob {
@@ -129,9 +129,9 @@ struct ftoep_plan_s {
   std::vector<void*> allocs;
   // launch counters (always on) and optional CUDA-event timing per kernel class
   bool prof_on = false;
-  int64_t launches[kNumClasses] = {0, 0, 0, 0, 0};
-  double prof_ms[kNumClasses] = {0, 0, 0, 0, 0};
-  int64_t prof_ops[kNumClasses] = {0, 0, 0, 0, 0};
+  int64_t launches[kNumClasses] = {0, 0, 0, 0, 0, 0};
+  double prof_ms[kNumClasses] = {0, 0, 0, 0, 0, 0};
+  int64_t prof_ops[kNumClasses] = {0, 0, 0, 0, 0, 0};
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
   std::vector<cudaEvent_t> evpool;
 };
@@ -383,9 +383,10 @@ DstArgs dst_args(ftoep_plan pl, const Prob& pb, Prec pr, void* z) {
 }
 
 // y = T x on nlines lines of length N (double in and out, arithmetic in precision pr:
-// double or float-float), through the product workspace.
+// double or float-float), through the product workspace.  cls >= 0 books every launch
+// under that kernel class instead of the transform/convolution classes.
 ftoep_status product_lines(ftoep_plan pl, Ws& w, Prob& pb, Prec pr, const void* spec, const double* x,
-                           double* y_or_null, int64_t nlines, int reverse) {
+                           double* y_or_null, int64_t nlines, int reverse, int cls = -1) {
   cudaStream_t st = w.st;
   PackArgs pa{};
   pa.x = x;
@@ -394,7 +395,7 @@ ftoep_status product_lines(ftoep_plan pl, Ws& w, Prob& pb, Prec pr, const void* 
   pa.N = pb.N;
   pa.nlines = nlines;
   pa.reverse = reverse;
-  LAUNCH(FTOEP_K_OTHER, launch_pack(pr, pa, st));
+  LAUNCH(cls >= 0 ? cls : FTOEP_K_OTHER, launch_pack(pr, pa, st));
   ConvArgs ca{};
   ca.zin = w.zmv;
   ca.zout = w.zmv;
@@ -407,11 +408,12 @@ ftoep_status product_lines(ftoep_plan pl, Ws& w, Prob& pb, Prec pr, const void* 
   ca.spec = spec;
   ca.tw = tw_of(pl, pr);
   ca.scratch = w.scratch_mv;
-  LAUNCH((2 * pb.Np <= nsmem_for(pr)) ? FTOEP_K_CONV_SMEM : FTOEP_K_CONV_FOURSTEP, launch_conv(pr, ca, st));
+  LAUNCH(cls >= 0 ? cls : (2 * pb.Np <= nsmem_for(pr)) ? FTOEP_K_CONV_SMEM : FTOEP_K_CONV_FOURSTEP,
+         launch_conv(pr, ca, st));
   if (y_or_null) {
     pa.y = y_or_null;
     pa.mode = 0;
-    LAUNCH(FTOEP_K_OTHER, launch_unpack(pr, pa, st));
+    LAUNCH(cls >= 0 ? cls : FTOEP_K_OTHER, launch_unpack(pr, pa, st));
   }
   return FTOEP_OK;
 }
@@ -465,7 +467,7 @@ ftoep_status solve_problem(ftoep_plan pl, Ws& w, Prob& pb, const double* f, doub
   TRY(scan_lines(pl, w, pb, w.r, u, u0, 0, 0));
   // residual of the same rows in the difference form, r = f + c tau M phi - E v - S u,
   // with the Toeplitz product E v in float-float (no tau^-g cancellation in this form)
-  TRY(product_lines(pl, w, pb, PFF, pb.spec_res, w.r, nullptr, pb.M, 0));
+  TRY(product_lines(pl, w, pb, PFF, pb.spec_res, w.r, nullptr, pb.M, 0, FTOEP_K_RESIDUAL));
   ResidualArgs ra{};
   ra.f = f;
   ra.u0 = nullptr;
@@ -482,7 +484,7 @@ ftoep_status solve_problem(ftoep_plan pl, Ws& w, Prob& pb, const double* f, doub
   ra.space = pb.d.space;
   ra.inv_h2 = 1.0 / (pb.h * pb.h);
   ra.lambda = pb.d.lambda;
-  LAUNCH(FTOEP_K_OTHER, launch_residual(ra, st));
+  LAUNCH(FTOEP_K_RESIDUAL, launch_residual(ra, st));
   // correction: same rows, zero initial data; v-correction lands in r, then u += tau cumsum
   DstArgs dr = dst_args(pl, pb, pr, w.z);
   dr.f = w.r;

@@ -15,6 +15,7 @@
 //     C1 = (H_a + H_b)/2, C2 = (H_a - H_b)/2,  partner of frequency k: n - k,
 // and H_a, H_b themselves are split out of FFT(h_a + i h_b) the same way.
 #include "fft.cuh"
+#include "fftr.cuh"
 #include "internal.h"
 
 namespace ftoep {
@@ -69,72 +70,97 @@ __global__ void __launch_bounds__(kThreads) inverse_spectrum_kernel(InvSpecArgs 
   }
 }
 
+// y - lambda tau S for one component: double arithmetic for the double path; for the
+// float path S' = lambda tau S is split into a float pair (hi + lo) once per block, so the
+// per-element work stays in FP32 (GB300 runs FP64 at 1/64 of the FP32 rate).
+__device__ __forceinline__ double shift_sub(double y, double sh, double) { return y - sh; }
+__device__ __forceinline__ float shift_sub(float y, float sh, float sl) { return (y - sh) - sl; }
+
+// s + c += x with the rounding error of the addition kept in c (Knuth two-sum); the double
+// path adds directly (c stays 0).
+__device__ __forceinline__ void acc2(double& s, double&, double x) { s += x; }
+__device__ __forceinline__ void acc2(float& s, float& c, float x) {
+  const float t = s + x;
+  const float bb = t - s;
+  c += (s - (t - bb)) + (x - bb);
+  s = t;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) block_inverse_kernel(BlockInvArgs A) {
   typedef Vt<T> V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
-  __shared__ double red[2][kThreads / 32];
+  __shared__ T red[4][kThreads];
   const int B = A.B, logn = A.logB + 1, n = 2 * B;
   const int64_t p = blockIdx.x;
-  V* zg = (V*)A.z + p * A.ld + A.t0;
+  V* __restrict__ zg = (V*)A.z + p * A.ld + A.t0;
   const double2 S = A.prefix[p];
   const double2 lt = A.lamtau[p];
   const double sx = lt.x * S.x, sy = lt.y * S.y;
-  for (int i = threadIdx.x; i < B; i += blockDim.x) {
-    const V y = zg[i];
-    sm[i] = mkv((T)((double)y.x - sx), (T)((double)y.y - sy));
-  }
+  const T sxh = (T)sx, syh = (T)sy;
+  const T sxl = (T)(sx - (double)sxh), syl = (T)(sy - (double)syh);
+  const V* __restrict__ tw = (const V*)A.tw;
+  const SmLayout L = sm_layout<V>(logn);
+  const int np = fftr_npasses<V>(logn);
+  fftr_pass<V, true>(0, logn, 1, tw, true, [&](int, int e) {
+    const V y = zg[e];
+    return mkv(shift_sub(y.x, sxh, sxl), shift_sub(y.y, syh, syl));
+  }, SmPut<V>{sm, L});
   __syncthreads();
-  const V* tw = (const V*)A.tw;
-  fft_dif<V>(sm, logn, 1, 0, tw, true);
-  const V* c1 = (const V*)A.c1 + p * (int64_t)n;
-  const V* c2 = (const V*)A.c2 + p * (int64_t)n;
+  fftr_passes<V, true>(sm, logn, 1, tw, 1, np, false);
+  const V* __restrict__ c1 = (const V*)A.c1 + p * (int64_t)n;
+  const V* __restrict__ c2 = (const V*)A.c2 + p * (int64_t)n;
   for (int pos = threadIdx.x; pos < n; pos += blockDim.x) {
     const int pp = partner_pos(pos, logn);
     if (pp < pos) continue;
-    const V z1 = sm[pos];
+    const int q1 = sm_pos<V>(L, 0, pos);
+    const V z1 = sm[q1];
     if (pp == pos) {
       V zc;
       zc.x = z1.x;
       zc.y = -z1.y;
-      sm[pos] = cadd(cmul(c1[pos], z1), cmul(c2[pos], zc));
+      sm[q1] = cadd(cmul(c1[pos], z1), cmul(c2[pos], zc));
     } else {
-      const V z2 = sm[pp];
+      const int q2 = sm_pos<V>(L, 0, pp);
+      const V z2 = sm[q2];
       V z1c, z2c;
       z1c.x = z1.x;
       z1c.y = -z1.y;
       z2c.x = z2.x;
       z2c.y = -z2.y;
-      sm[pos] = cadd(cmul(c1[pos], z1), cmul(c2[pos], z2c));
-      sm[pp] = cadd(cmul(c1[pp], z2), cmul(c2[pp], z1c));
+      sm[q1] = cadd(cmul(c1[pos], z1), cmul(c2[pos], z2c));
+      sm[q2] = cadd(cmul(c1[pp], z2), cmul(c2[pp], z1c));
     }
   }
   __syncthreads();
-  fft_dit<V>(sm, logn, 1, 0, tw, 2);
-  double ax = 0.0, ay = 0.0;
-  for (int i = threadIdx.x; i < B; i += blockDim.x) {
-    const V x = sm[i];
-    zg[i] = x;
-    ax += (double)x.x;
-    ay += (double)x.y;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    ax += __shfl_xor_sync(0xffffffffu, ax, o);
-    ay += __shfl_xor_sync(0xffffffffu, ay, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = ax;
-    red[1][threadIdx.x >> 5] = ay;
-  }
+  fftr_passes<V, false>(sm, logn, 1, tw, 0, np - 1, false);
+  // block sums of x for the running prefix: compensated (two-sum) per thread, then the
+  // per-thread pairs are added in double by one warp
+  T ax = (T)0, ay = (T)0, cx = (T)0, cy = (T)0;
+  fftr_pass<V, false>(np - 1, logn, 1, tw, false, SmAt<V>{sm, L}, [&](int, int e, const V& x) {
+    if (e < B) {
+      zg[e] = x;
+      acc2(ax, cx, x.x);
+      acc2(ay, cy, x.y);
+    }
+  });
+  red[0][threadIdx.x] = ax;
+  red[1][threadIdx.x] = ay;
+  red[2][threadIdx.x] = cx;
+  red[3][threadIdx.x] = cy;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
     double tx = 0.0, ty = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) {
-      tx += red[0][w];
-      ty += red[1][w];
+    for (int k = threadIdx.x; k < kThreads; k += 32) {
+      tx += (double)red[0][k] + (double)red[2][k];
+      ty += (double)red[1][k] + (double)red[3][k];
     }
-    A.prefix[p] = make_double2(S.x + tx, S.y + ty);
+    for (int o = 16; o > 0; o >>= 1) {
+      tx += __shfl_xor_sync(0xffffffffu, tx, o);
+      ty += __shfl_xor_sync(0xffffffffu, ty, o);
+    }
+    if (threadIdx.x == 0) A.prefix[p] = make_double2(S.x + tx, S.y + ty);
   }
 }
 

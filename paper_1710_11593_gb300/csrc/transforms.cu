@@ -8,6 +8,7 @@
 #include <cstdio>
 
 #include "fft.cuh"
+#include "fftr.cuh"
 #include "internal.h"
 
 namespace ftoep {
@@ -18,6 +19,12 @@ constexpr int kThreads = 256;
 
 template <typename T>
 using Vt = typename VecOf<T>::type;
+
+// Host-side copy of the pass radix of each arithmetic type (fftr.cuh EngineTraits).
+template <typename T> struct EngineTraitsHost;
+template <> struct EngineTraitsHost<float> { static constexpr int RB = 4; };
+template <> struct EngineTraitsHost<double> { static constexpr int RB = 3; };
+template <> struct EngineTraitsHost<FF> { static constexpr int RB = 3; };
 
 inline void set_smem(const void* fn, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -657,92 +664,119 @@ void spectrum_launch(const SpecArgs& a, cudaStream_t st) {
 
 // ------------------------------------------------------------------ convolution
 
-// One block per pair; the whole length-n transform in shared memory.
+// Pointwise product of spectrum values with a kernel spectrum in the same storage order
+// (the op of fftr_middle): x[j] *= spec[pos0 + j].
+template <typename V>
+struct SpecMul {
+  const V* __restrict__ spec;
+  template <class X, class RR>
+  __device__ __forceinline__ void operator()(int t, int pos0, X& x, RR) const {
+    (void)t;
+    static_for<0, RR::value>([&](auto JJ) {
+      constexpr int j = decltype(JJ)::value;
+      x[j] = cmul(x[j], spec[pos0 + j]);
+    });
+  }
+};
+
+// One block per pair; the whole length-n transform in shared memory.  The first forward
+// pass reads the input half straight from global memory, the last forward pass, the
+// product with the kernel spectrum and the first inverse pass run fused in registers, and
+// the last inverse pass writes (mode 0: subtracts) the wanted half straight to global.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) conv_smem_kernel(ConvArgs A) {
   typedef Vt<T> V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
-  const int n = 1 << A.logn, s = n >> 1;
+  const int logn = A.logn, s = 1 << (logn - 1);
   const int64_t p = blockIdx.x;
-  const V* zin = (const V*)A.zin + p * A.ld_in + A.in_off;
-  for (int i = threadIdx.x; i < s; i += blockDim.x) sm[i] = zin[i];
+  const V* __restrict__ zin = (const V*)A.zin + p * A.ld_in + A.in_off;
+  V* __restrict__ zo = (V*)A.zout + p * A.ld_out + A.out_off;
+  const V* __restrict__ tw = (const V*)A.tw;
+  const SmLayout L = sm_layout<V>(logn);
+  const int np = fftr_npasses<V>(logn);
+  fftr_pass<V, true>(0, logn, 1, tw, true, [&](int, int e) { return zin[e]; }, SmPut<V>{sm, L});
   __syncthreads();
-  const V* tw = (const V*)A.tw;
-  fft_dif<V>(sm, A.logn, 1, 0, tw, true);
-  const V* spec = (const V*)A.spec;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) sm[k] = cmul(sm[k], spec[k]);
-  __syncthreads();
-  fft_dit<V>(sm, A.logn, 1, 0, tw, A.mode == 0 ? 1 : 2);
-  V* zo = (V*)A.zout + p * A.ld_out + A.out_off;
-  if (A.mode == 0) {
-    for (int i = threadIdx.x; i < s; i += blockDim.x) zo[i] = csub(zo[i], sm[s + i]);
+  if (np < 2) {  // a single pass: plain product in shared memory
+    for (int k = threadIdx.x; k < 2 * s; k += blockDim.x) {
+      const int q = sm_pos<V>(L, 0, k);
+      sm[q] = cmul(sm[q], ((const V*)A.spec)[k]);
+    }
+    __syncthreads();
   } else {
-    for (int i = threadIdx.x; i < s; i += blockDim.x) zo[i] = sm[i];
+    fftr_passes<V, true>(sm, logn, 1, tw, 1, np - 1, false);
+    fftr_middle<V>(sm, logn, 1, SpecMul<V>{(const V*)A.spec});
+    __syncthreads();
+    fftr_passes<V, false>(sm, logn, 1, tw, 1, np - 1, false);
+  }
+  if (A.mode == 0) {
+    fftr_pass<V, false>(np - 1, logn, 1, tw, false, SmAt<V>{sm, L}, [&](int, int e, const V& v) {
+      if (e >= s) zo[e - s] = csub(zo[e - s], v);
+    });
+  } else {
+    fftr_pass<V, false>(np - 1, logn, 1, tw, false, SmAt<V>{sm, L}, [&](int, int e, const V& v) {
+      if (e < s) zo[e] = v;
+    });
   }
 }
 
-// Four-step: n = n1*n2, index j = j1*n2 + j2.  Step A transforms columns (over j1),
-// applies W_n^{j2 k1}; step B transforms rows (over j2), multiplies by the spectrum
-// (stored in the same order), inverts the rows and removes the twiddle; step C inverts
-// the columns.  Column transforms leave k1 in bit-reversed row order, which the
-// twiddles account for.
+// Four-step: n = n1*n2, index j = j1*n2 + j2.  Step A transforms C columns (over j1) per
+// block, applies W_n^{j2 k1} and writes the scratch; step B transforms `rows` rows (over
+// j2) per block, multiplies by the spectrum (stored in the same order), inverts the rows
+// and removes the twiddle; step C inverts the columns.  Column transforms leave k1 in
+// bit-reversed row order, which the twiddles account for.  Column kernels map consecutive
+// threads to consecutive columns (coalesced global access); the first and last passes of
+// every kernel read or write global memory directly.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) conv_col_fwd_kernel(ConvArgs A, int logn1, int logn2, int C) {
   typedef Vt<T> V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
-  const int n1 = 1 << logn1, n2 = 1 << logn2, n = n1 * n2, h1 = n1 >> 1;
-  const int lds = n1 + 1;
+  const int n2 = 1 << logn2, logn = logn1 + logn2, n = 1 << logn;
   const int c0 = blockIdx.x * C;
   const int64_t p = blockIdx.y;
-  const V* zin = (const V*)A.zin + p * A.ld_in + A.in_off;
-  for (int e0 = threadIdx.x; e0 < h1 * C; e0 += 4 * blockDim.x) {
-    V v[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = e0 + q * blockDim.x;
-      if (e < h1 * C) v[q] = zin[(int64_t)(e / C) * n2 + c0 + e % C];
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = e0 + q * blockDim.x;
-      if (e < h1 * C) sm[(e % C) * lds + e / C] = v[q];
-    }
-  }
+  const V* __restrict__ zin = (const V*)A.zin + p * A.ld_in + A.in_off + c0;
+  V* __restrict__ sc = (V*)A.scratch + p * (int64_t)n + c0;
+  const V* __restrict__ tw = (const V*)A.tw;
+  const V* __restrict__ twn = tw + (n - 2);
+  const SmLayout L = sm_layout<V>(logn1);
+  const int np = fftr_npasses<V>(logn1);
+  fftr_pass<V, true, true>(0, logn1, C, tw, true, [&](int t, int e) { return zin[(int64_t)e * n2 + t]; },
+                           SmPut<V>{sm, L});
   __syncthreads();
-  const V* tw = (const V*)A.tw;
-  fft_dif<V>(sm, logn1, C, lds, tw, true);
-  const V* twn = tw + (n - 2);
-  V* sc = (V*)A.scratch + p * (int64_t)n;
-  for (int e = threadIdx.x; e < n1 * C; e += blockDim.x) {
-    const int r = e / C, c = e % C;
-    const int j2 = c0 + c;
-    const int k1 = brev(r, logn1);
-    sc[(int64_t)r * n2 + j2] = cmul(sm[c * lds + r], twn[(int64_t)j2 * k1 & (n - 1)]);
-  }
+  fftr_passes<V, true, true>(sm, logn1, C, tw, 1, np - 1, false);
+  fftr_pass<V, true, true>(np - 1, logn1, C, tw, false, SmAt<V>{sm, L}, [&](int t, int e, const V& v) {
+    const int k1 = brev(e, logn1);
+    sc[(int64_t)e * n2 + t] = cmul(v, twn[((int64_t)(c0 + t) * k1) & (n - 1)]);
+  });
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) conv_row_kernel(ConvArgs A, int logn1, int logn2) {
+__global__ void __launch_bounds__(kThreads) conv_row_kernel(ConvArgs A, int logn1, int logn2, int rows) {
   typedef Vt<T> V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
-  const int n2 = 1 << logn2, n = n2 << logn1;
-  const int r = blockIdx.x;
+  const int n2 = 1 << logn2, logn = logn1 + logn2, n = 1 << logn;
+  const int r0 = blockIdx.x * rows;
   const int64_t p = blockIdx.y;
-  V* sc = (V*)A.scratch + p * (int64_t)n + (int64_t)r * n2;
-  for (int k = threadIdx.x; k < n2; k += blockDim.x) sm[k] = sc[k];
+  V* __restrict__ sc = (V*)A.scratch + p * (int64_t)n + (int64_t)r0 * n2;
+  const V* __restrict__ tw = (const V*)A.tw;
+  const V* __restrict__ twn = tw + (n - 2);
+  const SmLayout L = sm_layout<V>(logn2);
+  const int np = fftr_npasses<V>(logn2);
+  fftr_pass<V, true>(0, logn2, rows, tw, false, [&](int t, int e) { return sc[t * n2 + e]; }, SmPut<V>{sm, L});
   __syncthreads();
-  const V* tw = (const V*)A.tw;
-  fft_dif<V>(sm, logn2, 1, 0, tw, false);
-  const V* spec = (const V*)A.spec + (int64_t)r * n2;
-  for (int k = threadIdx.x; k < n2; k += blockDim.x) sm[k] = cmul(sm[k], spec[k]);
+  fftr_passes<V, true>(sm, logn2, rows, tw, 1, np - 1, false);
+  const V* __restrict__ spec = (const V*)A.spec + (int64_t)r0 * n2;
+  fftr_middle<V>(sm, logn2, rows, [&](int t, int pos0, auto& x, auto RR) {
+    SpecMul<V>{spec + t * n2}(t, pos0, x, RR);
+  });
   __syncthreads();
-  fft_dit<V>(sm, logn2, 1, 0, tw, 0);
-  const V* twn = tw + (n - 2);
-  const int k1 = brev(r, logn1);
-  for (int j2 = threadIdx.x; j2 < n2; j2 += blockDim.x) sc[j2] = cmulc(sm[j2], twn[(int64_t)j2 * k1 & (n - 1)]);
+  fftr_passes<V, false>(sm, logn2, rows, tw, 1, np - 1, false);
+  fftr_pass<V, false>(np - 1, logn2, rows, tw, false, SmAt<V>{sm, L}, [&](int t, int e, const V& v) {
+    const int k1 = brev(r0 + t, logn1);
+    sc[t * n2 + e] = cmulc(v, twn[((int64_t)e * k1) & (n - 1)]);
+  });
 }
 
 template <typename T>
@@ -750,36 +784,49 @@ __global__ void __launch_bounds__(kThreads) conv_col_inv_kernel(ConvArgs A, int 
   typedef Vt<T> V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
-  const int n1 = 1 << logn1, n2 = 1 << logn2, n = n1 * n2, h1 = n1 >> 1;
-  const int lds = n1 + 1;
+  const int n2 = 1 << logn2, logn = logn1 + logn2, n = 1 << logn, h1 = 1 << (logn1 - 1);
   const int c0 = blockIdx.x * C;
   const int64_t p = blockIdx.y;
-  const V* sc = (const V*)A.scratch + p * (int64_t)n;
-  for (int e0 = threadIdx.x; e0 < n1 * C; e0 += 4 * blockDim.x) {
-    V v[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = e0 + q * blockDim.x;
-      if (e < n1 * C) v[q] = sc[(int64_t)(e / C) * n2 + c0 + e % C];
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = e0 + q * blockDim.x;
-      if (e < n1 * C) sm[(e % C) * lds + e / C] = v[q];
-    }
-  }
+  const V* __restrict__ sc = (const V*)A.scratch + p * (int64_t)n + c0;
+  V* __restrict__ zo = (V*)A.zout + p * A.ld_out + A.out_off + c0;
+  const V* __restrict__ tw = (const V*)A.tw;
+  const SmLayout L = sm_layout<V>(logn1);
+  const int np = fftr_npasses<V>(logn1);
+  fftr_pass<V, false, true>(0, logn1, C, tw, false, [&](int t, int e) { return sc[(int64_t)e * n2 + t]; },
+                            SmPut<V>{sm, L});
   __syncthreads();
-  fft_dit<V>(sm, logn1, C, lds, (const V*)A.tw, A.mode == 0 ? 1 : 2);
-  V* zo = (V*)A.zout + p * A.ld_out + A.out_off;
-  for (int e = threadIdx.x; e < h1 * C; e += blockDim.x) {
-    const int jj = e / C, c = e % C;
-    const int64_t o = (int64_t)jj * n2 + c0 + c;
-    if (A.mode == 0) {
-      zo[o] = csub(zo[o], sm[c * lds + h1 + jj]);
-    } else {
-      zo[o] = sm[c * lds + jj];
-    }
+  fftr_passes<V, false, true>(sm, logn1, C, tw, 1, np - 1, false);
+  if (A.mode == 0) {
+    fftr_pass<V, false, true>(np - 1, logn1, C, tw, false, SmAt<V>{sm, L}, [&](int t, int e, const V& v) {
+      if (e >= h1) {
+        V* q = zo + (int64_t)(e - h1) * n2 + t;
+        *q = csub(*q, v);
+      }
+    });
+  } else {
+    fftr_pass<V, false, true>(np - 1, logn1, C, tw, false, SmAt<V>{sm, L}, [&](int t, int e, const V& v) {
+      if (e < h1) zo[(int64_t)e * n2 + t] = v;
+    });
   }
+}
+
+// Columns per block of the four-step column kernels (power of two): 128-byte row
+// segments, at most 64 KB of shared memory.
+template <typename T>
+int fourstep_cols(int logn1, int logn2) {
+  int C = 128 / (int)sizeof(Vt<T>);
+  while (C > 2 && (size_t)C * ((size_t)1 << logn1) * sizeof(Vt<T>) > 64 * 1024) C >>= 1;
+  while (C > 1 && C > (1 << logn2)) C >>= 1;
+  return C;
+}
+// Rows per block of the row kernel: about 16 elements per thread per pass.
+template <typename T>
+int fourstep_rows(int logn1, int logn2) {
+  const int per = kThreads * (1 << EngineTraitsHost<T>::RB);
+  int rows = per >> logn2;
+  if (rows < 1) rows = 1;
+  if (rows > (1 << logn1)) rows = 1 << logn1;
+  return rows;
 }
 
 template <typename T>
@@ -792,16 +839,17 @@ void conv_launch(const ConvArgs& a, cudaStream_t st) {
     return;
   }
   Split sp = split_of(a.logn);
-  const int C = four_step_cols<T>(sp.logn1);
-  const size_t smc = (size_t)C * ((size_t)(1 << sp.logn1) + 1) * sizeof(Vt<T>);
-  const size_t smr = (size_t)(1 << sp.logn2) * sizeof(Vt<T>);
+  const int C = fourstep_cols<T>(sp.logn1, sp.logn2);
+  const int rows = fourstep_rows<T>(sp.logn1, sp.logn2);
+  const size_t smc = (size_t)C * ((size_t)1 << sp.logn1) * sizeof(Vt<T>);
+  const size_t smr = (size_t)rows * ((size_t)1 << sp.logn2) * sizeof(Vt<T>);
   dim3 gc((unsigned)((1 << sp.logn2) / C), (unsigned)a.npairs);
-  dim3 gr((unsigned)(1 << sp.logn1), (unsigned)a.npairs);
+  dim3 gr((unsigned)((1 << sp.logn1) / rows), (unsigned)a.npairs);
   set_smem((const void*)conv_col_fwd_kernel<T>, smc);
   set_smem((const void*)conv_row_kernel<T>, smr);
   set_smem((const void*)conv_col_inv_kernel<T>, smc);
   conv_col_fwd_kernel<T><<<gc, kThreads, smc, st>>>(a, sp.logn1, sp.logn2, C);
-  conv_row_kernel<T><<<gr, kThreads, smr, st>>>(a, sp.logn1, sp.logn2);
+  conv_row_kernel<T><<<gr, kThreads, smr, st>>>(a, sp.logn1, sp.logn2, rows);
   conv_col_inv_kernel<T><<<gc, kThreads, smc, st>>>(a, sp.logn1, sp.logn2, C);
 }
 

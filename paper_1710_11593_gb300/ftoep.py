@@ -27,9 +27,9 @@ FP64, MIXED = 0, 1
 
 EXPORTS = ("ftoep_create", "ftoep_weights", "ftoep_solve", "ftoep_matvec", "ftoep_adjoint", "ftoep_profile",
            "ftoep_profile_read", "ftoep_sync", "ftoep_last_error", "ftoep_destroy")
-K_BLOCK_SOLVE, K_CONV_SMEM, K_CONV_FOURSTEP, K_SINE, K_OTHER = range(5)
+K_BLOCK_SOLVE, K_CONV_SMEM, K_CONV_FOURSTEP, K_SINE, K_OTHER, K_RESIDUAL = range(6)
 KERNEL_CLASSES = {K_BLOCK_SOLVE: "block_solve", K_CONV_SMEM: "conv_smem", K_CONV_FOURSTEP: "conv_fourstep",
-                  K_SINE: "sine", K_OTHER: "other"}
+                  K_SINE: "sine", K_OTHER: "other", K_RESIDUAL: "residual"}
 
 
 class FtoepError(RuntimeError):
