@@ -372,6 +372,7 @@ DstArgs dst_args(ftoep_plan pl, const Prob& pb, Prec pr, void* z) {
   da.inv_h2 = 1.0 / (pb.h * pb.h);
   da.lambda = pb.d.lambda;
   da.tw = tw_of(pl, pr);
+  da.dst_scale = 1.0 / std::sqrt(2.0 * (double)(pb.M + 1));
   if (pb.bluestein) {
     da.bluestein = 1;
     da.K = (int)(pb.M + 1);
@@ -386,10 +387,11 @@ DstArgs dst_args(ftoep_plan pl, const Prob& pb, Prec pr, void* z) {
 // double or float-float), through the product workspace.  cls >= 0 books every launch
 // under that kernel class instead of the transform/convolution classes.
 ftoep_status product_lines(ftoep_plan pl, Ws& w, Prob& pb, Prec pr, const void* spec, const double* x,
-                           double* y_or_null, int64_t nlines, int reverse, int cls = -1) {
+                           double* y_or_null, int64_t nlines, int reverse, int cls = -1, const float* x32 = nullptr) {
   cudaStream_t st = w.st;
   PackArgs pa{};
   pa.x = x;
+  pa.x32 = x32;
   pa.z = w.zmv;
   pa.ld = pb.Np;
   pa.N = pb.N;
@@ -418,12 +420,16 @@ ftoep_status product_lines(ftoep_plan pl, Ws& w, Prob& pb, Prec pr, const void* 
   return FTOEP_OK;
 }
 
-// Time sums along every line: u = base + tau * cumsum(in) (or tau * suffix sums).
+// Time sums along every line: u = base + tau * cumsum(in) (or tau * suffix sums); in32:
+// float input (forward only).
 ftoep_status scan_lines(ftoep_plan pl, Ws& w, Prob& pb, const double* in, double* out, const double* u0, int accumulate,
-                        int reverse) {
+                        int reverse, const float* in32 = nullptr) {
   cudaStream_t st = w.st;
   ScanArgs sc{};
   sc.in = in;
+  sc.in32 = in32;
+  sc.tau_h = (float)pb.tau;
+  sc.tau_l = (float)(pb.tau - (double)sc.tau_h);
   sc.out = out;
   sc.u0 = u0;
   sc.N = pb.N;
@@ -460,14 +466,16 @@ ftoep_status solve_problem(ftoep_plan pl, Ws& w, Prob& pb, const double* f, doub
     TRY(scan_lines(pl, w, pb, u, u, u0, 0, 0));
     return FTOEP_OK;
   }
-  // mixed: keep the solved v (physical space) in r, u = u0 + tau cumsum(v)
-  da.u = w.r;
+  // mixed: the solved v (physical space) in float in r, u = u0 + tau cumsum(v)
+  float* r32 = (float*)w.r;
+  da.u = nullptr;
+  da.u32 = r32;
   da.accumulate = 0;
   LAUNCH(FTOEP_K_SINE, launch_dst_inverse(pr, da, st));
-  TRY(scan_lines(pl, w, pb, w.r, u, u0, 0, 0));
+  TRY(scan_lines(pl, w, pb, nullptr, u, u0, 0, 0, r32));
   // residual of the same rows in the difference form, r = f + c tau M phi - E v - S u,
   // with the Toeplitz product E v in float-float (no tau^-g cancellation in this form)
-  TRY(product_lines(pl, w, pb, PFF, pb.spec_res, w.r, nullptr, pb.M, 0, FTOEP_K_RESIDUAL));
+  TRY(product_lines(pl, w, pb, PFF, pb.spec_res, nullptr, nullptr, pb.M, 0, FTOEP_K_RESIDUAL, r32));
   ResidualArgs ra{};
   ra.f = f;
   ra.u0 = nullptr;
@@ -476,8 +484,7 @@ ftoep_status solve_problem(ftoep_plan pl, Ws& w, Prob& pb, const double* f, doub
   ra.wphi = pb.wphi;
   ra.u = u;
   ra.tu = w.zmv;
-  ra.tu_ff = 1;
-  ra.r = w.r;
+  ra.r32 = r32;
   ra.ld = pb.Np;
   ra.N = pb.N;
   ra.M = pb.M;
@@ -487,14 +494,14 @@ ftoep_status solve_problem(ftoep_plan pl, Ws& w, Prob& pb, const double* f, doub
   LAUNCH(FTOEP_K_RESIDUAL, launch_residual(ra, st));
   // correction: same rows, zero initial data; v-correction lands in r, then u += tau cumsum
   DstArgs dr = dst_args(pl, pb, pr, w.z);
-  dr.f = w.r;
+  dr.f32 = r32;
   dr.diff_form = 1;
   LAUNCH(FTOEP_K_SINE, launch_dst_forward(pr, dr, st));
   TRY(solve_pairs(pl, w, pb, pr, w.z, pb.spec));
-  dr.u = w.r;
+  dr.u32 = r32;
   dr.accumulate = 0;
   LAUNCH(FTOEP_K_SINE, launch_dst_inverse(pr, dr, st));
-  TRY(scan_lines(pl, w, pb, w.r, u, nullptr, 1, 0));
+  TRY(scan_lines(pl, w, pb, nullptr, u, nullptr, 1, 0, r32));
   return FTOEP_OK;
 }
 
@@ -686,7 +693,8 @@ ftoep_status setup_problem(ftoep_plan pl, Prob& pb) {
   for (int64_t p = 0; p < pb.P; ++p) {
     double lam[2];
     for (int q = 0; q < 2; ++q) {
-      const int64_t m = 2 * p + q + 1;
+      // pair p: modes p+1 and M-p (sine transform); lines 2p, 2p+1 (no transform)
+      const int64_t m = q == 0 ? p + 1 : pb.M - p;
       if (pb.d.space) {
         const double sn = std::sin((double)m * 3.14159265358979323846 / (2.0 * (double)(pb.M + 1)));
         lam[q] = 4.0 / (pb.h * pb.h) * sn * sn;

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kThreads) block_inverse_kernel(BlockInvArgs A)
   const V* __restrict__ tw = (const V*)A.tw;
   const SmLayout L = sm_layout<V>(logn);
   const int np = fftr_npasses<V>(logn);
-  fftr_pass<V, true>(0, logn, 1, tw, true, [&](int, int e) {
+  fftr_pass<V, true, false, true>(0, logn, 1, tw, true, [&](int, int e) {
     const V y = zg[e];
     return mkv(shift_sub(y.x, sxh, sxl), shift_sub(y.y, syh, syl));
   }, SmPut<V>{sm, L});

@@ -316,49 +316,72 @@ __device__ __forceinline__ FftPlan fft_plan(int logn) {
 // TM (transform-major): consecutive threads take consecutive transforms (cnt a power of
 // two) -- the mapping for column transforms whose global loads are coalesced across
 // transforms; otherwise consecutive threads take consecutive units of one transform.
-template <typename V, int r, bool DIF, bool HZ, bool TM, class Ld, class St>
+template <typename V, int r, bool DIF, bool HZ, bool TM, int UB, bool RMW, class Ld, class St>
 __device__ __forceinline__ void run_pass(int logn, int cnt, int logg, const V* __restrict__ tw, Ld ld, St st) {
   constexpr int R = 1 << r;
   const int lm = logg - r;
   const int lu = logn - r;
   const int tot = cnt << lu;
-  for (int u = threadIdx.x; u < tot; u += blockDim.x) {
-    int t, b;
-    if constexpr (TM) {
-      t = u & (cnt - 1);
-      b = u / cnt;
-    } else {
-      t = u >> lu;
-      b = u & ((1 << lu) - 1);
-    }
-    const int grp = b >> lm, i = b & ((1 << lm) - 1);
-    const int e0 = (grp << logg) + i;
-    V x[R];
-    static_for<0, R>([&](auto JJ) {
-      constexpr int j = decltype(JJ)::value;
-      if constexpr (HZ && j >= R / 2) {
-        x[j] = vzero<V>();
+  // UB units per thread per iteration: all their loads (and, for a read-modify-write
+  // storer, the fetches of the values it updates) are issued before any arithmetic, which
+  // keeps UB*R global loads in flight
+  for (int u0 = threadIdx.x; u0 < tot; u0 += blockDim.x * UB) {
+    V x[UB][R];
+    [[maybe_unused]] V f[RMW ? UB : 1][RMW ? R : 1];
+    int tq[UB], e0q[UB], iq[UB];
+    static_for<0, UB>([&](auto QQ) {
+      constexpr int q = decltype(QQ)::value;
+      const int u = u0 + q * (int)blockDim.x;
+      int t, b;
+      if constexpr (TM) {
+        t = u & (cnt - 1);
+        b = u / cnt;
       } else {
-        x[j] = ld(t, e0 + (j << lm));
+        t = u >> lu;
+        b = u & ((1 << lu) - 1);
+      }
+      const int grp = b >> lm;
+      iq[q] = b & ((1 << lm) - 1);
+      tq[q] = t;
+      e0q[q] = (grp << logg) + iq[q];
+      if (UB == 1 || u < tot) {
+        static_for<0, R>([&](auto JJ) {
+          constexpr int j = decltype(JJ)::value;
+          if constexpr (HZ && j >= R / 2) {
+            x[q][j] = vzero<V>();
+          } else {
+            x[q][j] = ld(t, e0q[q] + (j << lm));
+          }
+          if constexpr (RMW) f[q][j] = st.fetch(t, e0q[q] + (j << lm));
+        });
       }
     });
-    if (lm == 0) {
-      if constexpr (DIF) dif_regs<V, r, HZ, false>(x, tw, logg, 0);
-      else dit_regs<V, r, false>(x, tw, logg, 0);
-    } else {
-      if constexpr (DIF) dif_regs<V, r, HZ, true>(x, tw, logg, i);
-      else dit_regs<V, r, true>(x, tw, logg, i);
-    }
-    static_for<0, R>([&](auto JJ) {
-      constexpr int j = decltype(JJ)::value;
-      st(t, e0 + (j << lm), x[j]);
+    static_for<0, UB>([&](auto QQ) {
+      constexpr int q = decltype(QQ)::value;
+      if (UB == 1 || u0 + q * (int)blockDim.x < tot) {
+        if (lm == 0) {
+          if constexpr (DIF) dif_regs<V, r, HZ, false>(x[q], tw, logg, 0);
+          else dit_regs<V, r, false>(x[q], tw, logg, 0);
+        } else {
+          if constexpr (DIF) dif_regs<V, r, HZ, true>(x[q], tw, logg, iq[q]);
+          else dit_regs<V, r, true>(x[q], tw, logg, iq[q]);
+        }
+        static_for<0, R>([&](auto JJ) {
+          constexpr int j = decltype(JJ)::value;
+          if constexpr (RMW) st(tq[q], e0q[q] + (j << lm), x[q][j], f[q][j]);
+          else st(tq[q], e0q[q] + (j << lm), x[q][j]);
+        });
+      }
     });
   }
 }
 
 // Pass p of the schedule (DIF pass p, or DIT pass p = DIF pass np-1-p) with the given
 // loader and storer.  No barrier.
-template <typename V, bool DIF, bool TM = false, class Ld, class St>
+// GL: the loader reads global memory (several units per thread keep loads in flight).
+// RMW: the storer updates global memory: st.fetch(t, e) is called in the load phase and
+// st(t, e, v, fetched) after the arithmetic.
+template <typename V, bool DIF, bool TM = false, bool GL = false, bool RMW = false, class Ld, class St>
 __device__ __forceinline__ void fftr_pass(int p, int logn, int cnt, const V* __restrict__ tw, bool half_zero, Ld ld,
                                           St st) {
   constexpr int RB = EngineTraits<V>::RB;
@@ -367,9 +390,14 @@ __device__ __forceinline__ void fftr_pass(int p, int logn, int cnt, const V* __r
   const int r = pd == 0 ? P.r0 : P.rb;
   const int logg = P.logg(pd);
   const bool hz = DIF && pd == 0 && half_zero;
-#define FTOEP_PASS_CASE(RR)                                                          \
-  if (hz) run_pass<V, RR, DIF, true, TM>(logn, cnt, logg, tw, ld, st);               \
-  else run_pass<V, RR, DIF, false, TM>(logn, cnt, logg, tw, ld, st);
+#define FTOEP_PASS_CASE(RR)                                                                     \
+  {                                                                                             \
+    constexpr int LH = (1 << RR) / 2, LF = 1 << RR;                                             \
+    constexpr int UBH = (GL || RMW) ? (LH >= 8 ? 1 : 8 / LH) : 1;                               \
+    constexpr int UBF = (GL || RMW) ? (LF >= 8 ? 1 : 8 / LF) : 1;                               \
+    if (hz) run_pass<V, RR, DIF, true, TM, UBH, RMW>(logn, cnt, logg, tw, ld, st);              \
+    else run_pass<V, RR, DIF, false, TM, UBF, RMW>(logn, cnt, logg, tw, ld, st);                \
+  }
   switch (r) {
     case 1: { FTOEP_PASS_CASE(1) break; }
     case 2: { FTOEP_PASS_CASE(2) break; }

@@ -22,9 +22,13 @@ void difference_weights(int kind, double gamma, double tau, int64_t n, double* e
 enum Prec { P64 = 0, P32 = 1, PFF = 2 };
 
 struct DstArgs {
-  // forward: f (+ wu0*u0 + wphi*phi) [M][N] doubles  ->  z pairs [P][ld]
-  // inverse: z pairs -> u [M][N] doubles (write or accumulate)
+  // forward: f (+ wu0*u0 + wphi*phi) [M][N] doubles (or f32)  ->  z pairs [P][ld]
+  // inverse: z pairs -> u [M][N] doubles (write or accumulate) or u32 floats
+  // Pair p holds modes p+1 (.x) and M-p (.y) (space 1) or rows 2p, 2p+1 (space 0).
   const double* f;      // forward input
+  const float* f32;     // forward input in float instead of f (no initial-data terms)
+  float* u32;           // inverse output in float instead of u (write only)
+  double dst_scale;     // 1/sqrt(2K)
   const double* u0;     // nullable
   const double* phi;    // nullable
   const double* wu0;    // length N (with u0)
@@ -60,6 +64,7 @@ int launch_dst_inverse(Prec prec, const DstArgs& a, cudaStream_t st);
 // reversal within [0,N)); unpack back.
 struct PackArgs {
   const double* x;  // lines (pack input)
+  const float* x32; // lines in float instead of x
   double* y;        // lines (unpack output)
   void* z;          // pairs
   int64_t ld, N, nlines;
@@ -74,8 +79,11 @@ int launch_unpack(Prec prec, const PackArgs& a, cudaStream_t st);
 //                or u0[j] (u0 != NULL) or 0;
 //   reverse = 1: out[j][n] = tau * sum_{k>=n} in[j][k].
 // in may equal out.
+// in32 (float input, forward only): the sums are float-float; tau = tau_h + tau_l.
 struct ScanArgs {
   const double* in;
+  const float* in32;
+  float tau_h, tau_l;
   double* out;
   const double* u0;
   int64_t N, M;
@@ -85,9 +93,9 @@ struct ScanArgs {
 };
 int launch_scan(const ScanArgs& a, cudaStream_t st);
 
-// Residual r = f + wu0*u0 + wphi*phi - (T x) - S(u), with (T x) given in pairs (double2
-// or float-float, tu_ff) and S the spatial operator: Dirichlet -u_xx (space 1) or
-// lambda*u (space 0).  r may alias the input of the product (it is read per element).
+// Residual r = f + wu0*u0 + wphi*phi - (T x) - S(u) in float, with (T x) given in
+// float-float pairs (line 2p in .x, 2p+1 in .y) and S the spatial operator: Dirichlet
+// -u_xx (space 1) or lambda*u (space 0).
 struct ResidualArgs {
   const double* f;
   const double* u0;
@@ -95,9 +103,8 @@ struct ResidualArgs {
   const double* wu0;
   const double* wphi;
   const double* u;
-  const void* tu;     // pairs [P][ld]
-  int tu_ff;
-  double* r;
+  const void* tu;     // ff2 pairs [ceil(M/2)][ld]
+  float* r32;
   int64_t ld, N, M;
   int space;
   double inv_h2, lambda;

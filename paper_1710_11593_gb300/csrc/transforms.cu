@@ -7,6 +7,7 @@
 // two components independently, so one complex FFT serves two real problems.
 #include <cstdio>
 
+#include "convert.cuh"
 #include "fft.cuh"
 #include "fftr.cuh"
 #include "internal.h"
@@ -35,12 +36,40 @@ template <typename T> __device__ __forceinline__ typename VecOf<T>::type make_pa
 template <> __device__ __forceinline__ double2 make_pair_of<double>(double a, double b) { return make_double2(a, b); }
 template <> __device__ __forceinline__ float2 make_pair_of<float>(double a, double b) { return make_float2((float)a, (float)b); }
 template <> __device__ __forceinline__ ff2 make_pair_of<FF>(double a, double b) { return ff2_from(a, b); }
+template <typename T> __device__ __forceinline__ typename VecOf<T>::type pair_of_floats(float a, float b);
+template <> __device__ __forceinline__ double2 pair_of_floats<double>(float a, float b) {
+  return make_double2(f2d_fast(a), f2d_fast(b));
+}
+template <> __device__ __forceinline__ float2 pair_of_floats<float>(float a, float b) { return make_float2(a, b); }
+template <> __device__ __forceinline__ ff2 pair_of_floats<FF>(float a, float b) {
+  ff2 r;
+  r.xh = a;
+  r.xl = 0.0f;
+  r.yh = b;
+  r.yl = 0.0f;
+  return r;
+}
 __device__ __forceinline__ double re_of(double2 v) { return v.x; }
 __device__ __forceinline__ double im_of(double2 v) { return v.y; }
 __device__ __forceinline__ double re_of(float2 v) { return (double)v.x; }
 __device__ __forceinline__ double im_of(float2 v) { return (double)v.y; }
 __device__ __forceinline__ double re_of(ff2 v) { return (double)v.xh + (double)v.xl; }
 __device__ __forceinline__ double im_of(ff2 v) { return (double)v.yh + (double)v.yl; }
+
+// Pointwise product of spectrum values with a kernel spectrum in the same storage order
+// (the op of fftr_middle): x[j] *= spec[pos0 + j].
+template <typename V>
+struct SpecMul {
+  const V* __restrict__ spec;
+  template <class X, class RR>
+  __device__ __forceinline__ void operator()(int t, int pos0, X& x, RR) const {
+    (void)t;
+    static_for<0, RR::value>([&](auto JJ) {
+      constexpr int j = decltype(JJ)::value;
+      x[j] = cmul(x[j], spec[pos0 + j]);
+    });
+  }
+};
 
 // ------------------------------------------------------------------ sine transform
 //
@@ -49,6 +78,13 @@ __device__ __forceinline__ double im_of(ff2 v) { return (double)v.yh + (double)v
 // columns a (in .x) and b (in .y) share one complex FFT: FFT(a + i b)_m has real part
 // 2 S_b[m] and imaginary part -2 S_a[m]; the orthonormal coefficient is
 // sqrt(2/K) S[m] = (FFT value)/sqrt(2K).  The transform is its own inverse.
+//
+// Mode pairing: pair p holds modes a = p+1 (in .x) and b = M-p = K-a (in .y); for odd M
+// the middle pair holds mode (M+1)/2 alone.  The reason is the storage order of the
+// forward FFT (bit-reversed): frequency a < K sits at an even position 2q and frequency
+// K + a at 2q + 1, and the odd symmetry gives Y_{K-a} = -Y_{K+a}.  So both modes of a pair
+// sit next to each other, and the transforms read their outputs in natural storage order
+// (free of shared-memory bank conflicts) instead of at scattered bit-reversed positions.
 
 // Right-hand side at (j, n): f plus the initial-data terms.  Original form: wu0[n]*u0[j];
 // difference form: -(S u0)_j with S the spatial operator (Dirichlet -u_xx or lambda).
@@ -69,330 +105,342 @@ __device__ __forceinline__ double rhs_value(const DstArgs& A, int64_t j, int64_t
   return v;
 }
 
+template <typename T> __device__ __forceinline__ T to_prec(double v);
+template <> __device__ __forceinline__ double to_prec<double>(double v) { return v; }
+template <> __device__ __forceinline__ float to_prec<float>(double v) { return d2f_fast(v); }
+template <typename T> __device__ __forceinline__ T from_float(float v);
+template <> __device__ __forceinline__ double from_float<double>(float v) { return f2d_fast(v); }
+template <> __device__ __forceinline__ float from_float<float>(float v) { return v; }
+
+// Forward input at (row j, column n); 0 beyond the last time column.
+template <typename T>
+__device__ __forceinline__ T dst_in(const DstArgs& A, int64_t j, int64_t n) {
+  if (n >= A.N) return (T)0;
+  if (A.f32) return from_float<T>(A.f32[j * A.N + n]);
+  return to_prec<T>(rhs_value(A, j, n));
+}
+// Inverse output at (row j, column n).
+template <typename T>
+__device__ __forceinline__ void dst_out(const DstArgs& A, int64_t j, int64_t n, T v) {
+  if (n >= A.N) return;
+  if (A.u32) {
+    A.u32[j * A.N + n] = (float)v;
+    return;
+  }
+  double* d = A.u + j * A.N + n;
+  const double dv = (double)v;
+  *d = A.accumulate ? *d + dv : dv;
+}
+__device__ __forceinline__ int64_t col_of(const DstArgs& A, int64_t n) {
+  return (A.reverse && n < A.N) ? A.N - 1 - n : n;
+}
+template <typename V> __device__ __forceinline__ V vneg(V v) {
+  V r;
+  r.x = -v.x;
+  r.y = -v.y;
+  return r;
+}
+
 constexpr int kDstThreads = 512;
 
+// No spatial transform (space 0): pairs of rows.
 template <typename T>
-__global__ void __launch_bounds__(kDstThreads) dst_forward_kernel(DstArgs A, int C) {
+__device__ void rows_forward(const DstArgs& A, int C) {
   typedef Vt<T> V;
   V* z = (V*)A.z;
   const int64_t col0 = (int64_t)blockIdx.x * C;
-  const int64_t M = A.M, N = A.N;
-  const int64_t P = (M + 1) / 2;
-  if (A.space == 0) {
-    // no spatial transform: pairs of rows
-    for (int64_t e = threadIdx.x; e < P * C; e += blockDim.x) {
-      const int64_t p = e / C;
-      const int c = (int)(e % C);
-      const int64_t n = col0 + c;
-      if (n >= A.ncols) continue;
-      double v[2] = {0.0, 0.0};
-      if (n < N) {
-        for (int q = 0; q < 2; ++q) {
-          const int64_t j = 2 * p + q;
-          if (j >= M) continue;
-          v[q] = rhs_value(A, j, n);
-        }
-      }
-      const int64_t nout = (A.reverse && n < N) ? N - 1 - n : n;
-      z[p * A.ld + nout] = mkv((T)v[0], (T)v[1]);
-    }
-    return;
-  }
-  extern __shared__ __align__(16) unsigned char smraw[];
-  V* sm = reinterpret_cast<V*>(smraw);
-  const int logK2 = A.logK2;
-  const int K2 = 1 << logK2, K = K2 >> 1;
-  const int lds = K2 + 1;
-  const int CP = C >> 1;
-  for (int cp = threadIdx.x; cp < CP; cp += blockDim.x) {
-    sm[cp * lds] = vzero<V>();
-    sm[cp * lds + K] = vzero<V>();
-  }
-  // four independent loads in flight per thread before the shared-memory stores
-  const int64_t tot = M * C;
-  for (int64_t e0 = threadIdx.x; e0 < tot; e0 += 4 * (int64_t)blockDim.x) {
-    double v[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t e = e0 + q * (int64_t)blockDim.x;
-      const int64_t n = col0 + (e % C);
-      v[q] = (e < tot && n < N) ? rhs_value(A, e / C, n) : 0.0;
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t e = e0 + q * (int64_t)blockDim.x;
-      if (e >= tot) break;
-      const int c = (int)(e % C);
-      const T tv = (T)v[q];
-      V* col = sm + (c >> 1) * lds;
-      const int pos = (int)(e / C) + 1;
-      if (c & 1) {
-        col[pos].y = tv;
-        col[K2 - pos].y = -tv;
-      } else {
-        col[pos].x = tv;
-        col[K2 - pos].x = -tv;
-      }
-    }
-  }
-  __syncthreads();
-  fft_dif<V>(sm, logK2, CP, lds, (const V*)A.tw, false);
-  const T scale = (T)(1.0 / sqrt(2.0 * (double)K));
+  const int64_t P = (A.M + 1) / 2;
   for (int64_t e = threadIdx.x; e < P * C; e += blockDim.x) {
     const int64_t p = e / C;
     const int c = (int)(e % C);
     const int64_t n = col0 + c;
     if (n >= A.ncols) continue;
-    const V* col = sm + (c >> 1) * lds;
-    const int m1 = (int)(2 * p + 1), m2 = m1 + 1;
-    const V y1 = col[brev(m1, logK2)];
-    const T v1 = (c & 1) ? y1.x : -y1.y;
-    T v2 = (T)0;
-    if (m2 <= M) {
-      const V y2 = col[brev(m2, logK2)];
-      v2 = (c & 1) ? y2.x : -y2.y;
+    const T v0 = dst_in<T>(A, 2 * p, n);
+    const T v1 = 2 * p + 1 < A.M ? dst_in<T>(A, 2 * p + 1, n) : (T)0;
+    z[p * A.ld + col_of(A, n)] = mkv(v0, v1);
+  }
+}
+template <typename T>
+__device__ void rows_inverse(const DstArgs& A, int C) {
+  typedef Vt<T> V;
+  const V* z = (const V*)A.z;
+  const int64_t col0 = (int64_t)blockIdx.x * C;
+  const int64_t P = (A.M + 1) / 2;
+  for (int64_t e = threadIdx.x; e < P * C; e += blockDim.x) {
+    const int64_t p = e / C;
+    const int c = (int)(e % C);
+    const int64_t n = col0 + c;
+    if (n >= A.N) continue;
+    const V zz = z[p * A.ld + col_of(A, n)];
+    dst_out<T>(A, 2 * p, n, zz.x);
+    if (2 * p + 1 < A.M) dst_out<T>(A, 2 * p + 1, n, zz.y);
+  }
+}
+
+// One block: C time columns (C/2 complex transforms of length 2K, K = M+1 a power of two).
+template <typename T>
+__global__ void __launch_bounds__(kDstThreads) dst_forward_kernel(DstArgs A, int C) {
+  typedef Vt<T> V;
+  if (A.space == 0) {
+    rows_forward<T>(A, C);
+    return;
+  }
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  V* z = (V*)A.z;
+  const int64_t col0 = (int64_t)blockIdx.x * C;
+  const int64_t M = A.M;
+  const int logK2 = A.logK2;
+  const int K2 = 1 << logK2, K = K2 >> 1;
+  const int CP = C >> 1;
+  const SmLayout L = sm_layout<V>(logK2);
+  for (int t = threadIdx.x; t < CP; t += blockDim.x) {
+    sm[sm_pos<V>(L, t, 0)] = vzero<V>();
+    sm[sm_pos<V>(L, t, K)] = vzero<V>();
+  }
+  // odd extension: row j of columns (2t, 2t+1) -> positions j+1 and 2K-j-1; four rows of
+  // loads in flight per thread
+  const int64_t tot = M * CP;
+  for (int64_t e0 = threadIdx.x; e0 < tot; e0 += 4 * (int64_t)blockDim.x) {
+    T va[4], vb[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t e = e0 + q * (int64_t)blockDim.x;
+      if (e < tot) {
+        const int64_t j = e / CP, n = col0 + 2 * (e % CP);
+        va[q] = dst_in<T>(A, j, n);
+        vb[q] = dst_in<T>(A, j, n + 1);
+      }
     }
-    const int64_t nout = (A.reverse && n < N) ? N - 1 - n : n;
-    z[p * A.ld + nout] = mkv(v1 * scale, v2 * scale);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t e = e0 + q * (int64_t)blockDim.x;
+      if (e < tot) {
+        const int j = (int)(e / CP), t = (int)(e % CP);
+        const V v = mkv(va[q], vb[q]);
+        sm[sm_pos<V>(L, t, j + 1)] = v;
+        sm[sm_pos<V>(L, t, K2 - j - 1)] = vneg(v);
+      }
+    }
+  }
+  __syncthreads();
+  fftr_dif<V>(sm, logK2, CP, (const V*)A.tw, false);
+  // positions 4q, 4q+1 (q >= 1) hold frequencies a = brev(4q) < K/2 and K + a; position
+  // 2, 3 the middle mode K/2 (q = 0)
+  const T scale = (T)A.dst_scale;
+  const int Q = K >> 1;
+  for (int e = threadIdx.x; e < Q * CP; e += blockDim.x) {
+    const int qq = e / CP, t = e % CP;
+    const int pos = qq == 0 ? 2 : 4 * qq;
+    const int a = brev(pos, logK2);
+    const int64_t p = a - 1;
+    const V ya = sm[sm_pos<V>(L, t, pos)];
+    const V ym = sm[sm_pos<V>(L, t, pos + 1)];
+    const bool self = 2 * a == K;
+    V c0, c1;
+    c0.x = -ya.y * scale;
+    c1.x = ya.x * scale;
+    c0.y = self ? (T)0 : ym.y * scale;
+    c1.y = self ? (T)0 : -ym.x * scale;
+    const int64_t n = col0 + 2 * t;
+    if (n < A.ncols) z[p * A.ld + col_of(A, n)] = c0;
+    if (n + 1 < A.ncols) z[p * A.ld + col_of(A, n + 1)] = c1;
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kDstThreads) dst_inverse_kernel(DstArgs A, int C) {
   typedef Vt<T> V;
-  const V* z = (const V*)A.z;
-  const int64_t col0 = (int64_t)blockIdx.x * C;
-  const int64_t M = A.M, N = A.N;
-  const int64_t P = (M + 1) / 2;
   if (A.space == 0) {
-    for (int64_t e = threadIdx.x; e < P * C; e += blockDim.x) {
-      const int64_t p = e / C;
-      const int c = (int)(e % C);
-      const int64_t n = col0 + c;
-      if (n >= N) continue;
-      const int64_t nin = A.reverse ? N - 1 - n : n;
-      const V zz = z[p * A.ld + nin];
-      for (int q = 0; q < 2; ++q) {
-        const int64_t j = 2 * p + q;
-        if (j >= M) continue;
-        const double v = (double)(q ? zz.y : zz.x);
-        double* dst = A.u + j * N + n;
-        *dst = A.accumulate ? *dst + v : v;
-      }
-    }
+    rows_inverse<T>(A, C);
     return;
   }
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
+  const V* z = (const V*)A.z;
+  const int64_t col0 = (int64_t)blockIdx.x * C;
   const int logK2 = A.logK2;
   const int K2 = 1 << logK2, K = K2 >> 1;
-  const int lds = K2 + 1;
   const int CP = C >> 1;
-  for (int cp = threadIdx.x; cp < CP; cp += blockDim.x) {
-    sm[cp * lds] = vzero<V>();
-    sm[cp * lds + K] = vzero<V>();
+  const int64_t P = K >> 1;
+  const SmLayout L = sm_layout<V>(logK2);
+  for (int t = threadIdx.x; t < CP; t += blockDim.x) {
+    sm[sm_pos<V>(L, t, 0)] = vzero<V>();
+    sm[sm_pos<V>(L, t, K)] = vzero<V>();
   }
-  const int64_t tot = P * C;
+  // pair p of columns (2t, 2t+1): modes a = p+1 and b = K-a -> positions a, 2K-a, b, 2K-b
+  const int64_t tot = P * CP;
   for (int64_t e0 = threadIdx.x; e0 < tot; e0 += 4 * (int64_t)blockDim.x) {
-    V zq[4];
+    V c0[4], c1[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int64_t e = e0 + q * (int64_t)blockDim.x;
       if (e < tot) {
-        const int64_t n = col0 + (e % C);
-        const int64_t nin = (A.reverse && n < N) ? N - 1 - n : n;
-        zq[q] = z[(e / C) * A.ld + nin];
+        const int64_t p = e / CP, n = col0 + 2 * (e % CP);
+        c0[q] = n < A.N ? z[p * A.ld + col_of(A, n)] : vzero<V>();
+        c1[q] = n + 1 < A.N ? z[p * A.ld + col_of(A, n + 1)] : vzero<V>();
       }
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int64_t e = e0 + q * (int64_t)blockDim.x;
-      if (e >= tot) break;
-      const int64_t p = e / C;
-      const int c = (int)(e % C);
-      const V zz = zq[q];
-      V* col = sm + (c >> 1) * lds;
-      const int m1 = (int)(2 * p + 1), m2 = m1 + 1;
-      if (c & 1) {
-        col[m1].y = zz.x;
-        col[K2 - m1].y = -zz.x;
-        if (m2 <= M) {
-          col[m2].y = zz.y;
-          col[K2 - m2].y = -zz.y;
-        }
-      } else {
-        col[m1].x = zz.x;
-        col[K2 - m1].x = -zz.x;
-        if (m2 <= M) {
-          col[m2].x = zz.y;
-          col[K2 - m2].x = -zz.y;
+      if (e < tot) {
+        const int a = (int)(e / CP) + 1, t = (int)(e % CP);
+        const int b = K - a;
+        const V va = mkv(c0[q].x, c1[q].x);
+        sm[sm_pos<V>(L, t, a)] = va;
+        sm[sm_pos<V>(L, t, K2 - a)] = vneg(va);
+        if (b != a) {
+          const V vb = mkv(c0[q].y, c1[q].y);
+          sm[sm_pos<V>(L, t, b)] = vb;
+          sm[sm_pos<V>(L, t, K2 - b)] = vneg(vb);
         }
       }
     }
   }
   __syncthreads();
-  fft_dif<V>(sm, logK2, CP, lds, (const V*)A.tw, false);
-  const double scale = 1.0 / sqrt(2.0 * (double)K);
-  for (int64_t e = threadIdx.x; e < M * C; e += blockDim.x) {
-    const int64_t j = e / C;
-    const int c = (int)(e % C);
-    const int64_t n = col0 + c;
-    if (n >= N) continue;
-    const V y = sm[(c >> 1) * lds + brev((int)j + 1, logK2)];
-    const double v = (double)((c & 1) ? y.x : -y.y) * scale;
-    double* dst = A.u + j * N + n;
-    *dst = A.accumulate ? *dst + v : v;
+  fftr_dif<V>(sm, logK2, CP, (const V*)A.tw, false);
+  // rows j = brev(4q) (and K/2 at q = 0) from position 4q, rows K - j from 4q + 1
+  const T scale = (T)A.dst_scale;
+  const int Q = K >> 1;
+  for (int e = threadIdx.x; e < Q * CP; e += blockDim.x) {
+    const int qq = e / CP, t = e % CP;
+    const int pos = qq == 0 ? 2 : 4 * qq;
+    const int j = brev(pos, logK2);
+    const V yj = sm[sm_pos<V>(L, t, pos)];
+    const int64_t n = col0 + 2 * t;
+    dst_out<T>(A, j - 1, n, -yj.y * scale);
+    dst_out<T>(A, j - 1, n + 1, yj.x * scale);
+    if (2 * j != K) {
+      const V ym = sm[sm_pos<V>(L, t, pos + 1)];
+      dst_out<T>(A, K - j - 1, n, ym.y * scale);
+      dst_out<T>(A, K - j - 1, n + 1, -ym.x * scale);
+    }
   }
 }
 
 // Sine transform for any K = M+1 (Bluestein / chirp-z).  With W = exp(-2 pi i / L),
 // L = 2K, and c_n = W^{n^2/2}: DFT(y)_k = c_k sum_n (y_n c_n) conj(c_{k-n}), a linear
 // convolution that a cyclic one of length P >= 2L-1 reproduces exactly.  One block
-// handles C time columns (C/2 complex column pairs, one P-buffer each).
+// handles C time columns (C/2 complex column pairs, one P-buffer each); the product with
+// the chirp's spectrum runs fused between the forward and inverse FFT, and the DFT comes
+// out in natural order.
 template <typename T>
 __global__ void __launch_bounds__(kDstThreads) dst_bluestein_kernel(DstArgs A, int C, int fwd) {
   typedef Vt<T> V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const int64_t col0 = (int64_t)blockIdx.x * C;
-  const int64_t M = A.M, N = A.N;
-  const int64_t P2 = (M + 1) / 2;
-  const int K = A.K, L = 2 * K;
-  const int P = 1 << A.logP, H = P >> 1;
-  const int lds = P + 1;
+  const int64_t M = A.M;
+  const int K = A.K, Lq = 2 * K;
+  const int logP = A.logP, P = 1 << logP, H = P >> 1;
   const int CP = C >> 1;
-  const V* chirp = (const V*)A.chirp;
-  for (int e = threadIdx.x; e < CP * H; e += blockDim.x) sm[(e / H) * lds + (e % H)] = vzero<V>();
+  const SmLayout Ls = sm_layout<V>(logP);
+  const V* __restrict__ chirp = (const V*)A.chirp;
+  const V* __restrict__ tw = (const V*)A.tw;
+  // zero [0, P/2) of every buffer; the upper half is never read (half-zero input) unless
+  // the whole transform is a single pass
+  const int np = fftr_npasses<V>(logP);
+  const int Z = np < 2 ? P : H;
+  for (int e = threadIdx.x; e < CP * Z; e += blockDim.x) sm[sm_pos<V>(Ls, e / Z, e % Z)] = vzero<V>();
   __syncthreads();
   if (fwd) {
-    const int64_t tot = M * C;
+    const int64_t tot = M * CP;
     for (int64_t e0 = threadIdx.x; e0 < tot; e0 += 4 * (int64_t)blockDim.x) {
-      double vq[4];
+      T va[4], vb[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int64_t e = e0 + q * (int64_t)blockDim.x;
-        const int64_t n = col0 + (e % C);
-        vq[q] = (e < tot && n < N) ? rhs_value(A, e / C, n) : 0.0;
+        if (e < tot) {
+          const int64_t j = e / CP, n = col0 + 2 * (e % CP);
+          va[q] = dst_in<T>(A, j, n);
+          vb[q] = dst_in<T>(A, j, n + 1);
+        }
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int64_t e = e0 + q * (int64_t)blockDim.x;
-        if (e >= tot) break;
-        const int c = (int)(e % C);
-        const T tv = (T)vq[q];
-        V* col = sm + (c >> 1) * lds;
-        const int pos = (int)(e / C) + 1;
-        if (c & 1) {
-          col[pos].y = tv;
-          col[L - pos].y = -tv;
-        } else {
-          col[pos].x = tv;
-          col[L - pos].x = -tv;
+        if (e < tot) {
+          const int j = (int)(e / CP), t = (int)(e % CP);
+          const V v = mkv(va[q], vb[q]);
+          sm[sm_pos<V>(Ls, t, j + 1)] = cmul(v, chirp[j + 1]);
+          sm[sm_pos<V>(Ls, t, Lq - j - 1)] = cmul(vneg(v), chirp[Lq - j - 1]);
         }
       }
     }
   } else {
     const V* z = (const V*)A.z;
-    const int64_t tot = P2 * C;
+    const int64_t tot = (int64_t)((M + 1) / 2) * CP;
     for (int64_t e0 = threadIdx.x; e0 < tot; e0 += 4 * (int64_t)blockDim.x) {
-     V zq[4];
+      V c0[4], c1[4];
 #pragma unroll
-     for (int q = 0; q < 4; ++q) {
-      const int64_t e = e0 + q * (int64_t)blockDim.x;
-      if (e < tot) {
-        const int64_t n = col0 + (e % C);
-        const int64_t nin = (A.reverse && n < N) ? N - 1 - n : n;
-        zq[q] = z[(e / C) * A.ld + nin];
-      }
-     }
-#pragma unroll
-     for (int q = 0; q < 4; ++q) {
-      const int64_t e = e0 + q * (int64_t)blockDim.x;
-      if (e >= tot) break;
-      const int64_t p = e / C;
-      const int c = (int)(e % C);
-      const V zz = zq[q];
-      V* col = sm + (c >> 1) * lds;
-      const int m1 = (int)(2 * p + 1), m2 = m1 + 1;
-      if (c & 1) {
-        col[m1].y = zz.x;
-        col[L - m1].y = -zz.x;
-        if (m2 <= M) {
-          col[m2].y = zz.y;
-          col[L - m2].y = -zz.y;
-        }
-      } else {
-        col[m1].x = zz.x;
-        col[L - m1].x = -zz.x;
-        if (m2 <= M) {
-          col[m2].x = zz.y;
-          col[L - m2].x = -zz.y;
+      for (int q = 0; q < 4; ++q) {
+        const int64_t e = e0 + q * (int64_t)blockDim.x;
+        if (e < tot) {
+          const int64_t p = e / CP, n = col0 + 2 * (e % CP);
+          c0[q] = n < A.N ? z[p * A.ld + col_of(A, n)] : vzero<V>();
+          c1[q] = n + 1 < A.N ? z[p * A.ld + col_of(A, n + 1)] : vzero<V>();
         }
       }
-     }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t e = e0 + q * (int64_t)blockDim.x;
+        if (e < tot) {
+          const int a = (int)(e / CP) + 1, t = (int)(e % CP);
+          const int b = K - a;
+          const V va = mkv(c0[q].x, c1[q].x);
+          sm[sm_pos<V>(Ls, t, a)] = cmul(va, chirp[a]);
+          sm[sm_pos<V>(Ls, t, Lq - a)] = cmul(vneg(va), chirp[Lq - a]);
+          if (b != a) {
+            const V vb = mkv(c0[q].y, c1[q].y);
+            sm[sm_pos<V>(Ls, t, b)] = cmul(vb, chirp[b]);
+            sm[sm_pos<V>(Ls, t, Lq - b)] = cmul(vneg(vb), chirp[Lq - b]);
+          }
+        }
+      }
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < CP * L; e += blockDim.x) {
-    V* q = sm + (e / L) * lds + (e % L);
-    *q = cmul(*q, chirp[e % L]);
-  }
+  fftr_passes<V, true>(sm, logP, CP, tw, 0, np - 1, true);
+  fftr_middle<V>(sm, logP, CP, SpecMul<V>{(const V*)A.bspec});
   __syncthreads();
-  const V* tw = (const V*)A.tw;
-  fft_dif<V>(sm, A.logP, CP, lds, tw, true);
-  const V* bs = (const V*)A.bspec;
-  for (int e = threadIdx.x; e < CP * P; e += blockDim.x) {
-    V* q = sm + (e / P) * lds + (e % P);
-    *q = cmul(*q, bs[e % P]);
-  }
-  __syncthreads();
-  fft_dit<V>(sm, A.logP, CP, lds, tw, 2);
-  const double scale = 1.0 / sqrt(2.0 * (double)K);
+  fftr_passes<V, false>(sm, logP, CP, tw, 1, np, false);
+  const T scale = (T)A.dst_scale;
   if (fwd) {
     V* z = (V*)A.z;
-    for (int64_t e = threadIdx.x; e < P2 * C; e += blockDim.x) {
-      const int64_t p = e / C;
-      const int c = (int)(e % C);
-      const int64_t n = col0 + c;
-      if (n >= A.ncols) continue;
-      const V* col = sm + (c >> 1) * lds;
-      const int m1 = (int)(2 * p + 1), m2 = m1 + 1;
-      const V y1 = cmul(col[m1], chirp[m1]);
-      const T v1 = (c & 1) ? y1.x : -y1.y;
-      T v2 = (T)0;
-      if (m2 <= M) {
-        const V y2 = cmul(col[m2], chirp[m2]);
-        v2 = (c & 1) ? y2.x : -y2.y;
-      }
-      const int64_t nout = (A.reverse && n < N) ? N - 1 - n : n;
-      z[p * A.ld + nout] = mkv((T)(v1 * (T)scale), (T)(v2 * (T)scale));
+    const int64_t P2 = (M + 1) / 2;
+    for (int64_t e = threadIdx.x; e < P2 * CP; e += blockDim.x) {
+      const int a = (int)(e / CP) + 1, t = (int)(e % CP);
+      const int b = K - a;
+      const int64_t p = a - 1;
+      const V ya = cmul(sm[sm_pos<V>(Ls, t, a)], chirp[a]);
+      const V yb = cmul(sm[sm_pos<V>(Ls, t, b)], chirp[b]);
+      const bool self = a == b;
+      V c0, c1;
+      c0.x = -ya.y * scale;
+      c1.x = ya.x * scale;
+      c0.y = self ? (T)0 : -yb.y * scale;
+      c1.y = self ? (T)0 : yb.x * scale;
+      const int64_t n = col0 + 2 * t;
+      if (n < A.ncols) z[p * A.ld + col_of(A, n)] = c0;
+      if (n + 1 < A.ncols) z[p * A.ld + col_of(A, n + 1)] = c1;
     }
   } else {
-    for (int64_t e = threadIdx.x; e < M * C; e += blockDim.x) {
-      const int64_t j = e / C;
-      const int c = (int)(e % C);
-      const int64_t n = col0 + c;
-      if (n >= N) continue;
-      const V y = cmul(sm[(c >> 1) * lds + (int)j + 1], chirp[j + 1]);
-      const double v = (double)((c & 1) ? y.x : -y.y) * scale;
-      double* dst = A.u + j * N + n;
-      *dst = A.accumulate ? *dst + v : v;
+    for (int64_t e = threadIdx.x; e < M * CP; e += blockDim.x) {
+      const int j = (int)(e / CP) + 1, t = (int)(e % CP);
+      const V y = cmul(sm[sm_pos<V>(Ls, t, j)], chirp[j]);
+      const int64_t n = col0 + 2 * t;
+      dst_out<T>(A, j - 1, n, -y.y * scale);
+      dst_out<T>(A, j - 1, n + 1, y.x * scale);
     }
   }
 }
 
+// Column pairs per block: as many as fit (power of two, <= 4 pairs) in ~160 KB of shared
+// memory.
 template <typename T>
-int bluestein_cols(int logP) {
-  const size_t per_pair = ((size_t)(1 << logP) + 1) * sizeof(Vt<T>);
-  int C = 4;
-  while (C > 2 && (size_t)(C / 2) * per_pair > 160 * 1024) C >>= 1;
-  return C;
-}
-
-template <typename T>
-int dst_cols(int logK2) {
-  // columns per block: as many as fit (even, <= 8) in ~160 KB of shared memory
-  const size_t per_pair = ((size_t)(1 << logK2) + 1) * sizeof(Vt<T>);
+int dst_cols(int logn) {
+  const size_t per_pair = ((size_t)1 << logn) * sizeof(Vt<T>);
   int C = 8;
   while (C > 2 && (size_t)(C / 2) * per_pair > 160 * 1024) C >>= 1;
   return C;
@@ -401,14 +449,14 @@ int dst_cols(int logK2) {
 template <typename T>
 void dst_launch(const DstArgs& a, bool fwd, cudaStream_t st) {
   if (a.space && a.bluestein) {
-    const int C = bluestein_cols<T>(a.logP);
-    const size_t smem = (size_t)(C / 2) * ((size_t)(1 << a.logP) + 1) * sizeof(Vt<T>);
+    const int C = dst_cols<T>(a.logP);
+    const size_t smem = (size_t)(C / 2) * ((size_t)1 << a.logP) * sizeof(Vt<T>);
     set_smem((const void*)dst_bluestein_kernel<T>, smem);
     dst_bluestein_kernel<T><<<(unsigned)((a.ncols + C - 1) / C), kDstThreads, smem, st>>>(a, C, fwd ? 1 : 0);
     return;
   }
-  int C = a.space ? dst_cols<T>(a.logK2) : 8;
-  size_t smem = a.space ? (size_t)(C / 2) * ((size_t)(1 << a.logK2) + 1) * sizeof(Vt<T>) : 0;
+  const int C = a.space ? dst_cols<T>(a.logK2) : 8;
+  const size_t smem = a.space ? (size_t)(C / 2) * ((size_t)1 << a.logK2) * sizeof(Vt<T>) : 0;
   dim3 grid((unsigned)((a.ncols + C - 1) / C));
   if (fwd) {
     set_smem((const void*)dst_forward_kernel<T>, smem);
@@ -427,6 +475,16 @@ __global__ void pack_kernel(PackArgs A) {
   const int64_t p = blockIdx.y;
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= A.ld) return;
+  if (A.x32) {  // float lines (float-float pairs with zero low parts; no conversion)
+    float v0 = 0.0f, v1 = 0.0f;
+    if (k < A.N) {
+      const int64_t src = A.reverse ? A.N - 1 - k : k;
+      v0 = A.x32[(2 * p) * A.N + src];
+      if (2 * p + 1 < A.nlines) v1 = A.x32[(2 * p + 1) * A.N + src];
+    }
+    ((V*)A.z)[p * A.ld + k] = pair_of_floats<T>(v0, v1);
+    return;
+  }
   double v0 = 0.0, v1 = 0.0;
   if (k < A.N) {
     const int64_t src = A.reverse ? A.N - 1 - k : k;
@@ -512,34 +570,147 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(ScanArgs A) {
   }
 }
 
+// Float input (mixed path): the running sums are float-float pairs (Knuth two-sum; no
+// FP64 arithmetic until the output, where base + tau*S costs two double additions).
+constexpr int kScanRun = 8;
+__device__ __forceinline__ void ffs_add(float& h, float& l, float bh, float bl) {
+  float rh, rl;
+  ff_add(h, l, bh, bl, rh, rl);
+  h = rh;
+  l = rl;
+}
+__global__ void __launch_bounds__(kThreads) scan32_kernel(ScanArgs A) {
+  __shared__ float wsh[kThreads / 32], wsl[kThreads / 32];
+  __shared__ float carry_h, carry_l;
+  const int64_t j = blockIdx.x;
+  const float* in = A.in32 + j * A.N;
+  double* out = A.out + j * A.N;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t chunk = (int64_t)kScanRun * kThreads;
+  const double base0 = A.u0 ? A.u0[j] : 0.0;
+  float ch = 0.0f, cl = 0.0f;  // carry (sum of all earlier chunks)
+  const int64_t nchunks = (A.N + chunk - 1) / chunk;
+  for (int64_t ci = 0; ci < nchunks; ++ci) {
+    const int64_t c0 = ci * chunk + (int64_t)kScanRun * threadIdx.x;
+    float vh[kScanRun], vl[kScanRun];
+    float v[kScanRun];
+#pragma unroll
+    for (int q = 0; q < kScanRun; ++q) v[q] = c0 + q < A.N ? in[c0 + q] : 0.0f;
+    float h = 0.0f, l = 0.0f;
+#pragma unroll
+    for (int q = 0; q < kScanRun; ++q) {  // inclusive run sums, error of each addition kept in l
+      const float t = h + v[q];
+      const float bb = t - h;
+      l += (h - (t - bb)) + (v[q] - bb);
+      h = t;
+      vh[q] = h;
+      vl[q] = l;
+    }
+    // exclusive scan of the run totals across the block
+    float xh = h, xl = l;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float yh = __shfl_up_sync(0xffffffffu, xh, o);
+      const float yl = __shfl_up_sync(0xffffffffu, xl, o);
+      if (lane >= o) ffs_add(xh, xl, yh, yl);
+    }
+    if (lane == 31) {
+      wsh[warp] = xh;
+      wsl[warp] = xl;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      float wh = lane < kThreads / 32 ? wsh[lane] : 0.0f, wl = lane < kThreads / 32 ? wsl[lane] : 0.0f;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float yh = __shfl_up_sync(0xffffffffu, wh, o);
+        const float yl = __shfl_up_sync(0xffffffffu, wl, o);
+        if (lane >= o) ffs_add(wh, wl, yh, yl);
+      }
+      if (lane < kThreads / 32) {
+        wsh[lane] = wh;
+        wsl[lane] = wl;
+      }
+      if (lane == kThreads / 32 - 1) {
+        carry_h = wh;
+        carry_l = wl;
+      }
+    }
+    __syncthreads();
+    // before = carry + (inclusive warp scan - own run) + earlier warps
+    float bh = ch, bl = cl;
+    ffs_add(bh, bl, xh, xl);
+    ffs_add(bh, bl, -h, -l);
+    if (warp > 0) ffs_add(bh, bl, wsh[warp - 1], wsl[warp - 1]);
+#pragma unroll
+    for (int q = 0; q < kScanRun; ++q) {
+      const int64_t pos = c0 + q;
+      if (pos >= A.N) break;
+      float sh = bh, sl = bl;
+      ffs_add(sh, sl, vh[q], vl[q]);
+      float ph, pl;
+      ff_mul(sh, sl, A.tau_h, A.tau_l, ph, pl);
+      const double base = A.accumulate ? out[pos] : base0;
+      out[pos] = (base + f2d_fast(ph)) + f2d_fast(pl);
+    }
+    ffs_add(ch, cl, carry_h, carry_l);
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ residual, dot
 
+// One thread: time column n, rows j0 .. j0+kResRows-1 (u with one halo row each side
+// stays in registers).  Double arithmetic only for t = f - S u (+ initial-data terms):
+// the spatial second difference cancels about log10(4/h^2) digits and needs u in full
+// double.  t is split into a float pair with integer operations and the float-float
+// product T x is subtracted as (t_hi - tx_hi) + (t_lo - tx_lo): the first difference is
+// exact whenever the residual is small against t, so r (stored in float, the precision of
+// the correction solve) is correct to about one float rounding plus 2^-48 |t|.
+constexpr int kResRows = 8;
 __global__ void residual_kernel(ResidualArgs A) {
-  const int64_t j = blockIdx.y;
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= A.N) return;
-  const int64_t idx = j * A.N + n;
-  double v = A.f[idx];
-  if (A.u0) v += A.wu0[n] * A.u0[j];
-  if (A.phi) v += A.wphi[n] * A.phi[j];
-  double tv;
-  if (A.tu_ff) {
-    const ff2 t = ((const ff2*)A.tu)[(j >> 1) * A.ld + n];
-    tv = (j & 1) ? im_of(t) : re_of(t);
-  } else {
-    const double2 t = ((const double2*)A.tu)[(j >> 1) * A.ld + n];
-    tv = (j & 1) ? t.y : t.x;
+  const int64_t j0 = (int64_t)blockIdx.y * kResRows;
+  const int64_t N = A.N, M = A.M;
+  double u[kResRows + 2], f[kResRows];
+#pragma unroll
+  for (int k = 0; k < kResRows + 2; ++k) {
+    const int64_t row = j0 - 1 + k;
+    u[k] = (row >= 0 && row < M) ? A.u[row * N + n] : 0.0;
   }
-  const double uj = A.u[idx];
-  double s;
-  if (A.space == 1) {
-    const double um = j > 0 ? A.u[idx - A.N] : 0.0;
-    const double up = j + 1 < A.M ? A.u[idx + A.N] : 0.0;
-    s = (2.0 * uj - um - up) * A.inv_h2;
-  } else {
-    s = A.lambda * uj;
+#pragma unroll
+  for (int k = 0; k < kResRows; ++k) {
+    const int64_t row = j0 + k;
+    f[k] = row < M ? A.f[row * N + n] : 0.0;
   }
-  A.r[idx] = v - tv - s;
+  ff2 tv[kResRows / 2];
+#pragma unroll
+  for (int k = 0; k < kResRows / 2; ++k) {
+    const int64_t pr = (j0 >> 1) + k;
+    tv[k] = (2 * pr < M) ? ((const ff2*)A.tu)[pr * A.ld + n] : vzero<ff2>();
+  }
+  const double wphi = A.phi ? A.wphi[n] : 0.0;
+  const double wu0 = A.u0 ? A.wu0[n] : 0.0;
+#pragma unroll
+  for (int k = 0; k < kResRows; ++k) {
+    const int64_t row = j0 + k;
+    if (row >= M) break;
+    double t;
+    if (A.space == 1) {
+      const double s2 = fma(2.0, u[k + 1], -u[k]) - u[k + 2];
+      t = fma(-s2, A.inv_h2, f[k]);
+    } else {
+      t = fma(-A.lambda, u[k + 1], f[k]);
+    }
+    if (A.phi) t = fma(wphi, A.phi[row], t);
+    if (A.u0) t = fma(wu0, A.u0[row], t);
+    float th, tl;
+    d2ff_fast(t, th, tl);
+    const ff2 x = tv[k >> 1];
+    const float xh = (k & 1) ? x.yh : x.xh, xl = (k & 1) ? x.yl : x.xl;
+    A.r32[row * N + n] = (th - xh) + (tl - xl);
+  }
 }
 
 __global__ void dot_kernel(DotArgs A) {
@@ -664,18 +835,26 @@ void spectrum_launch(const SpecArgs& a, cudaStream_t st) {
 
 // ------------------------------------------------------------------ convolution
 
-// Pointwise product of spectrum values with a kernel spectrum in the same storage order
-// (the op of fftr_middle): x[j] *= spec[pos0 + j].
+// Read-modify-write storers of the last inverse pass (mode 0: subtract the upper half of
+// the cyclic result from the output).
 template <typename V>
-struct SpecMul {
-  const V* __restrict__ spec;
-  template <class X, class RR>
-  __device__ __forceinline__ void operator()(int t, int pos0, X& x, RR) const {
-    (void)t;
-    static_for<0, RR::value>([&](auto JJ) {
-      constexpr int j = decltype(JJ)::value;
-      x[j] = cmul(x[j], spec[pos0 + j]);
-    });
+struct SubUpper {  // zo[e - s] -= v for e >= s
+  V* __restrict__ zo;
+  int s;
+  __device__ __forceinline__ V fetch(int, int e) const { return e >= s ? zo[e - s] : vzero<V>(); }
+  __device__ __forceinline__ void operator()(int, int e, const V& v, const V& f) const {
+    if (e >= s) zo[e - s] = csub(f, v);
+  }
+};
+template <typename V>
+struct SubUpperCols {  // column t: zo[(e - h1) n2 + t] -= v for e >= h1
+  V* __restrict__ zo;
+  int h1, n2;
+  __device__ __forceinline__ V fetch(int t, int e) const {
+    return e >= h1 ? zo[(int64_t)(e - h1) * n2 + t] : vzero<V>();
+  }
+  __device__ __forceinline__ void operator()(int t, int e, const V& v, const V& f) const {
+    if (e >= h1) zo[(int64_t)(e - h1) * n2 + t] = csub(f, v);
   }
 };
 
@@ -695,7 +874,7 @@ __global__ void __launch_bounds__(kThreads) conv_smem_kernel(ConvArgs A) {
   const V* __restrict__ tw = (const V*)A.tw;
   const SmLayout L = sm_layout<V>(logn);
   const int np = fftr_npasses<V>(logn);
-  fftr_pass<V, true>(0, logn, 1, tw, true, [&](int, int e) { return zin[e]; }, SmPut<V>{sm, L});
+  fftr_pass<V, true, false, true>(0, logn, 1, tw, true, [&](int, int e) { return zin[e]; }, SmPut<V>{sm, L});
   __syncthreads();
   if (np < 2) {  // a single pass: plain product in shared memory
     for (int k = threadIdx.x; k < 2 * s; k += blockDim.x) {
@@ -710,9 +889,7 @@ __global__ void __launch_bounds__(kThreads) conv_smem_kernel(ConvArgs A) {
     fftr_passes<V, false>(sm, logn, 1, tw, 1, np - 1, false);
   }
   if (A.mode == 0) {
-    fftr_pass<V, false>(np - 1, logn, 1, tw, false, SmAt<V>{sm, L}, [&](int, int e, const V& v) {
-      if (e >= s) zo[e - s] = csub(zo[e - s], v);
-    });
+    fftr_pass<V, false, false, false, true>(np - 1, logn, 1, tw, false, SmAt<V>{sm, L}, SubUpper<V>{zo, s});
   } else {
     fftr_pass<V, false>(np - 1, logn, 1, tw, false, SmAt<V>{sm, L}, [&](int, int e, const V& v) {
       if (e < s) zo[e] = v;
@@ -741,8 +918,8 @@ __global__ void __launch_bounds__(kThreads) conv_col_fwd_kernel(ConvArgs A, int 
   const V* __restrict__ twn = tw + (n - 2);
   const SmLayout L = sm_layout<V>(logn1);
   const int np = fftr_npasses<V>(logn1);
-  fftr_pass<V, true, true>(0, logn1, C, tw, true, [&](int t, int e) { return zin[(int64_t)e * n2 + t]; },
-                           SmPut<V>{sm, L});
+  fftr_pass<V, true, true, true>(0, logn1, C, tw, true, [&](int t, int e) { return zin[(int64_t)e * n2 + t]; },
+                                 SmPut<V>{sm, L});
   __syncthreads();
   fftr_passes<V, true, true>(sm, logn1, C, tw, 1, np - 1, false);
   fftr_pass<V, true, true>(np - 1, logn1, C, tw, false, SmAt<V>{sm, L}, [&](int t, int e, const V& v) {
@@ -764,7 +941,8 @@ __global__ void __launch_bounds__(kThreads) conv_row_kernel(ConvArgs A, int logn
   const V* __restrict__ twn = tw + (n - 2);
   const SmLayout L = sm_layout<V>(logn2);
   const int np = fftr_npasses<V>(logn2);
-  fftr_pass<V, true>(0, logn2, rows, tw, false, [&](int t, int e) { return sc[t * n2 + e]; }, SmPut<V>{sm, L});
+  fftr_pass<V, true, false, true>(0, logn2, rows, tw, false, [&](int t, int e) { return sc[t * n2 + e]; },
+                                  SmPut<V>{sm, L});
   __syncthreads();
   fftr_passes<V, true>(sm, logn2, rows, tw, 1, np - 1, false);
   const V* __restrict__ spec = (const V*)A.spec + (int64_t)r0 * n2;
@@ -792,17 +970,13 @@ __global__ void __launch_bounds__(kThreads) conv_col_inv_kernel(ConvArgs A, int 
   const V* __restrict__ tw = (const V*)A.tw;
   const SmLayout L = sm_layout<V>(logn1);
   const int np = fftr_npasses<V>(logn1);
-  fftr_pass<V, false, true>(0, logn1, C, tw, false, [&](int t, int e) { return sc[(int64_t)e * n2 + t]; },
-                            SmPut<V>{sm, L});
+  fftr_pass<V, false, true, true>(0, logn1, C, tw, false, [&](int t, int e) { return sc[(int64_t)e * n2 + t]; },
+                                  SmPut<V>{sm, L});
   __syncthreads();
   fftr_passes<V, false, true>(sm, logn1, C, tw, 1, np - 1, false);
   if (A.mode == 0) {
-    fftr_pass<V, false, true>(np - 1, logn1, C, tw, false, SmAt<V>{sm, L}, [&](int t, int e, const V& v) {
-      if (e >= h1) {
-        V* q = zo + (int64_t)(e - h1) * n2 + t;
-        *q = csub(*q, v);
-      }
-    });
+    fftr_pass<V, false, true, false, true>(np - 1, logn1, C, tw, false, SmAt<V>{sm, L},
+                                           SubUpperCols<V>{zo, h1, n2});
   } else {
     fftr_pass<V, false, true>(np - 1, logn1, C, tw, false, SmAt<V>{sm, L}, [&](int t, int e, const V& v) {
       if (e < h1) zo[(int64_t)e * n2 + t] = v;
@@ -883,12 +1057,13 @@ int launch_unpack(Prec prec, const PackArgs& a, cudaStream_t st) {
 }
 
 int launch_scan(const ScanArgs& a, cudaStream_t st) {
-  scan_kernel<<<(unsigned)a.M, kThreads, 0, st>>>(a);
+  if (a.in32) scan32_kernel<<<(unsigned)a.M, kThreads, 0, st>>>(a);
+  else scan_kernel<<<(unsigned)a.M, kThreads, 0, st>>>(a);
   return 1;
 }
 
 int launch_residual(const ResidualArgs& a, cudaStream_t st) {
-  dim3 grid((unsigned)((a.N + kThreads - 1) / kThreads), (unsigned)a.M);
+  dim3 grid((unsigned)((a.N + kThreads - 1) / kThreads), (unsigned)((a.M + kResRows - 1) / kResRows));
   residual_kernel<<<grid, kThreads, 0, st>>>(a);
   return 1;
 }
