@@ -58,27 +58,47 @@ __device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, f
   e = fmaf(al, bh, e);
   ff_fast_two_sum(p, e, rh, rl);
 }
+// (ah + al) + (bh + bl) with one two-sum on the high parts: the error is bounded by a
+// small multiple of 2^-48 (|a| + |b|) -- relative to the operands, not to the result.
+// That is the bound the normwise rounding analysis of an FFT needs (every butterfly's
+// error is charged against its inputs), and it costs 11 operations instead of 20.
+__device__ __forceinline__ void ff_add_fast(float ah, float al, float bh, float bl, float& rh, float& rl) {
+  float s, e;
+  ff_two_sum(ah, bh, s, e);
+  e += al + bl;
+  ff_fast_two_sum(s, e, rh, rl);
+}
 __device__ __forceinline__ ff2 cadd(ff2 a, ff2 b) {
   ff2 r;
-  ff_add(a.xh, a.xl, b.xh, b.xl, r.xh, r.xl);
-  ff_add(a.yh, a.yl, b.yh, b.yl, r.yh, r.yl);
+  ff_add_fast(a.xh, a.xl, b.xh, b.xl, r.xh, r.xl);
+  ff_add_fast(a.yh, a.yl, b.yh, b.yl, r.yh, r.yl);
   return r;
 }
 __device__ __forceinline__ ff2 csub(ff2 a, ff2 b) {
   ff2 r;
-  ff_add(a.xh, a.xl, -b.xh, -b.xl, r.xh, r.xl);
-  ff_add(a.yh, a.yl, -b.yh, -b.yl, r.yh, r.yl);
+  ff_add_fast(a.xh, a.xl, -b.xh, -b.xl, r.xh, r.xl);
+  ff_add_fast(a.yh, a.yl, -b.yh, -b.yl, r.yh, r.yl);
   return r;
 }
+// p q - r s in float-float: the two high products exactly (FMA residuals), their
+// difference by a two-sum, the cross terms of the low parts folded into the error word.
+__device__ __forceinline__ void ff_dot2(float ph, float pl, float qh, float ql, float rh_, float rl_, float sh,
+                                        float sl, float& oh, float& ol) {
+  const float a = ph * qh, b = rh_ * sh;
+  const float ea = fmaf(ph, qh, -a), eb = fmaf(rh_, sh, -b);
+  float d, ed;
+  ff_two_sum(a, -b, d, ed);
+  float e = ed + (ea - eb);
+  e = fmaf(ph, ql, e);
+  e = fmaf(pl, qh, e);
+  e = fmaf(-rh_, sl, e);
+  e = fmaf(-rl_, sh, e);
+  ff_fast_two_sum(d, e, oh, ol);
+}
 __device__ __forceinline__ ff2 cmul(ff2 a, ff2 b) {
-  float p1h, p1l, p2h, p2l, p3h, p3l, p4h, p4l;
-  ff_mul(a.xh, a.xl, b.xh, b.xl, p1h, p1l);
-  ff_mul(a.yh, a.yl, b.yh, b.yl, p2h, p2l);
-  ff_mul(a.xh, a.xl, b.yh, b.yl, p3h, p3l);
-  ff_mul(a.yh, a.yl, b.xh, b.xl, p4h, p4l);
   ff2 r;
-  ff_add(p1h, p1l, -p2h, -p2l, r.xh, r.xl);
-  ff_add(p3h, p3l, p4h, p4l, r.yh, r.yl);
+  ff_dot2(a.xh, a.xl, b.xh, b.xl, a.yh, a.yl, b.yh, b.yl, r.xh, r.xl);    // ax bx - ay by
+  ff_dot2(a.xh, a.xl, b.yh, b.yl, -a.yh, -a.yl, b.xh, b.xl, r.yh, r.yl);  // ax by + ay bx
   return r;
 }
 // a * conj(b)

@@ -145,26 +145,26 @@ template <typename V> __device__ __forceinline__ V mul_w83c(V v) {
 }
 template <> __device__ __forceinline__ ff2 mul_w8<ff2>(ff2 v) {
   ff2 r;
-  ff_add(v.xh, v.xl, v.yh, v.yl, r.xh, r.xl);
-  ff_add(v.yh, v.yl, -v.xh, -v.xl, r.yh, r.yl);
+  ff_add_fast(v.xh, v.xl, v.yh, v.yl, r.xh, r.xl);
+  ff_add_fast(v.yh, v.yl, -v.xh, -v.xl, r.yh, r.yl);
   return scale_r2(r);
 }
 template <> __device__ __forceinline__ ff2 mul_w83<ff2>(ff2 v) {
   ff2 r;
-  ff_add(v.yh, v.yl, -v.xh, -v.xl, r.xh, r.xl);
-  ff_add(-v.xh, -v.xl, -v.yh, -v.yl, r.yh, r.yl);
+  ff_add_fast(v.yh, v.yl, -v.xh, -v.xl, r.xh, r.xl);
+  ff_add_fast(-v.xh, -v.xl, -v.yh, -v.yl, r.yh, r.yl);
   return scale_r2(r);
 }
 template <> __device__ __forceinline__ ff2 mul_w8c<ff2>(ff2 v) {
   ff2 r;
-  ff_add(v.xh, v.xl, -v.yh, -v.yl, r.xh, r.xl);
-  ff_add(v.xh, v.xl, v.yh, v.yl, r.yh, r.yl);
+  ff_add_fast(v.xh, v.xl, -v.yh, -v.yl, r.xh, r.xl);
+  ff_add_fast(v.xh, v.xl, v.yh, v.yl, r.yh, r.yl);
   return scale_r2(r);
 }
 template <> __device__ __forceinline__ ff2 mul_w83c<ff2>(ff2 v) {
   ff2 r;
-  ff_add(-v.xh, -v.xl, -v.yh, -v.yl, r.xh, r.xl);
-  ff_add(v.xh, v.xl, -v.yh, -v.yl, r.yh, r.yl);
+  ff_add_fast(-v.xh, -v.xl, -v.yh, -v.yl, r.xh, r.xl);
+  ff_add_fast(v.xh, v.xl, -v.yh, -v.yl, r.yh, r.yl);
   return scale_r2(r);
 }
 

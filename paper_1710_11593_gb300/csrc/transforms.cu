@@ -7,6 +7,8 @@
 // two components independently, so one complex FFT serves two real problems.
 #include <cstdio>
 
+#include <cooperative_groups.h>
+
 #include "convert.cuh"
 #include "fft.cuh"
 #include "fftr.cuh"
@@ -28,7 +30,10 @@ template <> struct EngineTraitsHost<double> { static constexpr int RB = 3; };
 template <> struct EngineTraitsHost<FF> { static constexpr int RB = 3; };
 
 inline void set_smem(const void* fn, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (bytes > 48 * 1024) {
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+  }
 }
 
 // Conversions between double pairs and the storage types.
@@ -141,7 +146,7 @@ template <typename V> __device__ __forceinline__ V vneg(V v) {
   return r;
 }
 
-constexpr int kDstThreads = 512;
+constexpr int kDstThreads = 256;
 
 // No spatial transform (space 0): pairs of rows.
 template <typename T>
@@ -177,146 +182,218 @@ __device__ void rows_inverse(const DstArgs& A, int C) {
   }
 }
 
-// One block: C time columns (C/2 complex transforms of length 2K, K = M+1 a power of two).
+// Power-of-two K: one thread-block cluster of kDstCluster blocks handles 2*G*CPc time
+// columns (G = cluster size); block r owns the column pairs r*CPc .. r*CPc+CPc-1, one
+// length-2K transform each in its shared memory.  Global memory is read and written by
+// all blocks of the cluster over all its columns (a slice of the rows each), so every row
+// segment spans the cluster's 16..64 columns (128 bytes or more); values reach the owning
+// block through distributed shared memory.  The shared-memory budget per block stays small
+// (three blocks per SM) while the global access stays wide.
+constexpr int kDstCluster = 8;
+constexpr int kDstBatch = 8;     // global loads: rows per thread per round
+constexpr int kDstOutBatch = 4;  // remote shared-memory reads per thread per round
+
+__device__ __forceinline__ int slice_lo(int n, int r) { return (int)(((int64_t)n * r) / kDstCluster); }
+
 template <typename T>
-__global__ void __launch_bounds__(kDstThreads) dst_forward_kernel(DstArgs A, int C) {
+__global__ void __cluster_dims__(kDstCluster, 1, 1) __launch_bounds__(kDstThreads)
+    dst_forward_kernel(DstArgs A, int CPc) {
   typedef Vt<T> V;
-  if (A.space == 0) {
-    rows_forward<T>(A, C);
-    return;
-  }
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   V* z = (V*)A.z;
-  const int64_t col0 = (int64_t)blockIdx.x * C;
-  const int64_t M = A.M;
+  const int rank = (int)cl.block_rank();
+  const int lcp = 31 - __clz(CPc);
+  const int GP = kDstCluster * CPc, lgp = 31 - __clz(GP);  // column pairs of the cluster
+  const int64_t col0 = (int64_t)(blockIdx.x / kDstCluster) * (2 * GP);
+  const int M = (int)A.M;
   const int logK2 = A.logK2;
   const int K2 = 1 << logK2, K = K2 >> 1;
-  const int CP = C >> 1;
   const SmLayout L = sm_layout<V>(logK2);
-  for (int t = threadIdx.x; t < CP; t += blockDim.x) {
+  for (int t = threadIdx.x; t < CPc; t += blockDim.x) {
     sm[sm_pos<V>(L, t, 0)] = vzero<V>();
     sm[sm_pos<V>(L, t, K)] = vzero<V>();
   }
-  // odd extension: row j of columns (2t, 2t+1) -> positions j+1 and 2K-j-1; four rows of
-  // loads in flight per thread
-  const int64_t tot = M * CP;
-  for (int64_t e0 = threadIdx.x; e0 < tot; e0 += 4 * (int64_t)blockDim.x) {
-    T va[4], vb[4];
+  cl.sync();  // every block of the cluster is running before remote stores
+  // rows [j0, j1) of all the cluster's columns -> odd extension in the owners' buffers
+  const int j0 = slice_lo(M, rank), j1 = slice_lo(M, rank + 1);
+  const int tot = (j1 - j0) << lgp;
+  for (int e0 = threadIdx.x; e0 < tot; e0 += kDstBatch * (int)blockDim.x) {
+    T va[kDstBatch], vb[kDstBatch];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t e = e0 + q * (int64_t)blockDim.x;
+    for (int q = 0; q < kDstBatch; ++q) {
+      const int e = e0 + q * (int)blockDim.x;
       if (e < tot) {
-        const int64_t j = e / CP, n = col0 + 2 * (e % CP);
+        const int64_t j = j0 + (e >> lgp), n = col0 + 2 * (e & (GP - 1));
         va[q] = dst_in<T>(A, j, n);
         vb[q] = dst_in<T>(A, j, n + 1);
       }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t e = e0 + q * (int64_t)blockDim.x;
+    for (int q = 0; q < kDstBatch; ++q) {
+      const int e = e0 + q * (int)blockDim.x;
       if (e < tot) {
-        const int j = (int)(e / CP), t = (int)(e % CP);
+        const int j = j0 + (e >> lgp), gp = e & (GP - 1);
+        V* dst = cl.map_shared_rank(sm, gp >> lcp);
+        const int t = gp & (CPc - 1);
         const V v = mkv(va[q], vb[q]);
-        sm[sm_pos<V>(L, t, j + 1)] = v;
-        sm[sm_pos<V>(L, t, K2 - j - 1)] = vneg(v);
+        dst[sm_pos<V>(L, t, j + 1)] = v;
+        dst[sm_pos<V>(L, t, K2 - j - 1)] = vneg(v);
       }
     }
   }
-  __syncthreads();
-  fftr_dif<V>(sm, logK2, CP, (const V*)A.tw, false);
-  // positions 4q, 4q+1 (q >= 1) hold frequencies a = brev(4q) < K/2 and K + a; position
-  // 2, 3 the middle mode K/2 (q = 0)
+  cl.sync();
+  fftr_dif<V>(sm, logK2, CPc, (const V*)A.tw, false);
+  cl.sync();
+  // storage positions 4q, 4q+1 (q >= 1) hold frequencies a = brev(4q) < K/2 and K + a;
+  // positions 2, 3 the middle mode K/2 (q = 0).  Pair p = a - 1 holds modes a, K - a.
   const T scale = (T)A.dst_scale;
   const int Q = K >> 1;
-  for (int e = threadIdx.x; e < Q * CP; e += blockDim.x) {
-    const int qq = e / CP, t = e % CP;
-    const int pos = qq == 0 ? 2 : 4 * qq;
-    const int a = brev(pos, logK2);
-    const int64_t p = a - 1;
-    const V ya = sm[sm_pos<V>(L, t, pos)];
-    const V ym = sm[sm_pos<V>(L, t, pos + 1)];
-    const bool self = 2 * a == K;
-    V c0, c1;
-    c0.x = -ya.y * scale;
-    c1.x = ya.x * scale;
-    c0.y = self ? (T)0 : ym.y * scale;
-    c1.y = self ? (T)0 : -ym.x * scale;
-    const int64_t n = col0 + 2 * t;
-    if (n < A.ncols) z[p * A.ld + col_of(A, n)] = c0;
-    if (n + 1 < A.ncols) z[p * A.ld + col_of(A, n + 1)] = c1;
+  const int q0 = slice_lo(Q, rank), q1 = slice_lo(Q, rank + 1);
+  const int totq = (q1 - q0) << lgp;
+  for (int e0 = threadIdx.x; e0 < totq; e0 += kDstOutBatch * (int)blockDim.x) {
+    V ya[kDstOutBatch], ym[kDstOutBatch];
+#pragma unroll
+    for (int q = 0; q < kDstOutBatch; ++q) {  // remote reads of the batch first
+      const int e = e0 + q * (int)blockDim.x;
+      if (e < totq) {
+        const int qq = q0 + (e >> lgp), gp = e & (GP - 1);
+        const V* src = cl.map_shared_rank(sm, gp >> lcp);
+        const int t = gp & (CPc - 1);
+        const int pos = qq == 0 ? 2 : 4 * qq;
+        ya[q] = src[sm_pos<V>(L, t, pos)];
+        ym[q] = src[sm_pos<V>(L, t, pos + 1)];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kDstOutBatch; ++q) {
+      const int e = e0 + q * (int)blockDim.x;
+      if (e < totq) {
+        const int qq = q0 + (e >> lgp), gp = e & (GP - 1);
+        const int pos = qq == 0 ? 2 : 4 * qq;
+        const int a = brev(pos, logK2);
+        const int64_t p = a - 1;
+        const bool self = 2 * a == K;
+        V c0, c1;
+        c0.x = -ya[q].y * scale;
+        c1.x = ya[q].x * scale;
+        c0.y = self ? (T)0 : ym[q].y * scale;
+        c1.y = self ? (T)0 : -ym[q].x * scale;
+        const int64_t n = col0 + 2 * gp;
+        if (n < A.ncols) z[p * A.ld + col_of(A, n)] = c0;
+        if (n + 1 < A.ncols) z[p * A.ld + col_of(A, n + 1)] = c1;
+      }
+    }
   }
+  cl.sync();  // remote reads done before any block exits
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kDstThreads) dst_inverse_kernel(DstArgs A, int C) {
+__global__ void __cluster_dims__(kDstCluster, 1, 1) __launch_bounds__(kDstThreads)
+    dst_inverse_kernel(DstArgs A, int CPc) {
   typedef Vt<T> V;
-  if (A.space == 0) {
-    rows_inverse<T>(A, C);
-    return;
-  }
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const V* z = (const V*)A.z;
-  const int64_t col0 = (int64_t)blockIdx.x * C;
+  const int rank = (int)cl.block_rank();
+  const int lcp = 31 - __clz(CPc);
+  const int GP = kDstCluster * CPc, lgp = 31 - __clz(GP);
+  const int64_t col0 = (int64_t)(blockIdx.x / kDstCluster) * (2 * GP);
   const int logK2 = A.logK2;
   const int K2 = 1 << logK2, K = K2 >> 1;
-  const int CP = C >> 1;
-  const int64_t P = K >> 1;
+  const int P = K >> 1;
   const SmLayout L = sm_layout<V>(logK2);
-  for (int t = threadIdx.x; t < CP; t += blockDim.x) {
+  for (int t = threadIdx.x; t < CPc; t += blockDim.x) {
     sm[sm_pos<V>(L, t, 0)] = vzero<V>();
     sm[sm_pos<V>(L, t, K)] = vzero<V>();
   }
-  // pair p of columns (2t, 2t+1): modes a = p+1 and b = K-a -> positions a, 2K-a, b, 2K-b
-  const int64_t tot = P * CP;
-  for (int64_t e0 = threadIdx.x; e0 < tot; e0 += 4 * (int64_t)blockDim.x) {
-    V c0[4], c1[4];
+  cl.sync();
+  // pairs [p0, p1) of all columns: modes a = p+1 and b = K-a -> positions a, 2K-a, b, 2K-b
+  const int p0 = slice_lo(P, rank), p1 = slice_lo(P, rank + 1);
+  const int tot = (p1 - p0) << lgp;
+  for (int e0 = threadIdx.x; e0 < tot; e0 += kDstBatch * (int)blockDim.x) {
+    V c0[kDstBatch], c1[kDstBatch];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t e = e0 + q * (int64_t)blockDim.x;
+    for (int q = 0; q < kDstBatch; ++q) {
+      const int e = e0 + q * (int)blockDim.x;
       if (e < tot) {
-        const int64_t p = e / CP, n = col0 + 2 * (e % CP);
+        const int64_t p = p0 + (e >> lgp), n = col0 + 2 * (e & (GP - 1));
         c0[q] = n < A.N ? z[p * A.ld + col_of(A, n)] : vzero<V>();
         c1[q] = n + 1 < A.N ? z[p * A.ld + col_of(A, n + 1)] : vzero<V>();
       }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t e = e0 + q * (int64_t)blockDim.x;
+    for (int q = 0; q < kDstBatch; ++q) {
+      const int e = e0 + q * (int)blockDim.x;
       if (e < tot) {
-        const int a = (int)(e / CP) + 1, t = (int)(e % CP);
+        const int a = p0 + (e >> lgp) + 1, gp = e & (GP - 1);
         const int b = K - a;
+        V* dst = cl.map_shared_rank(sm, gp >> lcp);
+        const int t = gp & (CPc - 1);
         const V va = mkv(c0[q].x, c1[q].x);
-        sm[sm_pos<V>(L, t, a)] = va;
-        sm[sm_pos<V>(L, t, K2 - a)] = vneg(va);
+        dst[sm_pos<V>(L, t, a)] = va;
+        dst[sm_pos<V>(L, t, K2 - a)] = vneg(va);
         if (b != a) {
           const V vb = mkv(c0[q].y, c1[q].y);
-          sm[sm_pos<V>(L, t, b)] = vb;
-          sm[sm_pos<V>(L, t, K2 - b)] = vneg(vb);
+          dst[sm_pos<V>(L, t, b)] = vb;
+          dst[sm_pos<V>(L, t, K2 - b)] = vneg(vb);
         }
       }
     }
   }
-  __syncthreads();
-  fftr_dif<V>(sm, logK2, CP, (const V*)A.tw, false);
+  cl.sync();
+  fftr_dif<V>(sm, logK2, CPc, (const V*)A.tw, false);
+  cl.sync();
   // rows j = brev(4q) (and K/2 at q = 0) from position 4q, rows K - j from 4q + 1
   const T scale = (T)A.dst_scale;
   const int Q = K >> 1;
-  for (int e = threadIdx.x; e < Q * CP; e += blockDim.x) {
-    const int qq = e / CP, t = e % CP;
-    const int pos = qq == 0 ? 2 : 4 * qq;
-    const int j = brev(pos, logK2);
-    const V yj = sm[sm_pos<V>(L, t, pos)];
-    const int64_t n = col0 + 2 * t;
-    dst_out<T>(A, j - 1, n, -yj.y * scale);
-    dst_out<T>(A, j - 1, n + 1, yj.x * scale);
-    if (2 * j != K) {
-      const V ym = sm[sm_pos<V>(L, t, pos + 1)];
-      dst_out<T>(A, K - j - 1, n, ym.y * scale);
-      dst_out<T>(A, K - j - 1, n + 1, -ym.x * scale);
+  const int q0 = slice_lo(Q, rank), q1 = slice_lo(Q, rank + 1);
+  const int totq = (q1 - q0) << lgp;
+  for (int e0 = threadIdx.x; e0 < totq; e0 += kDstOutBatch * (int)blockDim.x) {
+    V yj[kDstOutBatch], ym[kDstOutBatch];
+#pragma unroll
+    for (int q = 0; q < kDstOutBatch; ++q) {
+      const int e = e0 + q * (int)blockDim.x;
+      if (e < totq) {
+        const int qq = q0 + (e >> lgp), gp = e & (GP - 1);
+        const V* src = cl.map_shared_rank(sm, gp >> lcp);
+        const int t = gp & (CPc - 1);
+        const int pos = qq == 0 ? 2 : 4 * qq;
+        yj[q] = src[sm_pos<V>(L, t, pos)];
+        ym[q] = src[sm_pos<V>(L, t, pos + 1)];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kDstOutBatch; ++q) {
+      const int e = e0 + q * (int)blockDim.x;
+      if (e < totq) {
+        const int qq = q0 + (e >> lgp), gp = e & (GP - 1);
+        const int pos = qq == 0 ? 2 : 4 * qq;
+        const int j = brev(pos, logK2);
+        const int64_t n = col0 + 2 * gp;
+        dst_out<T>(A, j - 1, n, -yj[q].y * scale);
+        dst_out<T>(A, j - 1, n + 1, yj[q].x * scale);
+        if (2 * j != K) {
+          dst_out<T>(A, K - j - 1, n, ym[q].y * scale);
+          dst_out<T>(A, K - j - 1, n + 1, -ym[q].x * scale);
+        }
+      }
     }
   }
+  cl.sync();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kDstThreads) rows_forward_kernel(DstArgs A, int C) {
+  rows_forward<T>(A, C);
+}
+template <typename T>
+__global__ void __launch_bounds__(kDstThreads) rows_inverse_kernel(DstArgs A, int C) {
+  rows_inverse<T>(A, C);
 }
 
 // Sine transform for any K = M+1 (Bluestein / chirp-z).  With W = exp(-2 pi i / L),
@@ -334,7 +411,7 @@ __global__ void __launch_bounds__(kDstThreads) dst_bluestein_kernel(DstArgs A, i
   const int64_t M = A.M;
   const int K = A.K, Lq = 2 * K;
   const int logP = A.logP, P = 1 << logP, H = P >> 1;
-  const int CP = C >> 1;
+  const int CP = C >> 1, lcp = 31 - __clz(CP);
   const SmLayout Ls = sm_layout<V>(logP);
   const V* __restrict__ chirp = (const V*)A.chirp;
   const V* __restrict__ tw = (const V*)A.tw;
@@ -345,23 +422,23 @@ __global__ void __launch_bounds__(kDstThreads) dst_bluestein_kernel(DstArgs A, i
   for (int e = threadIdx.x; e < CP * Z; e += blockDim.x) sm[sm_pos<V>(Ls, e / Z, e % Z)] = vzero<V>();
   __syncthreads();
   if (fwd) {
-    const int64_t tot = M * CP;
-    for (int64_t e0 = threadIdx.x; e0 < tot; e0 += 4 * (int64_t)blockDim.x) {
+    const int tot = (int)M << lcp;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += 4 * (int)blockDim.x) {
       T va[4], vb[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int64_t e = e0 + q * (int64_t)blockDim.x;
+        const int e = e0 + q * (int)blockDim.x;
         if (e < tot) {
-          const int64_t j = e / CP, n = col0 + 2 * (e % CP);
+          const int64_t j = (e >> lcp), n = col0 + 2 * ((e & (CP - 1)));
           va[q] = dst_in<T>(A, j, n);
           vb[q] = dst_in<T>(A, j, n + 1);
         }
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int64_t e = e0 + q * (int64_t)blockDim.x;
+        const int e = e0 + q * (int)blockDim.x;
         if (e < tot) {
-          const int j = (int)(e / CP), t = (int)(e % CP);
+          const int j = (e >> lcp), t = (e & (CP - 1));
           const V v = mkv(va[q], vb[q]);
           sm[sm_pos<V>(Ls, t, j + 1)] = cmul(v, chirp[j + 1]);
           sm[sm_pos<V>(Ls, t, Lq - j - 1)] = cmul(vneg(v), chirp[Lq - j - 1]);
@@ -370,23 +447,23 @@ __global__ void __launch_bounds__(kDstThreads) dst_bluestein_kernel(DstArgs A, i
     }
   } else {
     const V* z = (const V*)A.z;
-    const int64_t tot = (int64_t)((M + 1) / 2) * CP;
-    for (int64_t e0 = threadIdx.x; e0 < tot; e0 += 4 * (int64_t)blockDim.x) {
+    const int tot = (int)((M + 1) / 2) << lcp;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += 4 * (int)blockDim.x) {
       V c0[4], c1[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int64_t e = e0 + q * (int64_t)blockDim.x;
+        const int e = e0 + q * (int)blockDim.x;
         if (e < tot) {
-          const int64_t p = e / CP, n = col0 + 2 * (e % CP);
+          const int64_t p = (e >> lcp), n = col0 + 2 * ((e & (CP - 1)));
           c0[q] = n < A.N ? z[p * A.ld + col_of(A, n)] : vzero<V>();
           c1[q] = n + 1 < A.N ? z[p * A.ld + col_of(A, n + 1)] : vzero<V>();
         }
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int64_t e = e0 + q * (int64_t)blockDim.x;
+        const int e = e0 + q * (int)blockDim.x;
         if (e < tot) {
-          const int a = (int)(e / CP) + 1, t = (int)(e % CP);
+          const int a = (e >> lcp) + 1, t = (e & (CP - 1));
           const int b = K - a;
           const V va = mkv(c0[q].x, c1[q].x);
           sm[sm_pos<V>(Ls, t, a)] = cmul(va, chirp[a]);
@@ -409,8 +486,8 @@ __global__ void __launch_bounds__(kDstThreads) dst_bluestein_kernel(DstArgs A, i
   if (fwd) {
     V* z = (V*)A.z;
     const int64_t P2 = (M + 1) / 2;
-    for (int64_t e = threadIdx.x; e < P2 * CP; e += blockDim.x) {
-      const int a = (int)(e / CP) + 1, t = (int)(e % CP);
+    for (int e = threadIdx.x; e < ((int)P2 << lcp); e += blockDim.x) {
+      const int a = (e >> lcp) + 1, t = (e & (CP - 1));
       const int b = K - a;
       const int64_t p = a - 1;
       const V ya = cmul(sm[sm_pos<V>(Ls, t, a)], chirp[a]);
@@ -426,8 +503,8 @@ __global__ void __launch_bounds__(kDstThreads) dst_bluestein_kernel(DstArgs A, i
       if (n + 1 < A.ncols) z[p * A.ld + col_of(A, n + 1)] = c1;
     }
   } else {
-    for (int64_t e = threadIdx.x; e < M * CP; e += blockDim.x) {
-      const int j = (int)(e / CP) + 1, t = (int)(e % CP);
+    for (int e = threadIdx.x; e < ((int)M << lcp); e += blockDim.x) {
+      const int j = (e >> lcp) + 1, t = (e & (CP - 1));
       const V y = cmul(sm[sm_pos<V>(Ls, t, j)], chirp[j]);
       const int64_t n = col0 + 2 * t;
       dst_out<T>(A, j - 1, n, -y.y * scale);
@@ -436,14 +513,24 @@ __global__ void __launch_bounds__(kDstThreads) dst_bluestein_kernel(DstArgs A, i
   }
 }
 
-// Column pairs per block: as many as fit (power of two, <= 4 pairs) in ~160 KB of shared
-// memory.
+// Columns per block (even, C/2 a power of two): as many column pairs (<= 4) as keep the
+// block's shared memory within 64 KB (three blocks per SM), at least one pair.
 template <typename T>
 int dst_cols(int logn) {
   const size_t per_pair = ((size_t)1 << logn) * sizeof(Vt<T>);
   int C = 8;
-  while (C > 2 && (size_t)(C / 2) * per_pair > 160 * 1024) C >>= 1;
+  while (C > 2 && (size_t)(C / 2) * per_pair > 64 * 1024) C >>= 1;
   return C;
+}
+
+// Column pairs per block of the cluster kernels: 1, 2 or 4 transforms within 64 KB of
+// shared memory (one transform if it is larger).
+template <typename T>
+int dst_pairs_per_block(int logK2) {
+  const size_t per = ((size_t)1 << logK2) * sizeof(Vt<T>);
+  int c = 4;
+  while (c > 1 && (size_t)c * per > 64 * 1024) c >>= 1;
+  return c;
 }
 
 template <typename T>
@@ -455,15 +542,23 @@ void dst_launch(const DstArgs& a, bool fwd, cudaStream_t st) {
     dst_bluestein_kernel<T><<<(unsigned)((a.ncols + C - 1) / C), kDstThreads, smem, st>>>(a, C, fwd ? 1 : 0);
     return;
   }
-  const int C = a.space ? dst_cols<T>(a.logK2) : 8;
-  const size_t smem = a.space ? (size_t)(C / 2) * ((size_t)1 << a.logK2) * sizeof(Vt<T>) : 0;
-  dim3 grid((unsigned)((a.ncols + C - 1) / C));
+  if (!a.space) {
+    const int C = 8;
+    dim3 grid((unsigned)((a.ncols + C - 1) / C));
+    if (fwd) rows_forward_kernel<T><<<grid, kDstThreads, 0, st>>>(a, C);
+    else rows_inverse_kernel<T><<<grid, kDstThreads, 0, st>>>(a, C);
+    return;
+  }
+  const int CPc = dst_pairs_per_block<T>(a.logK2);
+  const int cols = 2 * kDstCluster * CPc;
+  const size_t smem = (size_t)CPc * ((size_t)1 << a.logK2) * sizeof(Vt<T>);
+  dim3 grid((unsigned)(((a.ncols + cols - 1) / cols) * kDstCluster));
   if (fwd) {
     set_smem((const void*)dst_forward_kernel<T>, smem);
-    dst_forward_kernel<T><<<grid, kDstThreads, smem, st>>>(a, C);
+    dst_forward_kernel<T><<<grid, kDstThreads, smem, st>>>(a, CPc);
   } else {
     set_smem((const void*)dst_inverse_kernel<T>, smem);
-    dst_inverse_kernel<T><<<grid, kDstThreads, smem, st>>>(a, C);
+    dst_inverse_kernel<T><<<grid, kDstThreads, smem, st>>>(a, CPc);
   }
 }
 
@@ -929,7 +1024,7 @@ __global__ void __launch_bounds__(kThreads) conv_col_fwd_kernel(ConvArgs A, int 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) conv_row_kernel(ConvArgs A, int logn1, int logn2, int rows) {
+__global__ void __launch_bounds__(kThreads, 3) conv_row_kernel(ConvArgs A, int logn1, int logn2, int rows) {
   typedef Vt<T> V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);

@@ -52,11 +52,14 @@ class ftoep_tuning(ctypes.Structure):
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load libftoep.so (built by ``paper_1710_11593_gb300.build``)."""
+def load(path: Optional[str] = None):
+    """Load libftoep.so (built by ``paper_1710_11593_gb300.build``; FTOEP_LIB in the
+    environment names another build of the same library)."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = os.environ.get("FTOEP_LIB", LIB_PATH)
     if not os.path.exists(path):
         raise FtoepError(FTOEP_EUNSUPPORTED, f"{path} not found: build it with paper_1710_11593_gb300.build.build()")
     lib = ctypes.CDLL(path)
