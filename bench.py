@@ -1,10 +1,14 @@
 #!/usr/bin/env python3
 """Benchmark of the Caputo L1 time-marching solve (libftoep) on synthetic workloads.
 
-Default workload: time-fractional diffusion, gamma = 0.7, M = 1023 interior points,
-N = 65536 steps, exact u = t^2 sin(pi x) (f in closed form), double-precision path.
-One step = one full solve (sine transform, half-split Toeplitz solve of every mode,
-inverse transform) of the whole field with inputs resident in HBM.
+Default workload: the batched mixed-precision solve -- 512 independent problems with
+N log-uniform in [2^10, 2^17], M log-uniform in [63, 2047], gamma in (0.1, 0.95) u
+(1.05, 1.9), random separable sources (seed 1234) -- compared with the plain double
+solve of the same batch.  One step = one full solve of every problem (sine transform,
+half-split Toeplitz solve of every mode, inverse transform, residual and one correction
+sweep) with inputs resident in HBM.  --workload diffusion|wave|scalar time the single
+problems (gamma 0.7, M 1023, N 65536 double; gamma 1.5, M 4095, N 262144 mixed; the scalar
+ODE, N 1024).
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle (plain
 O(M N^2) direct time marching) on a bounded time prefix of the same workload.
@@ -36,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="diffusion", choices=["diffusion", "wave", "scalar", "batched"])
+    ap.add_argument("--workload", default="batched", choices=["diffusion", "wave", "scalar", "batched"])
     ap.add_argument("--nprob", type=int, default=512, help="batched workload: number of problems")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
                     help="default: fp64 for diffusion/scalar, mixed for wave")
@@ -76,7 +80,7 @@ def block_flops_per_unknown(B, L, Sf):
 
 
 def tuning_of(precision, Np):
-    B = min(2048, Np)
+    B = min(4096, Np)
     L = min(16, B)
     return B, L, 64
 
@@ -84,6 +88,14 @@ def tuning_of(precision, Np):
 def flop_model(p, precision):
     """Nominal flops of one solve per kernel class (5 n log2 n per complex FFT of length n,
     6 per complex product, 2 per multiply-add), following the schedule of the library."""
+    return work_model(p, precision)[0]
+
+
+def work_model(p, precision):
+    """(flops, bytes) of one solve per kernel class.  Bytes are the compulsory HBM bytes
+    of each class's algorithm: every array the class reads or writes crosses HBM once
+    (z pairs 8 B per complex float / 16 B double, fields 8 B per double, 4 B per float);
+    the four-step scratch round trips are not counted (they are the implementation's)."""
     Np = 16
     while Np < p.N:
         Np *= 2
@@ -92,29 +104,80 @@ def flop_model(p, precision):
     nblk = -(-p.N // B)
     ncols = nblk * B
     nsolve = 1 if precision == "fp64" else 2
+    zb = 16 if precision == "fp64" else 8  # bytes per complex of the solve
     # block solve = causal convolution with the block inverse: FFT and inverse FFT of length
-    # 2B per pair plus two complex products per point: 10 log2(2B) + 14 flops per unknown
+    # 2B per pair plus two complex products per point; reads z, writes z, reads C1, C2
     block = nsolve * nblk * (2 * P * B) * (10 * math.log2(2 * B) + 14)
+    block_b = nsolve * nblk * P * (2 * B * zb + 2 * (2 * B) * zb)
     conv_smem = conv_4 = 0.0
+    smem_b = four_b = 0.0
     nsmem = 4096 if precision == "fp64" else 8192
     for v in range(1, nblk):
         s = B << ((v & -v).bit_length() - 1)
         fl = P * (20 * s * math.log2(2 * s) + 12 * s)
+        by = P * 3 * s * zb  # input half, output half read and written
         if 2 * s <= nsmem:
             conv_smem += fl
+            smem_b += by
         else:
             conv_4 += fl
+            four_b += by
     conv_smem *= nsolve
     conv_4 *= nsolve
-    sine = 0.0
+    smem_b *= nsolve
+    four_b *= nsolve
+    sine = sine_b = 0.0
     if p.space == 1:
         K2 = 2 * (p.M + 1)
         sine = 2 * nsolve * (ncols / 2) * 5 * K2 * math.log2(K2)
-    out = {"block_solve": block, "conv_smem": conv_smem, "conv_fourstep": conv_4, "sine": sine}
-    if precision == "mixed":  # residual product of length 2Np in float-float
+        fb = 8  # double field in, out (fp64) / f double, v float, r float (mixed)
+        sine_b = nsolve * (p.M * p.N * (fb + (fb if precision == "fp64" else 4)) + 2 * P * ncols * zb)
+    flops = {"block_solve": block, "conv_smem": conv_smem, "conv_fourstep": conv_4, "sine": sine}
+    byts = {"block_solve": block_b, "conv_smem": smem_b, "conv_fourstep": four_b, "sine": sine_b}
+    if precision == "mixed":  # residual product of length 2Np in float-float, residual kernel
         n = 2 * Np
-        out["residual"] = P * (10 * n * math.log2(n) + 6 * n)
+        flops["residual"] = P * (10 * n * math.log2(n) + 6 * n)
+        byts["residual"] = P * n * 16 * 2 + p.M * p.N * (8 + 8 + 4)
+    return flops, byts
+
+
+def roofline_of(flops, byts, prof, steps, precision):
+    """Roofline of the dominant kernel class: achieved flop rate against the ALU peak of
+    its arithmetic and achieved algorithmic-byte rate against the measured HBM copy
+    bandwidth; the binding one (larger fraction) is reported, the other beside it."""
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    name, (ms, ops, launches) = dom[0], dom[1]
+    if name not in flops or ms <= 0 or flops[name] <= 0:
+        return None
+    sec = ms * 1e-3
+    if precision == "mixed" and name != "residual":
+        peak, what = FP32_PEAK_TFLOPS, "FP32 (152 SMs x 128 lanes x 2 flops x 2.07 GHz)"
+    else:
+        peak, what = FP64_PEAK_TFLOPS, "FP64 (recipe nominal 1.25; DFMA probe 1.19)"
+    alu = flops[name] * steps / sec / 1e12
+    hbm_peak = measured_peaks().get("hbm_gbs", 6800.0)
+    hbm = byts.get(name, 0.0) * steps / sec / 1e9
+    alu_frac, hbm_frac = alu / peak, hbm / hbm_peak
+    alu_obj = {"bound": "alu", "achieved": alu, "peak": peak, "unit": "TFLOP/s", "frac": alu_frac,
+               "peak_note": what}
+    hbm_obj = {"bound": "hbm", "achieved": hbm, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac,
+               "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs)"}
+    main, other = (alu_obj, hbm_obj) if alu_frac >= hbm_frac else (hbm_obj, alu_obj)
+    out = dict(main)
+    out.update({"kernel_class": name, "traffic": None, "per_launch_ms": ms / max(1, ops),
+                "launches": launches, "other_bound": other,
+                "note": "flops: 5 n log2 n per complex FFT of length n, 6 per complex product; bytes: "
+                        "compulsory HBM bytes of the class (no four-step scratch); event time of the "
+                        "class over the timed steps"})
     return out
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -193,21 +256,30 @@ def run_reference(args):
         return 0
     p, wname = workload(args.workload, args.nprob, M=args.M, N=args.N)
     if isinstance(p, list):
-        p = p[0]
-    nprefix = min(p.N, 1024 if p.M > 1 else p.N)
+        # batched workload: each step is the oracle on the first min(N, 512) levels of the
+        # first 8 problems (all their points)
+        sample_probs = [(q, min(q.N, 512)) for q in p[:8]]
+        sample = "first min(N,512) levels of the first 8 problems (same tau), all points; O(M N^2) direct marching"
+        config = {"workload": wname, "nprob": len(p), "precision": "fp64"}
+    else:
+        nprefix = min(p.N, 1024 if p.M > 1 else p.N)
+        sample_probs = [(p, nprefix)]
+        sample = f"first {nprefix} of {p.N} time steps, all {p.M} points (same tau); O(M N^2) direct marching"
+        config = {"workload": wname, "M": p.M, "N": p.N, "gamma": p.gamma, "precision": "fp64"}
+    units = sum(q.M * n for q, n in sample_probs)
     for _ in range(args.warmup):
-        time_oracle(p, nprefix)
-    tot = 0.0
+        for q, n in sample_probs:
+            time_oracle(q, n)
+    tot, th = 0.0, 1
     for _ in range(args.steps):
-        _, dts, th = time_oracle(p, nprefix)
-        tot += dts
+        for q, n in sample_probs:
+            _, dts, th = time_oracle(q, n)
+            tot += dts
     dt = tot / args.steps
-    v = p.M * nprefix / dt
-    sample = f"first {nprefix} of {p.N} time steps, all {p.M} points (same tau); O(M N^2) direct marching"
+    v = units / dt
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "unknowns/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": wname, "M": p.M, "N": p.N, "gamma": p.gamma, "precision": "fp64"},
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
            "cpu_baseline": {"value": v, "unit": "unknowns/s", "cores": th, "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -251,7 +323,7 @@ def run_batched(args):
         plan.solve(f, u)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
-    plan.profile(True)
+    plan.profile(False)  # resets the launch counters; no per-launch events in the timed steps
     barrier()
     torch.cuda.synchronize()
     clocks.start()
@@ -265,6 +337,10 @@ def run_batched(args):
     barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
+    launches = sum(v[2] for v in plan.profile_read().values())
+    # kernel-class times from one more (untimed) step with a CUDA-event pair around every launch
+    plan.profile(True)
+    plan.solve(f, u)
     prof = plan.profile_read()
     plan.profile(False)
     if world > 1:
@@ -272,9 +348,17 @@ def run_batched(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = world * units / (ms * 1e-3)
-    launches = sum(v[2] for v in prof.values())
     busy = sum(x[0] for x in prof.values())
     shares = {k: v[0] / max(1e-9, busy) for k, v in prof.items()}
+    fl, by = {}, {}
+    for p in probs:
+        f1, b1 = work_model(p, precision)
+        for k in f1:
+            fl[k] = fl.get(k, 0.0) + f1[k]
+            by[k] = by.get(k, 0.0) + b1[k]
+    roof = roofline_of(fl, by, prof, 1, precision)
+    if roof:
+        roof["note"] += "; problems run on 4 concurrent streams, so class event times include shared GPU time"
     # end to end through host buffers (pinned), copies inside the call
     e2e = None
     try:
@@ -337,7 +421,7 @@ def run_batched(args):
                "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f32+f64", "data": "synthetic",
                "config": {"workload": wname, "nprob": len(probs), "unknowns": units, "precision": precision,
                           "l2": f"inputs larger than L2 (f = {units * 8 / 1e9:.1f} GB)"},
-               "roofline": None, "kernel_time_share": shares, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+               "roofline": roof, "kernel_time_share": shares, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                "gpu_launches": launches, "compare": compare}
         print(json.dumps(out))
     if world > 1:
@@ -374,7 +458,7 @@ def run_ours(args):
         plan.solve(f, u)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
-    plan.profile(True)
+    plan.profile(False)  # resets the launch counters; no per-launch events in the timed steps
     barrier()
     torch.cuda.synchronize()
     clocks.start()
@@ -388,6 +472,10 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
+    launches = sum(v[2] for v in plan.profile_read().values())
+    # kernel-class times from one more (untimed) step with a CUDA-event pair around every launch
+    plan.profile(True)
+    plan.solve(f, u)
     prof = plan.profile_read()
     plan.profile(False)
     if world > 1:
@@ -396,25 +484,12 @@ def run_ours(args):
         ms = float(t.item())
     units = p.M * p.N
     value = world * units / (ms * 1e-3)
-    launches = sum(v[2] for v in prof.values())
     tot_ms = sum(x[0] for x in prof.values())
     shares = {k: v[0] / max(1e-9, tot_ms) for k, v in prof.items()}
 
-    # roofline of the dominant kernel class: nominal flops of the timed steps / its event time
-    model = flop_model(p, precision)
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
-    roof = None
-    if dom[0] in model and dom[1][0] > 0 and model[dom[0]] > 0:
-        flops = model[dom[0]] * args.steps
-        ach = flops / (dom[1][0] * 1e-3) / 1e12
-        if precision == "mixed" and dom[0] != "residual":
-            peak, what = FP32_PEAK_TFLOPS, "FP32 (152 SMs x 128 lanes x 2 x 2.07 GHz)"
-        else:
-            peak, what = FP64_PEAK_TFLOPS, "FP64 (recipe nominal 1.25; DFMA probe 1.19)"
-        roof = {"bound": "alu", "kernel_class": dom[0], "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None, "per_launch_ms": dom[1][0] / max(1, dom[1][1]),
-                "note": "nominal flops (5 n log2 n per complex FFT of length n, 6 per complex product) of "
-                        "the class / its CUDA-event time; peak = " + what}
+    # roofline of the dominant kernel class
+    fl, by = work_model(p, precision)
+    roof = roofline_of(fl, by, prof, 1, precision)
 
     # end to end: same solve through the C ABI with pinned HOST buffers (copies inside)
     fh = f.cpu().pin_memory()

@@ -782,7 +782,7 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
     pb.tau = pb.d.T / (double)pb.N;
     pb.h = pb.d.space ? pb.d.L / (double)(pb.M + 1) : 1.0;
     pb.scale = scheme_scale(pb.d.kind, pb.d.gamma, pb.tau);
-    const int Bdef = 2048;
+    const int Bdef = 4096;
     const int Ldef = 16;
     int B = (tune && tune->fft_tile) ? tune->fft_tile : Bdef;
     if (B > np) B = (int)np;
