@@ -648,8 +648,8 @@ ftoep_status build_bluestein(ftoep_plan pl, Prob& pb) {
 ftoep_status build_block_inverse(ftoep_plan pl, Ws& w, Prob& pb, Prec pr, void** c1, void** c2) {
   cudaStream_t st = w.st;
   const int64_t n = 2 * (int64_t)pb.B;
-  ALLOC(*c1, (size_t)pb.P * n * velem(pr));
-  ALLOC(*c2, (size_t)pb.P * n * velem(pr));
+  ALLOC(*c1, (size_t)pb.P * n * velem(pr));  // C1 and C2 share one Hermitian-packed array
+  *c2 = nullptr;
   double2* z = (double2*)w.z;
   LAUNCH(FTOEP_K_OTHER, launch_unit_impulse(z, pb.Np, pb.P, pb.B, st));
   CK(cudaMemsetAsync(w.prefix, 0, (size_t)pb.P * sizeof(double2), st));

@@ -45,6 +45,11 @@ __global__ void unit_impulse_kernel(double2* z, int64_t ld, int64_t npairs, int 
   for (int i = threadIdx.x; i < B; i += blockDim.x) z[p * ld + i] = i == 0 ? make_double2(1.0, 1.0) : make_double2(0.0, 0.0);
 }
 
+// C1 and C2 are spectra of real sequences ((h_a +- h_b)/2), so C(n-k) = conj(C(k)), and the
+// solve visits every frequency together with its partner.  One length-n array holds both:
+// at the position of the lower of the two partner positions C1, at the partner's position
+// C2 of that lower one; the two self-partner frequencies (0 and n/2) are real and share
+// their slot as (C1, C2).
 template <typename TS>
 __global__ void __launch_bounds__(kThreads) inverse_spectrum_kernel(InvSpecArgs A) {
   typedef Vt<TS> VS;
@@ -57,16 +62,20 @@ __global__ void __launch_bounds__(kThreads) inverse_spectrum_kernel(InvSpecArgs 
   __syncthreads();
   fft_dif<double2>(sm, logn, 1, 0, A.tw64, true);
   const double inv = 1.0 / (double)n;
-  VS* c1 = (VS*)A.c1 + p * (int64_t)n;
-  VS* c2 = (VS*)A.c2 + p * (int64_t)n;
+  VS* c = (VS*)A.c1 + p * (int64_t)n;
   for (int pos = threadIdx.x; pos < n; pos += blockDim.x) {
-    const double2 zk = sm[pos];
-    const double2 zp = sm[partner_pos(pos, logn)];
-    // H_a = (Zk + conj Zp)/2, H_b = (Zk - conj Zp)/(2i)
+    const int pp = partner_pos(pos, logn);
+    const int lo = pos < pp ? pos : pp;
+    const double2 zk = sm[lo];
+    const double2 zp = sm[partner_pos(lo, logn)];
+    // H_a = (Zk + conj Zp)/2, H_b = (Zk - conj Zp)/(2i) at the lower position
     const double har = 0.5 * (zk.x + zp.x), hai = 0.5 * (zk.y - zp.y);
     const double hbr = 0.5 * (zk.y + zp.y), hbi = -0.5 * (zk.x - zp.x);
-    c1[pos] = mkv((TS)(0.5 * (har + hbr) * inv), (TS)(0.5 * (hai + hbi) * inv));
-    c2[pos] = mkv((TS)(0.5 * (har - hbr) * inv), (TS)(0.5 * (hai - hbi) * inv));
+    const double c1r = 0.5 * (har + hbr) * inv, c1i = 0.5 * (hai + hbi) * inv;
+    const double c2r = 0.5 * (har - hbr) * inv, c2i = 0.5 * (hai - hbi) * inv;
+    if (pos == pp) c[pos] = mkv((TS)c1r, (TS)c2r);
+    else if (pos < pp) c[pos] = mkv((TS)c1r, (TS)c1i);
+    else c[pos] = mkv((TS)c2r, (TS)c2i);
   }
 }
 
@@ -109,28 +118,31 @@ __global__ void __launch_bounds__(kThreads) block_inverse_kernel(BlockInvArgs A)
   }, SmPut<V>{sm, L});
   __syncthreads();
   fftr_passes<V, true>(sm, logn, 1, tw, 1, np, false);
-  const V* __restrict__ c1 = (const V*)A.c1 + p * (int64_t)n;
-  const V* __restrict__ c2 = (const V*)A.c2 + p * (int64_t)n;
+  const V* __restrict__ cs = (const V*)A.c1 + p * (int64_t)n;
   for (int pos = threadIdx.x; pos < n; pos += blockDim.x) {
     const int pp = partner_pos(pos, logn);
     if (pp < pos) continue;
     const int q1 = sm_pos<V>(L, 0, pos);
     const V z1 = sm[q1];
-    if (pp == pos) {
-      V zc;
-      zc.x = z1.x;
-      zc.y = -z1.y;
-      sm[q1] = cadd(cmul(c1[pos], z1), cmul(c2[pos], zc));
+    V z1c;
+    z1c.x = z1.x;
+    z1c.y = -z1.y;
+    if (pp == pos) {  // real C1, C2 packed in one slot
+      const V c = cs[pos];
+      V r;
+      r.x = c.x * z1.x + c.y * z1c.x;
+      r.y = c.x * z1.y + c.y * z1c.y;
+      sm[q1] = r;
     } else {
+      const V c1 = cs[pos], c2 = cs[pp];
       const int q2 = sm_pos<V>(L, 0, pp);
       const V z2 = sm[q2];
-      V z1c, z2c;
-      z1c.x = z1.x;
-      z1c.y = -z1.y;
+      V z2c;
       z2c.x = z2.x;
       z2c.y = -z2.y;
-      sm[q1] = cadd(cmul(c1[pos], z1), cmul(c2[pos], z2c));
-      sm[q2] = cadd(cmul(c1[pp], z2), cmul(c2[pp], z1c));
+      // Y_k = C1_k Z_k + C2_k conj(Z_{n-k}); at the partner the conjugate coefficients
+      sm[q1] = cadd(cmul(c1, z1), cmul(c2, z2c));
+      sm[q2] = cadd(cmulc(z2, c1), cmulc(z1c, c2));
     }
   }
   __syncthreads();

@@ -176,7 +176,8 @@ size_t block_solve_smem(Prec prec, int B, int Sf);
 
 // Block solve by the inverse of the block operator (block_inverse.cu): per pair the
 // spectra C1, C2 (length 2B, this library's FFT order, divided by 2B) of the two modes'
-// inverse first columns h (first B entries of T_m^-1 e_1).
+// inverse first columns h (first B entries of T_m^-1 e_1), Hermitian-packed into one
+// length-2B array c1 (C1 at the lower of two partner positions, C2 at the other; c2 unused).
 struct InvSpecArgs {
   const double2* h;   // [npairs][ldh]: h of mode 2p in .x, of mode 2p+1 in .y
   int64_t ldh;
