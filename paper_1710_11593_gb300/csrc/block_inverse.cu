@@ -96,7 +96,7 @@ __device__ __forceinline__ void acc2(float& s, float& c, float x) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) block_inverse_kernel(BlockInvArgs A) {
+__global__ void __launch_bounds__(kThreads, 3) block_inverse_kernel(BlockInvArgs A) {
   typedef Vt<T> V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);

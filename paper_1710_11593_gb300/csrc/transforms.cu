@@ -958,7 +958,7 @@ struct SubUpperCols {  // column t: zo[(e - h1) n2 + t] -= v for e >= h1
 // product with the kernel spectrum and the first inverse pass run fused in registers, and
 // the last inverse pass writes (mode 0: subtracts) the wanted half straight to global.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) conv_smem_kernel(ConvArgs A) {
+__global__ void __launch_bounds__(kThreads, 3) conv_smem_kernel(ConvArgs A) {
   typedef Vt<T> V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
