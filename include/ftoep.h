@@ -182,6 +182,16 @@ ftoep_status ftoep_profile_read(ftoep_plan p, int kclass, double* total_ms, int6
 ftoep_status ftoep_matvec_noalloc(const double* a, int64_t N, const double* x, double* y, int64_t nlines,
                                   int transpose, void* cuda_stream);
 
+/* Autotuner (no counterpart in the paper).  Times ftoep_solve on synthetic zero fields for
+ * each candidate time-block length fft_tile in {1024, 2048, 4096} (a plan per candidate,
+ * one warm-up and two timed solves with CUDA events on cuda_stream, device memory freed
+ * afterwards) and writes the fastest tuning to *out (other fields 0 = library choice).
+ * When the problems together exceed 2^28 unknowns the candidates are timed on a sample:
+ * problems taken evenly over the list sorted by M*N, up to that many unknowns.  Blocks
+ * until done.  Errors: FTOEP_EINVAL (bad problems, out NULL), FTOEP_ENOMEM, FTOEP_ECUDA;
+ * *out is left unchanged on error. */
+ftoep_status ftoep_autotune(const ftoep_problem* probs, int nprob, void* cuda_stream, ftoep_tuning* out);
+
 /* Wait for the plan's stream; returns FTOEP_ETIMEOUT if a device-side wait gave up,
  * FTOEP_ECUDA on an asynchronous CUDA error. */
 ftoep_status ftoep_sync(ftoep_plan p);

@@ -112,6 +112,17 @@ namespace ftoep {
 void set_global_error(const char* msg) { g_create_error = msg; }
 }  // namespace ftoep
 
+// A solve captured as a CUDA graph for one set of device pointers (see ftoep_solve).
+struct SolveGraph {
+  const void* f = nullptr;
+  const void* u = nullptr;
+  const void* u0 = nullptr;
+  const void* phi = nullptr;
+  int runs = 0;                   // direct runs seen before the capture
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches[6] = {0, 0, 0, 0, 0, 0};  // kernels per replay, per class
+};
+
 struct ftoep_plan_s {
   std::vector<Prob> probs;
   cudaStream_t stream = nullptr;  // caller's stream
@@ -134,6 +145,9 @@ struct ftoep_plan_s {
   int64_t prof_ops[kNumClasses] = {0, 0, 0, 0, 0, 0};
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
   std::vector<cudaEvent_t> evpool;
+  std::vector<SolveGraph> graphs;  // most recently used last
+  cudaStream_t gstream = nullptr;  // root stream the graphs are captured and replayed on
+  cudaEvent_t gev_in = nullptr, gev_out = nullptr;
 };
 
 namespace {
@@ -925,13 +939,12 @@ ftoep_status ftoep_weights(ftoep_plan pl, int iprob, double* a, double* dadgamma
   return FTOEP_OK;
 }
 
-ftoep_status ftoep_solve(ftoep_plan pl, const double* f, double* u, const double* u0, const double* phi) {
-  if (!pl) return fail(nullptr, FTOEP_EINVAL, "plan is NULL");
-  if (!f || !u) return fail(pl, FTOEP_EINVAL, "f and u must not be NULL");
-  const size_t fb = (size_t)pl->total_field * sizeof(double);
-  if ((const char*)f < (const char*)u + fb && (const char*)u < (const char*)f + fb)
-    return fail(pl, FTOEP_EINVAL, "f and u overlap");
-  const bool host = !is_device_ptr(f) || !is_device_ptr(u) || !is_device_ptr(u0) || !is_device_ptr(phi);
+}  // extern "C"
+
+namespace {
+
+// Every problem of the plan on its stream, forked from and joined back to the caller's.
+ftoep_status solve_all(ftoep_plan pl, const double* f, double* u, const double* u0, const double* phi, bool host) {
   TRY(fork_streams(pl));
   for (auto& pb : pl->probs) {
     Ws& w = pl->ws[pb.stream];
@@ -959,7 +972,111 @@ ftoep_status ftoep_solve(ftoep_plan pl, const double* f, double* u, const double
     }
   }
   TRY(join_streams(pl));
-  if (host) TRY(sync_plan(pl));
+  return FTOEP_OK;
+}
+
+constexpr size_t kMaxGraphs = 4;
+
+// Device-pointer solves are replayed from a CUDA graph: the first call with a pointer set
+// runs directly (and finishes every lazy set-up), the second is captured -- the fork to
+// the internal streams, all kernels of every problem and the join -- and launched, later
+// calls launch the captured graph.  Capture and replay run on a root stream of the plan,
+// ordered after the caller's stream by an event and joined back by another, so the
+// caller's stream may be the legacy default stream.  Not used with host buffers or while
+// the instrumentation is on.
+ftoep_status capture_solve(ftoep_plan pl, SolveGraph* g, const double* f, double* u, const double* u0,
+                           const double* phi) {
+  int64_t before[kNumClasses];
+  for (int c = 0; c < kNumClasses; ++c) before[c] = pl->launches[c];
+  // the root stream stands in for the caller's stream (and for a single problem's stream
+  // when that is the caller's) while the sequence is recorded
+  cudaStream_t caller = pl->stream;
+  std::vector<cudaStream_t> saved;
+  for (auto& w : pl->ws) {
+    saved.push_back(w.st);
+    if (w.st == caller) w.st = pl->gstream;
+  }
+  pl->stream = pl->gstream;
+  ftoep_status st = FTOEP_OK;
+  cudaGraph_t graph = nullptr;
+  cudaError_t ec = cudaStreamBeginCapture(pl->gstream, cudaStreamCaptureModeThreadLocal);
+  if (ec == cudaSuccess) {
+    st = solve_all(pl, f, u, u0, phi, false);
+    ec = cudaStreamEndCapture(pl->gstream, &graph);
+  }
+  pl->stream = caller;
+  for (size_t i = 0; i < pl->ws.size(); ++i) pl->ws[i].st = saved[i];
+  if (st != FTOEP_OK || ec != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return st != FTOEP_OK ? st : fail(pl, FTOEP_ECUDA, "capture of the solve: %s", cudaGetErrorString(ec));
+  }
+  cudaGraphExec_t exec = nullptr;
+  ec = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ec != cudaSuccess) return fail(pl, FTOEP_ECUDA, "graph instantiate: %s", cudaGetErrorString(ec));
+  g->exec = exec;
+  for (int c = 0; c < kNumClasses; ++c) {
+    g->launches[c] = pl->launches[c] - before[c];
+    pl->launches[c] = before[c];  // counted at launch below
+  }
+  return FTOEP_OK;
+}
+
+ftoep_status solve_device(ftoep_plan pl, const double* f, double* u, const double* u0, const double* phi) {
+  if (pl->prof_on) return solve_all(pl, f, u, u0, phi, false);
+  SolveGraph* g = nullptr;
+  for (size_t i = 0; i < pl->graphs.size(); ++i) {
+    SolveGraph& c = pl->graphs[i];
+    if (c.f == f && c.u == u && c.u0 == u0 && c.phi == phi) {
+      std::rotate(pl->graphs.begin() + i, pl->graphs.begin() + i + 1, pl->graphs.end());
+      g = &pl->graphs.back();
+      break;
+    }
+  }
+  if (!g) {
+    if (pl->graphs.size() == kMaxGraphs) {
+      if (pl->graphs.front().exec) cudaGraphExecDestroy(pl->graphs.front().exec);
+      pl->graphs.erase(pl->graphs.begin());
+    }
+    SolveGraph n;
+    n.f = f;
+    n.u = u;
+    n.u0 = u0;
+    n.phi = phi;
+    pl->graphs.push_back(n);
+    g = &pl->graphs.back();
+  }
+  if (!g->exec && g->runs++ == 0) return solve_all(pl, f, u, u0, phi, false);
+  if (!pl->gstream) {
+    CK(cudaStreamCreateWithFlags(&pl->gstream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&pl->gev_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&pl->gev_out, cudaEventDisableTiming));
+  }
+  if (!g->exec) TRY(capture_solve(pl, g, f, u, u0, phi));
+  CK(cudaEventRecord(pl->gev_in, pl->stream));
+  CK(cudaStreamWaitEvent(pl->gstream, pl->gev_in, 0));
+  CK(cudaGraphLaunch(g->exec, pl->gstream));
+  CK(cudaEventRecord(pl->gev_out, pl->gstream));
+  CK(cudaStreamWaitEvent(pl->stream, pl->gev_out, 0));
+  for (int c = 0; c < kNumClasses; ++c) pl->launches[c] += g->launches[c];
+  return FTOEP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ftoep_status ftoep_solve(ftoep_plan pl, const double* f, double* u, const double* u0, const double* phi) {
+  if (!pl) return fail(nullptr, FTOEP_EINVAL, "plan is NULL");
+  if (!f || !u) return fail(pl, FTOEP_EINVAL, "f and u must not be NULL");
+  const size_t fb = (size_t)pl->total_field * sizeof(double);
+  if ((const char*)f < (const char*)u + fb && (const char*)u < (const char*)f + fb)
+    return fail(pl, FTOEP_EINVAL, "f and u overlap");
+  const bool host = !is_device_ptr(f) || !is_device_ptr(u) || !is_device_ptr(u0) || !is_device_ptr(phi);
+  if (!host) return solve_device(pl, f, u, u0, phi);
+  TRY(solve_all(pl, f, u, u0, phi, true));
+  TRY(sync_plan(pl));
   return FTOEP_OK;
 }
 
@@ -1101,6 +1218,93 @@ ftoep_status ftoep_profile_read(ftoep_plan pl, int kclass, double* total_ms, int
   return FTOEP_OK;
 }
 
+ftoep_status ftoep_autotune(const ftoep_problem* probs, int nprob, void* cuda_stream, ftoep_tuning* out) {
+  g_create_error.clear();
+  if (!out || !probs || nprob < 1) return fail(nullptr, FTOEP_EINVAL, "autotune: need problems and out");
+  for (int i = 0; i < nprob; ++i) TRY(validate(probs[i], i, nullptr));
+  // sample: evenly over the problems sorted by size, up to 2^28 unknowns in total
+  const int64_t cap = (int64_t)1 << 28;
+  std::vector<int> order(nprob);
+  for (int i = 0; i < nprob; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(),
+            [&](int a, int b) { return probs[a].M * probs[a].N < probs[b].M * probs[b].N; });
+  int64_t total = 0;
+  for (int i = 0; i < nprob; ++i) total += probs[i].M * probs[i].N;
+  std::vector<ftoep_problem> sample;
+  if (total <= cap) {
+    sample.assign(probs, probs + nprob);
+  } else {
+    int64_t used = 0;
+    for (int k = 1; k <= nprob; k *= 2) {  // strides nprob, nprob/2, ... until the cap
+      sample.clear();
+      used = 0;
+      const int stride = std::max(1, nprob / k);
+      for (int i = stride / 2; i < nprob; i += stride) {
+        const ftoep_problem& q = probs[order[i]];
+        if (used + q.M * q.N > cap) continue;
+        sample.push_back(q);
+        used += q.M * q.N;
+      }
+      if ((int)sample.size() >= std::min(nprob, 16)) break;
+    }
+    if (sample.empty()) {  // every problem alone exceeds the cap: the smallest one
+      sample.push_back(probs[order[0]]);
+    }
+  }
+  int64_t units = 0;
+  for (auto& q : sample) units += q.M * q.N;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  double *f = nullptr, *u = nullptr;
+  if (cudaMalloc(&f, (size_t)units * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&u, (size_t)units * sizeof(double)) != cudaSuccess) {
+    cudaFree(f);
+    cudaGetLastError();
+    return fail(nullptr, FTOEP_ENOMEM, "autotune: no memory for %lld sample unknowns", (long long)units);
+  }
+  cudaMemsetAsync(f, 0, (size_t)units * sizeof(double), st);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int cand[] = {1024, 2048, 4096};
+  float best_ms = -1.0f;
+  int best = 0;
+  ftoep_status status = FTOEP_OK;
+  for (int c : cand) {
+    ftoep_tuning t{};
+    t.fft_tile = c;
+    ftoep_plan pl = nullptr;
+    status = ftoep_create(&pl, sample.data(), (int)sample.size(), &t, cuda_stream);
+    if (status != FTOEP_OK) break;
+    status = ftoep_solve(pl, f, u, nullptr, nullptr);
+    if (status == FTOEP_OK) cudaEventRecord(e0, st);
+    for (int r = 0; r < 2 && status == FTOEP_OK; ++r) status = ftoep_solve(pl, f, u, nullptr, nullptr);
+    if (status == FTOEP_OK) {
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (best_ms < 0.0f || ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    } else {
+      g_create_error = pl->err;
+    }
+    ftoep_destroy(pl);
+    if (status != FTOEP_OK) break;
+  }
+  cudaStreamSynchronize(st);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(f);
+  cudaFree(u);
+  if (status != FTOEP_OK) return status;
+  ftoep_tuning r{};
+  r.fft_tile = best;
+  *out = r;
+  return FTOEP_OK;
+}
+
 ftoep_status ftoep_sync(ftoep_plan pl) {
   if (!pl) return fail(nullptr, FTOEP_EINVAL, "plan is NULL");
   return sync_plan(pl);
@@ -1133,6 +1337,12 @@ ftoep_status ftoep_destroy(ftoep_plan pl) {
     if (w.own && w.st) cudaStreamDestroy(w.st);
   }
   if (pl->fork) cudaEventDestroy(pl->fork);
+  if (pl->gstream) cudaStreamSynchronize(pl->gstream);
+  for (auto& g : pl->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (pl->gstream) cudaStreamDestroy(pl->gstream);
+  if (pl->gev_in) cudaEventDestroy(pl->gev_in);
+  if (pl->gev_out) cudaEventDestroy(pl->gev_out);
   delete pl;
   return FTOEP_OK;
 }

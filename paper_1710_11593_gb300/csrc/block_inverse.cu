@@ -27,9 +27,7 @@ constexpr int kThreads = 256;
 template <typename T>
 using Vt = typename VecOf<T>::type;
 
-inline void set_smem(const void* fn, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
+inline void set_smem(const void* fn, size_t bytes) { set_smem_once(fn, bytes); }
 
 // Storage position of the partner (n - k mod n) of the frequency stored at `pos`
 // (bit-reversed storage of a decimation-in-frequency FFT of length n = 2^logn).

@@ -165,8 +165,7 @@ size_t smem_bytes(int B, int Sf) {
 template <typename T>
 void launch(const BlockArgs& a, cudaStream_t st) {
   const size_t smem = smem_bytes<T>(a.B, a.Sf);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute((const void*)block_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  set_smem_once((const void*)block_solve_kernel<T>, smem);
   block_solve_kernel<T><<<(unsigned)a.npairs, kThreads, smem, st>>>(a);
 }
 

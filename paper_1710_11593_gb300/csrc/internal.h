@@ -204,5 +204,7 @@ int launch_block_inverse(Prec prec, const BlockInvArgs& a, cudaStream_t st);
 
 // Largest shared-memory FFT length of each precision.
 int nsmem_for(Prec prec);
+// Opt a kernel in to `bytes` of dynamic shared memory (once per kernel and size).
+void set_smem_once(const void* fn, size_t bytes);
 
 }  // namespace ftoep

@@ -6,6 +6,9 @@
 // mode (or line) 2p in .x and 2p+1 in .y.  Convolution with a real kernel acts on the
 // two components independently, so one complex FFT serves two real problems.
 #include <cstdio>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include <cooperative_groups.h>
 
@@ -29,12 +32,7 @@ template <> struct EngineTraitsHost<float> { static constexpr int RB = 4; };
 template <> struct EngineTraitsHost<double> { static constexpr int RB = 3; };
 template <> struct EngineTraitsHost<FF> { static constexpr int RB = 3; };
 
-inline void set_smem(const void* fn, size_t bytes) {
-  if (bytes > 48 * 1024) {
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
-  }
-}
+inline void set_smem(const void* fn, size_t bytes) { set_smem_once(fn, bytes); }
 
 // Conversions between double pairs and the storage types.
 template <typename T> __device__ __forceinline__ typename VecOf<T>::type make_pair_of(double a, double b);
@@ -1123,6 +1121,34 @@ void conv_launch(const ConvArgs& a, cudaStream_t st) {
 }
 
 }  // namespace
+
+// Dynamic shared memory above 48 KB needs an opt-in per kernel; it is set once per
+// kernel and size (a host-side cache), so solves -- and captured solves -- issue stream
+// work only.
+void set_smem_once(const void* fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return;
+  static std::mutex mu;
+  struct Entry {
+    const void* fn;
+    int dev;
+    size_t bytes;
+  };
+  static std::vector<Entry> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto& d : done) {
+    if (d.fn == fn && d.dev == dev) {
+      if (d.bytes >= bytes) return;
+      d.bytes = bytes;
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      return;
+    }
+  }
+  done.push_back({fn, dev, bytes});
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+}
 
 int nsmem_for(Prec prec) { return prec == P32 ? 8192 : 4096; }
 int bluestein_max_K(Prec prec) { return prec == P64 ? 2048 : 4096; }

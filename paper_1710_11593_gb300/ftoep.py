@@ -71,6 +71,7 @@ def load(path: Optional[str] = None):
     lib.ftoep_matvec.argtypes = [vp, ci, dp, dp, i64, ci]
     lib.ftoep_adjoint.argtypes = [vp, dp, dp, dp, dp]
     lib.ftoep_profile.argtypes = [vp, ci]
+    lib.ftoep_autotune.argtypes = [ctypes.POINTER(ftoep_problem), ci, vp, ctypes.POINTER(ftoep_tuning)]
     lib.ftoep_profile_read.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                        ctypes.POINTER(i64)]
     lib.ftoep_sync.argtypes = [vp]
@@ -202,6 +203,19 @@ def ftoep_sync(plan: int):
 
 def ftoep_destroy(plan: int):
     load().ftoep_destroy(plan)
+
+
+def ftoep_autotune(problems: Sequence[ProblemSpec], stream: Optional[int] = None) -> dict:
+    """Time the candidate block lengths on the problems (C ABI ftoep_autotune) and return the
+    fastest tuning as a dict for Plan(..., tuning=...)."""
+    lib = load()
+    arr = (ftoep_problem * len(problems))(*[p.to_c() for p in problems])
+    out = ftoep_tuning()
+    st = current_stream_handle() if stream is None else stream
+    rc = lib.ftoep_autotune(arr, len(problems), ctypes.c_void_p(st), ctypes.byref(out))
+    _check(rc, None)
+    return {"leaf": out.leaf, "fft_tile": out.fft_tile, "gemm_max_level": out.gemm_max_level,
+            "modes_per_cta": out.modes_per_cta}
 
 
 class Plan:
