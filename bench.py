@@ -172,6 +172,43 @@ def roofline_of(flops, byts, prof, steps, precision):
     return out
 
 
+class Ranks:
+    """Rank context of one bench process (one process per GPU, launched by torchrun).
+    The workload is a replica per rank (no data-path collective): the value is the units of
+    all ranks over the slowest rank's time (weak scaling)."""
+
+    def __init__(self, backend="nccl", device="cuda"):
+        import torch.distributed as dist
+        self.dist = dist
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.device = device
+        if self.world > 1 and not dist.is_initialized():
+            dist.init_process_group(backend)
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def max(self, x):
+        """Largest x over the ranks (every rank gets it)."""
+        if self.world == 1:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def value(self, units_per_rank, ms_max):
+        """Whole-job throughput: units of all ranks / slowest rank's time."""
+        return self.world * units_per_rank / (ms_max * 1e-3)
+
+    def close(self):
+        if self.world > 1 and self.dist.is_initialized():
+            self.dist.destroy_process_group()
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -291,15 +328,11 @@ def run_reference(args):
 def run_batched(args):
     """Config-4 workload: all problems in one plan (internal streams, longest first)."""
     import torch
-    import torch.distributed as dist
     from paper_1710_11593_gb300 import ftoep, workloads as wl
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rk = Ranks()
+    world, rank, local = rk.world, rk.rank, rk.local
     torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
     ftoep.load()
     probs, wname = workload("batched", args.nprob)
     precision = args.precision or "mixed"
@@ -315,9 +348,7 @@ def run_batched(args):
     u = torch.empty_like(f)
     plan = ftoep.Plan(specs)
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
+    barrier = rk.barrier
 
     for _ in range(args.warmup):
         plan.solve(f, u)
@@ -343,11 +374,8 @@ def run_batched(args):
     plan.solve(f, u)
     prof = plan.profile_read()
     plan.profile(False)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * units / (ms * 1e-3)
+    ms = rk.max(ms)
+    value = rk.value(units, ms)
     busy = sum(x[0] for x in prof.values())
     shares = {k: v[0] / max(1e-9, busy) for k, v in prof.items()}
     fl, by = {}, {}
@@ -424,22 +452,17 @@ def run_batched(args):
                "roofline": roof, "kernel_time_share": shares, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                "gpu_launches": launches, "compare": compare}
         print(json.dumps(out))
-    if world > 1:
-        dist.destroy_process_group()
+    rk.close()
     return 0
 
 
 def run_ours(args):
     import torch
-    import torch.distributed as dist
     from paper_1710_11593_gb300 import ftoep, workloads as wl
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rk = Ranks()
+    world, rank, local = rk.world, rk.rank, rk.local
     torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
     ftoep.load()
 
     p, wname = workload(args.workload, M=args.M, N=args.N)
@@ -450,9 +473,7 @@ def run_ours(args):
     u = torch.empty_like(f)
     plan = ftoep.Plan([spec])
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
+    barrier = rk.barrier
 
     for _ in range(args.warmup):
         plan.solve(f, u)
@@ -478,12 +499,9 @@ def run_ours(args):
     plan.solve(f, u)
     prof = plan.profile_read()
     plan.profile(False)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = rk.max(ms)
     units = p.M * p.N
-    value = world * units / (ms * 1e-3)
+    value = rk.value(units, ms)
     tot_ms = sum(x[0] for x in prof.values())
     shares = {k: v[0] / max(1e-9, tot_ms) for k, v in prof.items()}
 
@@ -502,10 +520,7 @@ def run_ours(args):
         plan.solve(fh, uh)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / esteps
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = rk.max(e2e_s)
     e2e = {"value": world * units / e2e_s, "unit": "unknowns/s", "h2d_bytes_per_step": fh.numel() * 8,
            "d2h_bytes_per_step": uh.numel() * 8}
     del fh, uh
@@ -562,8 +577,7 @@ def run_ours(args):
                "clocks": clk, "gpu_launches": launches, "compare": compare,
                "max_abs_err_vs_exact": disc}
         print(json.dumps(out))
-    if world > 1:
-        dist.destroy_process_group()
+    rk.close()
     return 0
 
 
