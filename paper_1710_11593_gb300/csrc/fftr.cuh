@@ -6,8 +6,8 @@
 // (bit-reversed in, natural out, unnormalised) -- computed in passes that each merge
 // r = log2(R) radix-2 stages: a thread loads R elements at stride m = g/R of one group of
 // size g, runs the r stages in registers, and stores them back in place.  One pass of
-// radix 16 replaces four shared-memory round trips and four barriers of the stage-by-stage
-// form; the in-place order of a merged pass is exactly that of its stages, so outputs,
+// radix 8 replaces three shared-memory round trips and three barriers of the stage-by-stage
+// form (the engine supports radix up to 16); the in-place order of a merged pass is exactly that of its stages, so outputs,
 // spectra and partner indices keep the bit-reversed convention.
 //
 // Twiddles: stage k of a pass (sub-group size G = g/2^k) multiplies element (i + j m) by
@@ -17,10 +17,13 @@
 // W_G^i is 1 and no table is read.
 //
 // Shared-memory layout: `cnt` transforms of length n = 2^logn back to back; element e of
-// transform t sits at  t*n + (e ^ (((e >> S) ^ brev(t)) & xm)),  S = log2(elements per
-// 128-byte wavefront), xm = min(n, 2^S) - 1, brev over log2(xm+1) bits.  The XOR is a
-// permutation inside each 2^S-element chunk; it makes every pass of the schedule below and
-// the column-wise (one lane per transform) loads and stores free of bank conflicts.
+// transform t sits at  t*n + (e ^ (((e >> RB) ^ brev(t)) & xm)),  RB = log2(pass radix),
+// xm = min(n, 2^S) - 1 with S = log2(elements per 128-byte wavefront), brev over
+// log2(xm+1) bits.  The XOR only changes the low S bits (a permutation inside each
+// 2^S-element chunk, invertible because its source bits start at RB); with the source
+// shifted by the pass radix every pass of the schedule below, the column-wise (one lane per
+// transform) loads and stores and natural-order access are free of bank conflicts (checked
+// exhaustively with a bank model for 8- and 16-byte elements at radix 8 and 16).
 #pragma once
 
 #include "fft.cuh"
@@ -42,7 +45,10 @@ __device__ __forceinline__ void static_for(F&& f) {
 template <typename V> struct EngineTraits;
 template <> struct EngineTraits<float2> {
   static constexpr int S = 4;   // 16 elements of 8 bytes per wavefront
-  static constexpr int RB = 4;  // radix-16 passes
+  // radix-8 passes: radix 16 needs one pass fewer but ~40 more registers per thread; the
+  // float kernels are latency-bound, and the extra resident warps of radix 8 were worth more
+  // (measured on the batched solve: 3.04 s against 3.11 s per step)
+  static constexpr int RB = 3;
 };
 template <> struct EngineTraits<double2> {
   static constexpr int S = 3;
@@ -71,9 +77,9 @@ __device__ __forceinline__ SmLayout sm_layout(int logn) {
 
 template <typename V>
 __device__ __forceinline__ int sm_pos(const SmLayout& L, int t, int e) {
-  constexpr int S = EngineTraits<V>::S;
+  constexpr int RB = EngineTraits<V>::RB;
   const int bt = L.lb ? (int)(__brev((unsigned)(t & L.xm)) >> (32 - L.lb)) : 0;
-  return (t << L.logn) + (e ^ (((e >> S) ^ bt) & L.xm));
+  return (t << L.logn) + (e ^ (((e >> RB) ^ bt) & L.xm));
 }
 
 // ------------------------------------------------------------------ constant twiddles

@@ -28,7 +28,7 @@ using Vt = typename VecOf<T>::type;
 
 // Host-side copy of the pass radix of each arithmetic type (fftr.cuh EngineTraits).
 template <typename T> struct EngineTraitsHost;
-template <> struct EngineTraitsHost<float> { static constexpr int RB = 4; };
+template <> struct EngineTraitsHost<float> { static constexpr int RB = 3; };
 template <> struct EngineTraitsHost<double> { static constexpr int RB = 3; };
 template <> struct EngineTraitsHost<FF> { static constexpr int RB = 3; };
 
