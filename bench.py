@@ -106,9 +106,10 @@ def work_model(p, precision):
     nsolve = 1 if precision == "fp64" else 2
     zb = 16 if precision == "fp64" else 8  # bytes per complex of the solve
     # block solve = causal convolution with the block inverse: FFT and inverse FFT of length
-    # 2B per pair plus two complex products per point; reads z, writes z, reads C1, C2
+    # 2B per pair plus two complex products per point; reads z, writes z, reads the
+    # Hermitian-packed C1/C2 array (2B complex per pair)
     block = nsolve * nblk * (2 * P * B) * (10 * math.log2(2 * B) + 14)
-    block_b = nsolve * nblk * P * (2 * B * zb + 2 * (2 * B) * zb)
+    block_b = nsolve * nblk * P * (2 * B * zb + (2 * B) * zb)
     conv_smem = conv_4 = 0.0
     smem_b = four_b = 0.0
     nsmem = 4096 if precision == "fp64" else 8192

@@ -81,8 +81,10 @@ typedef enum {
 
 typedef enum {
   FTOEP_FP64 = 0,  /* all arithmetic in double precision                               */
-  FTOEP_MIXED = 1  /* float convolutions and transforms, double leaf substitutions and
-                      a double-precision residual; one residual-correction sweep         */
+  FTOEP_MIXED = 1  /* float solve (sine transforms, block inverses, convolutions; the
+                      running sums of the all-ones part in double), then one correction
+                      sweep: residual with a float-float (~48-bit) Toeplitz product and the
+                      spatial stencil in double, correction solved in float and added     */
 } ftoep_precision;
 
 /* One problem.  T: final time (> 0).  L: length of the space interval (> 0, ignored for
@@ -98,12 +100,15 @@ typedef struct {
   int64_t N, M;
 } ftoep_problem;
 
-/* Optional tuning (NULL or 0 fields = library choice).
- * leaf: size of the dense forward-substitution leaves (power of two, 1..16).
- * fft_tile: largest time block solved inside one thread block (power of two).
- * gemm_max_level: largest half-split level handled by direct (dense) block products
- *   instead of FFTs.
- * modes_per_cta: reserved (mode pairs per thread block of the sine transform). */
+/* Optional tuning (NULL or 0 fields = library choice; ftoep_autotune picks fft_tile).
+ * fft_tile: the time block length B (power of two, 16..4096; default 4096, capped at N
+ *   rounded up to a power of two).  Every block of B levels is solved by a causal
+ *   convolution with the per-mode inverse of the block operator (one FFT of length 2B);
+ *   the half-split updates between blocks are circulant convolutions.
+ * leaf, gemm_max_level: shape the substitution that builds the per-mode block inverses
+ *   once at plan creation (leaf: dense forward-substitution size, power of two <= 16;
+ *   levels below gemm_max_level use dense products instead of FFTs).
+ * modes_per_cta: reserved. */
 typedef struct {
   int leaf, fft_tile, gemm_max_level, modes_per_cta;
 } ftoep_tuning;
@@ -125,7 +130,12 @@ ftoep_status ftoep_weights(ftoep_plan p, int iprob, double* a, double* dadgamma)
 /* Solve every problem of the plan: u = A^-1 (f + initial-data terms), where A is the
  * space-time operator of the scheme (Eq. 20 and its hyperbolic analogue).
  * f, u: concatenated fields (see top); u0, phi: concatenated length-M vectors or NULL
- * (zero).  phi is only used by hyperbolic problems.  f and u must not overlap. */
+ * (zero).  phi is only used by hyperbolic problems.  f and u must not overlap.
+ * Device buffers: the second call with the same (f, u, u0, phi) pointers captures the
+ * whole solve (all problems, internal streams) as one CUDA graph of the plan and later
+ * calls replay it -- the buffers' contents may change between calls, the pointers name
+ * the graph (the plan keeps the four most recent).  Host buffers and calls while
+ * ftoep_profile is on run the kernels directly. */
 ftoep_status ftoep_solve(ftoep_plan p, const double* f, double* u, const double* u0, const double* phi);
 
 /* y = T x (transpose = 0) or y = T^T x (transpose = 1) for nlines independent lines of
