@@ -175,3 +175,31 @@ def test_adjoint_and_gamma_gradient(ft, oracle):
         dldf, dg = plan.adjoint(torch.from_numpy(dLdu).cuda(), uu)
     assert _rel(dldf.cpu().numpy(), lam_ref) < 1e-12
     assert abs(dg[0] - grad_ref) <= 1e-9 * abs(grad_ref)
+
+
+@pytest.mark.parametrize("kind,gamma,M,N,prec", [
+    (0, 0.5, 1, 1, 0),      # one step, one point (M+1 = 2: the smallest sine transform, a self pair)
+    (1, 1.5, 1, 2, 0),
+    (0, 0.7, 3, 5, 1),      # mixed, M+1 = 4
+    (1, 1.3, 1, 17, 1),
+    (0, 0.6, 7, 16, 0),     # N exactly one minimal block
+    (1, 1.7, 2, 1, 0),      # chirp-z transform with a single step
+])
+def test_degenerate_sizes(ft, oracle, kind, gamma, M, N, prec):
+    f = wl.random_field((M, N), seed=17 * M + N)
+    ref = oracle.march(kind, 1, gamma, f)
+    u = _solve_gpu(ft, kind, gamma, f, precision=prec)
+    assert _rel(u, ref) < (1e-12 if prec == 0 else 1e-6)
+
+
+@pytest.mark.parametrize("kind,gamma,M,N,prec", [
+    (0, 0.7, 8191, 40, 1),  # largest power-of-two M+1, mixed
+    (1, 1.4, 4095, 40, 0),  # largest power-of-two M+1, double
+    (0, 0.6, 4094, 30, 1),  # largest chirp-z M+1 = 4095, mixed
+    (1, 1.6, 2046, 30, 0),  # largest chirp-z M+1 = 2047, double
+])
+def test_largest_sine_transforms(ft, oracle, kind, gamma, M, N, prec):
+    f = wl.random_field((M, N), seed=M + N)
+    ref = oracle.march(kind, 1, gamma, f)
+    u = _solve_gpu(ft, kind, gamma, f, precision=prec)
+    assert _rel(u, ref) < (1e-12 if prec == 0 else 1e-6)

@@ -1,0 +1,65 @@
+"""Argument checks of the C ABI (host logic, no GPU needed): every invalid problem or
+tuning is rejected by ftoep_create / ftoep_autotune with FTOEP_EINVAL, sizes beyond the
+sine-transform and step limits with FTOEP_EUNSUPPORTED, before any device work."""
+import pytest
+
+from paper_1710_11593_gb300 import ftoep
+
+
+def _spec(**kw):
+    d = dict(kind=0, gamma=0.5, N=64, M=7, space=1, precision=0)
+    d.update(kw)
+    return ftoep.ProblemSpec(d["kind"], d["gamma"], d["N"], d["M"], d["space"], d["precision"],
+                             **{k: v for k, v in d.items() if k in ("T", "L", "lam")})
+
+
+@pytest.mark.parametrize("kw,status,msg", [
+    (dict(kind=0, gamma=1.0), ftoep.FTOEP_EINVAL, "not in (0,1)"),
+    (dict(kind=0, gamma=0.0), ftoep.FTOEP_EINVAL, "not in (0,1)"),
+    (dict(kind=1, gamma=0.5), ftoep.FTOEP_EINVAL, "not in (1,2)"),
+    (dict(kind=1, gamma=2.0), ftoep.FTOEP_EINVAL, "not in (1,2)"),
+    (dict(kind=2, gamma=0.5), ftoep.FTOEP_EINVAL, "unknown kind"),
+    (dict(space=2), ftoep.FTOEP_EINVAL, "unknown space"),
+    (dict(precision=3), ftoep.FTOEP_EINVAL, "unknown precision"),
+    (dict(N=0), ftoep.FTOEP_EINVAL, "must be >= 1"),
+    (dict(M=0), ftoep.FTOEP_EINVAL, "must be >= 1"),
+    (dict(T=0.0), ftoep.FTOEP_EINVAL, "T must be > 0"),
+    (dict(T=float("nan")), ftoep.FTOEP_EINVAL, "T must be > 0"),
+    (dict(L=-1.0), ftoep.FTOEP_EINVAL, "L must be > 0"),
+    (dict(space=0, lam=-1.0), ftoep.FTOEP_EINVAL, "lambda must be >= 0"),
+    (dict(N=(1 << 22) + 1), ftoep.FTOEP_EUNSUPPORTED, "N > 2^22"),
+    (dict(M=8192, precision=1), ftoep.FTOEP_EUNSUPPORTED, "M+1 = 8193"),   # above the power-of-two mixed limit
+    (dict(M=4096, precision=0), ftoep.FTOEP_EUNSUPPORTED, "M+1 = 4097"),   # chirp-z double limit 2048
+    (dict(M=4200, precision=1), ftoep.FTOEP_EUNSUPPORTED, "M+1 = 4201"),   # chirp-z mixed limit 4096
+])
+def test_invalid_problem_rejected(kw, status, msg):
+    with pytest.raises(ftoep.FtoepError) as ei:
+        ftoep.ftoep_create([_spec(**kw)], None, 0)
+    assert ei.value.status == status
+    assert msg in str(ei.value)
+
+
+@pytest.mark.parametrize("tune,msg", [
+    ({"leaf": 3}, "leaf"),
+    ({"leaf": 32}, "leaf"),
+    ({"fft_tile": 8}, "fft_tile"),
+    ({"fft_tile": 8192}, "fft_tile"),
+    ({"fft_tile": 100}, "fft_tile"),
+    ({"gemm_max_level": 4096}, "gemm_max_level"),
+])
+def test_invalid_tuning_rejected(tune, msg):
+    with pytest.raises(ftoep.FtoepError) as ei:
+        ftoep.ftoep_create([_spec()], tune, 0)
+    assert ei.value.status == ftoep.FTOEP_EINVAL and msg in str(ei.value)
+
+
+def test_invalid_problem_in_a_batch_names_its_index():
+    with pytest.raises(ftoep.FtoepError) as ei:
+        ftoep.ftoep_create([_spec(), _spec(), _spec(kind=1, gamma=0.7)], None, 0)
+    assert ei.value.status == ftoep.FTOEP_EINVAL and "problem 2" in str(ei.value)
+
+
+def test_autotune_validates_before_timing():
+    with pytest.raises(ftoep.FtoepError) as ei:
+        ftoep.ftoep_autotune([_spec(gamma=1.5)], stream=0)
+    assert ei.value.status == ftoep.FTOEP_EINVAL
