@@ -3,14 +3,17 @@
 //
 // ftoep_solve, per problem (difference form, see solve_problem):
 //   1. right-hand side + sine transform along space      -> mode pairs z[P][Np]
-//   2. per time block of length B: in-block half-split solve; then the one cross-block
-//      update that becomes due (level s = B * 2^ctz(block+1)) as a circulant convolution
+//   2. per time block of length B: the block solve as a causal convolution with the
+//      per-mode block inverse; then the one cross-block update that becomes due (level
+//      s = B * 2^ctz(block+1)) as a circulant convolution
 //   3. inverse sine transform, u = u0 + tau * cumsum(v)
-//   mixed precision: 1-3 in float (double leaves and running sums), then the residual of
-//   the original form in double, 1-3 on it, u += correction.
+//   mixed precision: 1-3 in float (running sums of the all-ones part in double), then the
+//   residual of the same difference-form rows (float-float Toeplitz product, spatial
+//   stencil in double), 1-3 on it, u += correction.
 // A plan with several problems runs them on up to kMaxStreams internal streams (longest
 // first, each onto the least-loaded stream), each stream with its own workspace; the
-// caller's stream forks to them and joins them again through events.
+// caller's stream forks to them and joins them again through events.  Device-pointer
+// solves are captured once as a CUDA graph and replayed (solve_device).
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>

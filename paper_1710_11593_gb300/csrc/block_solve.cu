@@ -11,6 +11,10 @@
 // precision; levels s < Sf are direct products (s^2 multiply-adds per component);
 // levels s >= Sf are cyclic convolutions of length 2s in shared memory, exact for this
 // block because the needed entries a_1 .. a_{2s-1} never wrap around.
+//
+// Used once per plan: applied to a unit impulse it yields the first B entries h_m of
+// every mode's inverse block operator, from which block_inverse.cu builds the spectra
+// of the block solve that the timed path uses.
 #include "fft.cuh"
 #include "internal.h"
 

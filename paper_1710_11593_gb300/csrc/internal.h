@@ -179,7 +179,7 @@ size_t block_solve_smem(Prec prec, int B, int Sf);
 // inverse first columns h (first B entries of T_m^-1 e_1), Hermitian-packed into one
 // length-2B array c1 (C1 at the lower of two partner positions, C2 at the other; c2 unused).
 struct InvSpecArgs {
-  const double2* h;   // [npairs][ldh]: h of mode 2p in .x, of mode 2p+1 in .y
+  const double2* h;   // [npairs][ldh]: h of the pair's first mode in .x, of its second mode in .y
   int64_t ldh;
   int64_t npairs;
   int B, logB;
