@@ -149,3 +149,53 @@ def test_config3_wave_mixed_full(ft, oracle):
     assert np.max(np.abs(up - ref)) < 1e-6 * umax
     for m in (2, 4000):
         assert np.max(np.abs(_project_gpu(u, m))) < 1e-6 * umax
+
+
+def _all_modes_gpu(u):
+    """Every sine mode of the field at once: the orthonormal DST-I matrix (built in double
+    from its definition, not by the library) times u, on the GPU -- test-side only."""
+    import torch
+    M = u.shape[0]
+    j = torch.arange(1, M + 1, dtype=torch.int64, device=u.device)
+    arg = torch.remainder(j[:, None] * j[None, :], 2 * (M + 1)).to(torch.float64) * (np.pi / (M + 1))
+    return (np.sqrt(2.0 / (M + 1)) * torch.sin(arg)) @ u
+
+
+@pytest.mark.parametrize("prec,forced,tol", [(0, (1,), 1e-12), (1, (1,), 1e-7)])
+def test_config2_every_unforced_mode_vanishes(ft, prec, forced, tol):
+    """The config-2 source is sin(pi x_j) times a function of time, the m = 1 eigenvector of
+    the discrete Laplacian, so the exact discrete solution has no other mode: all 1022 of
+    them must stay at the path's rounding level against the forced one."""
+    p = wl.config_diffusion()
+    u = _gpu_solve(ft, p, prec)
+    modal = _all_modes_gpu(u)
+    scale = float(modal[0].abs().max())
+    keep = [m - 1 for m in forced]
+    mask = np.ones(p.M, dtype=bool)
+    mask[keep] = False
+    import torch
+    other = modal[torch.from_numpy(mask).to(modal.device)]
+    assert float(other.abs().max()) < tol * scale
+
+
+def test_config3_every_unforced_mode_vanishes(ft):
+    """Config 3 forces modes 1 and 3 only; the other 4093 modes of the mixed solve must stay
+    at its rounding level against them."""
+    import torch
+    p = wl.config_wave()
+    u = _gpu_solve(ft, p, ft.MIXED)
+    scale = float(u.abs().max())
+    worst = 0.0
+    for r0 in range(0, p.M, 512):  # row blocks of the projection keep the temporaries small
+        M = p.M
+        j = torch.arange(1, M + 1, dtype=torch.int64, device=u.device)
+        rows = torch.arange(r0 + 1, min(M, r0 + 512) + 1, dtype=torch.int64, device=u.device)
+        arg = torch.remainder(rows[:, None] * j[None, :], 2 * (M + 1)).to(torch.float64) * (np.pi / (M + 1))
+        S = np.sqrt(2.0 / (M + 1)) * torch.sin(arg)
+        modal = S @ u
+        for m in (1, 3):
+            if r0 < m <= r0 + 512:
+                modal[m - 1 - r0] = 0.0
+        worst = max(worst, float(modal.abs().max()))
+        del modal, S
+    assert worst < 1e-7 * scale
