@@ -47,6 +47,10 @@
  * exceeds its bound sets a flag in the plan; the next call that synchronises
  * (ftoep_sync, ftoep_adjoint with a host gamma-gradient, any call with host buffers)
  * returns FTOEP_ETIMEOUT.  ftoep_last_error gives a message for the last failure.
+ *
+ * Threads: a plan's workspace, counters and captured graphs are shared by its calls, so
+ * calls on one plan must not overlap in time from different host threads; different
+ * plans are independent.
  */
 #ifndef FTOEP_H
 #define FTOEP_H
