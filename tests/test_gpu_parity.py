@@ -203,3 +203,24 @@ def test_largest_sine_transforms(ft, oracle, kind, gamma, M, N, prec):
     ref = oracle.march(kind, 1, gamma, f)
     u = _solve_gpu(ft, kind, gamma, f, precision=prec)
     assert _rel(u, ref) < (1e-12 if prec == 0 else 1e-6)
+
+
+@pytest.mark.parametrize("kind,gamma,prec,tol", [(0, 0.6, 0, 1e-13), (1, 1.5, 0, 1e-13),
+                                                 (0, 0.6, 1, 1e-9), (1, 1.5, 1, 1e-9)])
+def test_longest_line_backward_error(ft, kind, gamma, prec, tol):
+    """N = 2^22 (the step limit), two lines without space: the oracle cannot march that far,
+    so the check is the backward error of the solve, a property at any size:
+    |T u + lambda u - f| <= tol (|a|_1 |u| + lambda |u| + |f|) with T u from the library's
+    double circulant-embedded product and a from ftoep_weights."""
+    import torch
+    N, M, lam = 1 << 22, 2, 1.0
+    f = torch.from_numpy(wl.random_field((M, N), seed=kind * 10 + prec)).cuda()
+    with ft.Plan([ft.ProblemSpec(kind, gamma, N, M, 0, prec, lam=lam)]) as plan:
+        u = plan.solve(f)
+        tu = plan.matvec(0, u)
+        a = plan.weights(0)
+        plan.sync()
+    r = tu + lam * u - f
+    umax = float(u.abs().max())
+    scale = float(np.abs(a).sum()) * umax + lam * umax + float(f.abs().max())
+    assert float(r.abs().max()) <= tol * scale
