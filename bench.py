@@ -412,7 +412,10 @@ def run_batched(args):
         while k > 1 and 2 * 8 * e_units > budget:
             k -= 1
             e_units -= probs[k].M * probs[k].N
-        eplan = plan if k == len(probs) else ftoep.Plan(specs[:k])
+        if k < len(probs):  # free the full plan's workspace before the sample's
+            plan.close()
+            plan = None
+        eplan = plan if plan is not None else ftoep.Plan(specs[:k])
         fh = f[:e_units].cpu().pin_memory()
         uh = torch.empty_like(fh).pin_memory()
         eplan.solve(fh, uh)
@@ -429,7 +432,8 @@ def run_batched(args):
         del fh, uh
     except (RuntimeError, ValueError, OSError) as exc:  # host memory
         e2e = {"unavailable": str(exc)[:200]}
-    plan.close()
+    if plan is not None:
+        plan.close()
     compare = None
     if not args.no_compare:
         other = "fp64" if precision == "mixed" else "mixed"
