@@ -46,6 +46,9 @@ def parse():
                     help="default: fp64 for diffusion/scalar, mixed for wave")
     ap.add_argument("--no-compare", action="store_true", help="skip the mixed-precision comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-singles", action="store_true", help="batched: skip the single-problem lines")
+    ap.add_argument("--scheduler", type=int, default=0, choices=[0, 1, 2],
+                    help="single workloads: 0 library choice, 1 per-level launches, 2 persistent chain")
     ap.add_argument("--M", type=int, default=None, help="override the workload's interior points (profiling cases)")
     ap.add_argument("--N", type=int, default=None, help="override the workload's time steps (profiling cases)")
     return ap.parse_args()
@@ -135,6 +138,9 @@ def work_model(p, precision):
         sine_b = nsolve * (p.M * p.N * (fb + (fb if precision == "fp64" else 4)) + 2 * P * ncols * zb)
     flops = {"block_solve": block, "conv_smem": conv_smem, "conv_fourstep": conv_4, "sine": sine}
     byts = {"block_solve": block_b, "conv_smem": smem_b, "conv_fourstep": four_b, "sine": sine_b}
+    # the persistent per-pair solve runs the block solves and every cross-block level
+    flops["chain"] = block + conv_smem + conv_4
+    byts["chain"] = block_b + smem_b + four_b
     if precision == "mixed":  # residual product of length 2Np in float-float, residual kernel
         n = 2 * Np
         flops["residual"] = P * (10 * n * math.log2(n) + 6 * n)
@@ -142,22 +148,27 @@ def work_model(p, precision):
     return flops, byts
 
 
-def roofline_of(flops, byts, prof, steps, precision):
-    """Roofline of the dominant kernel class: achieved flop rate against the ALU peak of
-    its arithmetic and achieved algorithmic-byte rate against the measured HBM copy
-    bandwidth; the binding one (larger fraction) is reported, the other beside it."""
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
-    name, (ms, ops, launches) = dom[0], dom[1]
-    if name not in flops or ms <= 0 or flops[name] <= 0:
+def roofline_of(flops, byts, prof, ms_per_step, precision):
+    """Roofline of the dominant kernel class.  The class times come from one instrumented
+    solve in which every kernel runs on one stream (no overlap), so the class's share of
+    that solve times ms_per_step is its time inside a timed step; achieved = the class's
+    algorithmic flops (bytes) per step over that time, against the ALU peak of its
+    arithmetic (bytes: the measured HBM copy bandwidth).  The binding one (larger
+    fraction) is reported, the other beside it."""
+    total = sum(v[0] for v in prof.values())
+    name = max(prof, key=lambda k: prof[k][0])
+    ms, ops, launches = prof[name]
+    if name not in flops or ms <= 0 or total <= 0 or flops[name] <= 0:
         return None
-    sec = ms * 1e-3
-    if precision == "mixed" and name != "residual":
-        peak, what = FP32_PEAK_TFLOPS, "FP32 (152 SMs x 128 lanes x 2 flops x 2.07 GHz)"
+    share = ms / total
+    sec = share * ms_per_step * 1e-3
+    if precision == "mixed":  # float and float-float arithmetic: FP32 instructions
+        peak, what = FP32_PEAK_TFLOPS, "FP32 from unit counts: 152 SMs x 128 lanes x 2 flops x 2.07 GHz"
     else:
-        peak, what = FP64_PEAK_TFLOPS, "FP64 (recipe nominal 1.25; DFMA probe 1.19)"
-    alu = flops[name] * steps / sec / 1e12
+        peak, what = FP64_PEAK_TFLOPS, "FP64 nominal 1.25 TFLOP/s (DFMA probe: 1.19)"
+    alu = flops[name] / sec / 1e12
     hbm_peak = measured_peaks().get("hbm_gbs", 6800.0)
-    hbm = byts.get(name, 0.0) * steps / sec / 1e9
+    hbm = byts.get(name, 0.0) / sec / 1e9
     alu_frac, hbm_frac = alu / peak, hbm / hbm_peak
     alu_obj = {"bound": "alu", "achieved": alu, "peak": peak, "unit": "TFLOP/s", "frac": alu_frac,
                "peak_note": what}
@@ -165,12 +176,22 @@ def roofline_of(flops, byts, prof, steps, precision):
                "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs)"}
     main, other = (alu_obj, hbm_obj) if alu_frac >= hbm_frac else (hbm_obj, alu_obj)
     out = dict(main)
-    out.update({"kernel_class": name, "traffic": None, "per_launch_ms": ms / max(1, ops),
-                "launches": launches, "other_bound": other,
+    out.update({"kernel_class": name, "class_share": share, "class_ms_per_step": share * ms_per_step,
+                "launches_per_step": launches, "per_launch_ms": share * ms_per_step / max(1, launches),
+                "traffic": None, "other_bound": other,
                 "note": "flops: 5 n log2 n per complex FFT of length n, 6 per complex product; bytes: "
-                        "compulsory HBM bytes of the class (no four-step scratch); event time of the "
-                        "class over the timed steps"})
+                        "compulsory HBM bytes of the class (no four-step scratch); class time = its share of "
+                        "one single-stream instrumented solve x ms_per_step"})
     return out
+
+
+def class_profile(plan, f, u):
+    """Kernel-class event times of one instrumented solve (every kernel on one stream)."""
+    plan.profile(True)
+    plan.solve(f, u)
+    prof = plan.profile_read()
+    plan.profile(False)
+    return prof
 
 
 class Ranks:
@@ -340,10 +361,91 @@ def run_reference(args):
 
 # ----------------------------------------------------------------------------- GPU arm
 
-def run_batched(args):
-    """Config-4 workload: all problems in one plan (internal streams, longest first)."""
+def batch_field(probs, device="cuda"):
+    import torch
+    from paper_1710_11593_gb300 import workloads as wl
+    units = sum(p.M * p.N for p in probs)
+    f = torch.empty(units, dtype=torch.float64, device=device)
+    off = 0
+    for p in probs:
+        n = p.M * p.N
+        wl.materialize_torch(p.source, p.kind, p.N, p.M, device=device, out=f[off:off + n].view(p.M, p.N))
+        off += n
+    return f
+
+
+def timed(plan, f, u, steps, warmup, rk, local, clocks=True):
+    """Warm-up solves, then `steps` solves between CUDA events on the plan's stream (the
+    current torch stream), barrier and synchronize on both sides.  Returns (ms per step,
+    kernels launched per step, clock record)."""
+    import torch
+    for _ in range(warmup):
+        plan.solve(f, u)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local) if clocks else None
+    plan.profile(False)  # resets the launch counters; no per-launch events in the timed steps
+    rk.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        plan.solve(f, u)
+    e1.record()
+    torch.cuda.synchronize()
+    rk.barrier()
+    clk = sampler.stop() if sampler else None
+    launches = sum(v[2] for v in plan.profile_read().values()) / max(1, steps)
+    return e0.elapsed_time(e1) / steps, launches, clk
+
+
+def oracle_prefix_error(p, u, n0):
+    """Relative error (2-norm and max over max) of the first n0 levels of the GPU field u
+    [M][N] against the oracle's solve of the n0-level problem with the same tau."""
+    import numpy as np
+    from oracle import oracle as orc
+    from paper_1710_11593_gb300 import workloads as wl
+    fpre = wl.materialize(p.source, p.kind, p.N, p.M, t=wl.time_points(p.kind, p.N, p.T)[:n0])
+    ref = orc.march(p.kind, p.space, p.gamma, fpre, T=p.T * n0 / p.N, L=p.L, lam=p.lam)
+    got = u[:, :n0].cpu().numpy()
+    return float(max(np.linalg.norm(got - ref) / np.linalg.norm(ref), np.max(np.abs(got - ref)) / np.max(np.abs(ref))))
+
+
+def run_single(name, precision, steps, warmup, rk, local, tuning=None):
+    """One single-problem workload: timed solves, class roofline, error against the oracle on
+    a 1024-level prefix."""
     import torch
     from paper_1710_11593_gb300 import ftoep, workloads as wl
+    p, wname = workload(name)
+    prec = ftoep.FP64 if precision == "fp64" else ftoep.MIXED
+    spec = ftoep.ProblemSpec(p.kind, p.gamma, p.N, p.M, p.space, prec, lam=p.lam)
+    f = wl.materialize_torch(p.source, p.kind, p.N, p.M, device="cuda")
+    u = torch.empty_like(f)
+    with ftoep.Plan([spec], tuning=tuning) as plan:
+        ms, launches, _ = timed(plan, f, u, steps, warmup, rk, local, clocks=False)
+        prof = class_profile(plan, f, u)
+        plan.solve(f, u)
+        plan.sync()
+    ms = rk.max(ms)
+    fl, by = work_model(p, precision)
+    out = {"workload": wname, "precision": precision, "ms_per_step": ms, "value": p.M * p.N / (ms * 1e-3),
+           "unit": "unknowns/s", "gpu_launches": launches,
+           "roofline": roofline_of(fl, by, prof, ms, precision),
+           "kernel_time_share": {k: v[0] / max(1e-9, sum(x[0] for x in prof.values())) for k, v in prof.items()},
+           "rel_err_vs_oracle_prefix": oracle_prefix_error(p, u, min(p.N, 1024)),
+           "oracle_prefix_levels": min(p.N, 1024)}
+    del f, u
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batched(args):
+    """Config-4 workload: all problems in one plan (chain schedule: groups of problems, one
+    persistent launch per solve and group)."""
+    import torch
+    from paper_1710_11593_gb300 import ftoep
 
     rk = Ranks()
     world, rank, local = rk.world, rk.rank, rk.local
@@ -354,41 +456,11 @@ def run_batched(args):
     prec = ftoep.FP64 if precision == "fp64" else ftoep.MIXED
     specs = [ftoep.ProblemSpec(p.kind, p.gamma, p.N, p.M, p.space, prec) for p in probs]
     units = sum(p.M * p.N for p in probs)
-    f = torch.empty(units, dtype=torch.float64, device="cuda")
-    off = 0
-    for p in probs:
-        n = p.M * p.N
-        wl.materialize_torch(p.source, p.kind, p.N, p.M, device="cuda", out=f[off:off + n].view(p.M, p.N))
-        off += n
+    f = batch_field(probs)
     u = torch.empty_like(f)
     plan = ftoep.Plan(specs)
-
-    barrier = rk.barrier
-
-    for _ in range(args.warmup):
-        plan.solve(f, u)
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    plan.profile(False)  # resets the launch counters; no per-launch events in the timed steps
-    barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        plan.solve(f, u)
-    e1.record()
-    torch.cuda.synchronize()
-    barrier()
-    clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    launches = sum(v[2] for v in plan.profile_read().values())
-    # kernel-class times from one more (untimed) step with a CUDA-event pair around every launch
-    plan.profile(True)
-    plan.solve(f, u)
-    prof = plan.profile_read()
-    plan.profile(False)
+    ms, launches, clk = timed(plan, f, u, args.steps, args.warmup, rk, local)
+    prof = class_profile(plan, f, u)
     ms = rk.max(ms)
     value = rk.value(units, ms)
     busy = sum(x[0] for x in prof.values())
@@ -399,9 +471,7 @@ def run_batched(args):
         for k in f1:
             fl[k] = fl.get(k, 0.0) + f1[k]
             by[k] = by.get(k, 0.0) + b1[k]
-    roof = roofline_of(fl, by, prof, 1, precision)
-    if roof:
-        roof["note"] += "; problems run on 4 concurrent streams, so class event times include shared GPU time"
+    roof = roofline_of(fl, by, prof, ms, precision)
     # end to end through host buffers (pinned), copies inside the call.  All ranks of a node
     # share its host memory: the pinned buffers of all ranks are kept within 3/4 of it, and
     # when the whole batch does not fit the end-to-end step covers a prefix of the problems
@@ -439,15 +509,12 @@ def run_batched(args):
         other = "fp64" if precision == "mixed" else "mixed"
         specs2 = [ftoep.ProblemSpec(p.kind, p.gamma, p.N, p.M, p.space,
                                     ftoep.FP64 if other == "fp64" else ftoep.MIXED) for p in probs]
-        plan2 = ftoep.Plan(specs2)
         u2 = torch.empty_like(f)
-        plan2.solve(f, u2)
-        torch.cuda.synchronize()
-        e0.record()
-        plan2.solve(f, u2)
-        e1.record()
-        torch.cuda.synchronize()
-        ms2 = e0.elapsed_time(e1)
+        with ftoep.Plan(specs2) as plan2:
+            # two warm-up solves: the first runs directly, the second captures the graph, so
+            # the timed solve is a replay like the timed steps of the main leg
+            ms2, launches2, _ = timed(plan2, f, u2, 1, 2, rk, local, clocks=False)
+        ms2 = rk.max(ms2)
         fp64u = u2 if other == "fp64" else u
         mixu = u if other == "fp64" else u2
         # relative error per problem, worst case
@@ -458,10 +525,21 @@ def run_batched(args):
             a, b = mixu[off:off + n], fp64u[off:off + n]
             worst = max(worst, float(torch.linalg.norm(a - b) / torch.linalg.norm(b)))
             off += n
+        fl2 = {}
+        for p in probs:
+            for kk, vv in work_model(p, other)[0].items():
+                fl2[kk] = fl2.get(kk, 0.0) + vv
+        solve_flops = fl2["chain"] + fl2["sine"]
         compare = {"precision": other, "value": world * units / (ms2 * 1e-3), "ms_per_step": ms2,
+                   "gpu_launches": launches2,
                    "mixed_speedup_vs_fp64": (ms2 / ms) if other == "fp64" else (ms / ms2),
                    "mixed_rel_err_vs_fp64_gpu_worst_problem": worst}
-        plan2.close()
+        if other == "fp64":
+            compare["fp64_tflops_whole_step"] = solve_flops / (ms2 * 1e-3) / 1e12
+            compare["fp64_frac_of_peak_whole_step"] = compare["fp64_tflops_whole_step"] / FP64_PEAK_TFLOPS
+        del u2
+    del f, u
+    torch.cuda.empty_cache()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # oracle on a bounded sample: the first 2048 levels of 8 problems (all their points)
@@ -473,14 +551,18 @@ def run_batched(args):
             tot_s += dt
         cpu = {"value": tot_units / tot_s, "unit": "unknowns/s", "cores": th, "kind": "oracle",
                "sample": f"first min(N,2048) levels of the first 8 problems, {tot_s:.1f} s; O(M N^2) direct marching"}
+    singles = None
+    if not args.no_singles:
+        singles = [run_single("diffusion", "fp64", 10, 3, rk, local), run_single("wave", "mixed", 5, 3, rk, local)]
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f32+f64", "data": "synthetic",
                "config": {"workload": wname, "nprob": len(probs), "unknowns": units, "precision": precision,
+                          "scheduler": "chain",
                           "l2": f"inputs larger than L2 (f = {units * 8 / 1e9:.1f} GB)"},
                "roofline": roof, "kernel_time_share": shares, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-               "gpu_launches": launches, "compare": compare}
+               "gpu_launches": launches, "compare": compare, "singles": singles}
         print(json.dumps(out))
     rk.close()
     return 0
@@ -501,43 +583,17 @@ def run_ours(args):
     spec = ftoep.ProblemSpec(p.kind, p.gamma, p.N, p.M, p.space, prec, lam=p.lam)
     f = wl.materialize_torch(p.source, p.kind, p.N, p.M, device="cuda")
     u = torch.empty_like(f)
-    plan = ftoep.Plan([spec])
-
-    barrier = rk.barrier
-
-    for _ in range(args.warmup):
-        plan.solve(f, u)
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    plan.profile(False)  # resets the launch counters; no per-launch events in the timed steps
-    barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        plan.solve(f, u)
-    e1.record()
-    torch.cuda.synchronize()
-    barrier()
-    clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    launches = sum(v[2] for v in plan.profile_read().values())
-    # kernel-class times from one more (untimed) step with a CUDA-event pair around every launch
-    plan.profile(True)
-    plan.solve(f, u)
-    prof = plan.profile_read()
-    plan.profile(False)
+    tuning = {"scheduler": args.scheduler} if args.scheduler else None
+    plan = ftoep.Plan([spec], tuning=tuning)
+    ms, launches, clk = timed(plan, f, u, args.steps, args.warmup, rk, local)
+    prof = class_profile(plan, f, u)
     ms = rk.max(ms)
     units = p.M * p.N
     value = rk.value(units, ms)
     tot_ms = sum(x[0] for x in prof.values())
     shares = {k: v[0] / max(1e-9, tot_ms) for k, v in prof.items()}
-
-    # roofline of the dominant kernel class
     fl, by = work_model(p, precision)
-    roof = roofline_of(fl, by, prof, 1, precision)
+    roof = roofline_of(fl, by, prof, ms, precision)
 
     # end to end: same solve through the C ABI with pinned HOST buffers (copies inside)
     fh = f.cpu().pin_memory()
@@ -564,24 +620,15 @@ def run_ours(args):
         other = "mixed" if precision == "fp64" else "fp64"
         spec2 = ftoep.ProblemSpec(p.kind, p.gamma, p.N, p.M, p.space,
                                   ftoep.MIXED if other == "mixed" else ftoep.FP64, lam=p.lam)
-        plan2 = ftoep.Plan([spec2])
         u2 = torch.empty_like(f)
-        plan2.solve(f, u2)
-        torch.cuda.synchronize()
-        csteps = max(1, min(args.steps, 3))
-        e0.record()
-        for _ in range(csteps):
-            plan2.solve(f, u2)
-        e1.record()
-        torch.cuda.synchronize()
-        ms2 = e0.elapsed_time(e1) / csteps
+        with ftoep.Plan([spec2], tuning=tuning) as plan2:
+            ms2, _, _ = timed(plan2, f, u2, max(1, min(args.steps, 3)), 2, rk, local, clocks=False)
         fp64u = u if precision == "fp64" else u2
         mixu = u2 if precision == "fp64" else u
         rel = float(torch.linalg.norm(mixu - fp64u) / torch.linalg.norm(fp64u))
         compare = {"precision": other, "value": world * units / (ms2 * 1e-3), "ms_per_step": ms2,
                    "mixed_speedup_vs_fp64": (ms / ms2) if other == "mixed" else (ms2 / ms),
                    "mixed_rel_err_vs_fp64_gpu": rel}
-        plan2.close()
         del u2
 
     cpu = None
@@ -602,7 +649,7 @@ def run_ours(args):
                "data": "synthetic",
                "config": {"workload": wname, "M": p.M, "N": p.N, "gamma": p.gamma, "precision": precision,
                           "l2": f"inputs larger than L2 (f = {f.numel() * 8 / 1e9:.2f} GB)",
-                          "block": B, "leaf": L, "first_fft_level": Sf},
+                          "block": B, "scheduler": args.scheduler or "library choice"},
                "roofline": roof, "kernel_time_share": shares, "cpu_baseline": cpu, "e2e": e2e,
                "clocks": clk, "gpu_launches": launches, "compare": compare,
                "max_abs_err_vs_exact": disc}

@@ -43,10 +43,10 @@
  *
  * Streams and errors: every call is ordered on the CUDA stream given to ftoep_create
  * and may return before the GPU work has finished.  Errors are returned as status
- * codes only; nothing aborts or throws across this interface.  A device-side wait that
- * exceeds its bound sets a flag in the plan; the next call that synchronises
- * (ftoep_sync, ftoep_adjoint with a host gamma-gradient, any call with host buffers)
- * returns FTOEP_ETIMEOUT.  ftoep_last_error gives a message for the last failure.
+ * codes only; nothing aborts or throws across this interface.  No kernel of the library
+ * waits for another block or launch (blocks synchronise only within themselves or their
+ * hardware cluster), so no call can time out.  ftoep_last_error gives a message for the
+ * last failure.
  *
  * Threads: a plan's workspace, counters and captured graphs are shared by its calls, so
  * calls on one plan must not overlap in time from different host threads; different
@@ -69,7 +69,8 @@ typedef enum {
   FTOEP_EINVAL = 1,       /* bad argument (range, null pointer, size mismatch)        */
   FTOEP_ENOMEM = 2,       /* device or host allocation failed                          */
   FTOEP_ECUDA = 3,        /* a CUDA runtime call failed                                */
-  FTOEP_ETIMEOUT = 4,     /* a bounded device-side wait gave up                        */
+  FTOEP_ETIMEOUT = 4,     /* reserved: never returned (the library has no device-side
+                             waits)                                                    */
   FTOEP_EUNSUPPORTED = 5  /* valid input that this build does not handle               */
 } ftoep_status;
 
@@ -104,17 +105,31 @@ typedef struct {
   int64_t N, M;
 } ftoep_problem;
 
-/* Optional tuning (NULL or 0 fields = library choice; ftoep_autotune picks fft_tile).
+/* Schedules of the pair solves (ftoep_tuning.scheduler). */
+typedef enum {
+  FTOEP_SCHED_AUTO = 0,   /* library choice: chain for plans of several problems, else levels */
+  FTOEP_SCHED_LEVELS = 1, /* one launch per time block and per cross-block level, all pairs
+                             of a problem in each launch, problems on internal streams     */
+  FTOEP_SCHED_CHAIN = 2   /* one persistent launch per solve for every pair of a group of
+                             problems: each block runs one pair's whole time recursion, pairs
+                             taken longest chain first from a work counter; groups of
+                             problems sized to a memory budget (half the free device memory
+                             at plan creation, at most 32 GiB of pair arrays)              */
+} ftoep_scheduler;
+
+/* Optional tuning (NULL or 0 fields = library choice; ftoep_autotune picks fft_tile and
+ * scheduler).
  * fft_tile: the time block length B (power of two, 16..4096; default 4096, capped at N
  *   rounded up to a power of two).  Every block of B levels is solved by a causal
  *   convolution with the per-mode inverse of the block operator (one FFT of length 2B);
  *   the half-split updates between blocks are circulant convolutions.
- * leaf, gemm_max_level: shape the substitution that builds the per-mode block inverses
- *   once at plan creation (leaf: dense forward-substitution size, power of two <= 16;
- *   levels below gemm_max_level use dense products instead of FFTs).
- * modes_per_cta: reserved. */
+ * leaf, gemm_max_level: shape only the substitution that builds the per-mode block
+ *   inverses once at plan creation (leaf: dense forward-substitution size, power of two
+ *   <= 16; levels below gemm_max_level use dense products instead of FFTs).  The solves
+ *   themselves do not depend on them (up to rounding of the block inverses).
+ * scheduler: an ftoep_scheduler value. */
 typedef struct {
-  int leaf, fft_tile, gemm_max_level, modes_per_cta;
+  int leaf, fft_tile, gemm_max_level, scheduler;
 } ftoep_tuning;
 
 /* Create a plan for nprob problems (1 <= nprob).  Computes the weights a_j of every
@@ -165,16 +180,20 @@ typedef enum {
   FTOEP_K_CONV_FOURSTEP = 2,  /* cross-block circulant convolution, three-kernel four-step  */
   FTOEP_K_SINE = 3,           /* sine transforms along space                                */
   FTOEP_K_OTHER = 4,          /* packing, time sums, reductions, spectra                    */
-  FTOEP_K_RESIDUAL = 5        /* mixed path: float-float residual product and residual      */
+  FTOEP_K_RESIDUAL = 5,       /* mixed path: float-float residual product and residual      */
+  FTOEP_K_CHAIN = 6           /* persistent per-pair solve (block solves and every level)   */
 } ftoep_kernel_class;
 
 /* Instrumentation (no counterpart in the paper).  ftoep_profile waits for the stream,
  * clears the per-class counters and switches CUDA-event timing of every subsequent
  * operation on (enable != 0) or off.  Kernel launches are always counted.
- * ftoep_profile_read waits for the stream and returns, for one class, the summed event
- * time in milliseconds of the timed operations, the number of timed operations (one
- * operation = one launcher call: 1 kernel, or 3 for the four-step convolution) and the
- * number of kernels launched since the last ftoep_profile.  Any output may be NULL. */
+ * While timing is on, every problem's kernels run on the plan's stream one after another
+ * (no internal streams, no graph), so the class times add up to the instrumented solve
+ * and do not overlap.  ftoep_profile_read waits for the stream and returns, for one class,
+ * the summed event time in milliseconds of the timed operations, the number of timed
+ * operations (one operation = one launcher call: 1 kernel, or 3 for the four-step
+ * convolution) and the number of kernels launched since the last ftoep_profile.  Any
+ * output may be NULL. */
 ftoep_status ftoep_profile(ftoep_plan p, int enable);
 ftoep_status ftoep_profile_read(ftoep_plan p, int kclass, double* total_ms, int64_t* ops, int64_t* launches);
 
@@ -184,15 +203,19 @@ ftoep_status ftoep_profile_read(ftoep_plan p, int kclass, double* total_ms, int6
  * allocate, loops where cudaMalloc's blocking and device synchronisation are not
  * acceptable).  y = T x (transpose = 0) or T^T x (transpose = 1) for nlines lines of
  * length N, T lower-triangular Toeplitz with first column a (N doubles, e.g. from
- * ftoep_weights).  a, x, y: device pointers, [nlines][N]; x and y may not overlap.
+ * ftoep_weights).  a, x, y: device (or managed) memory, [nlines][N]; host memory returns
+ * FTOEP_EINVAL before any launch (nothing is staged); x and y may not overlap.  A CUDA error
+ * pending from earlier work is reported as FTOEP_ECUDA and left in place.
  * Work is ordered on cuda_stream (a cudaStream_t, NULL = legacy default stream).
  * All intermediates live in one static device array of 16.8 MB compiled into the
  * library (held on every GPU that loads it until the process exits); hence N <= 32768,
  * larger N returns FTOEP_EINVAL.  Nothing is allocated or freed, ever.  The first call
  * on a device (with that device current) looks up the array's address and writes its
  * twiddle tables, synchronising the device once: make that first call before any stream
- * capture.  Calls share the array, so calls whose GPU work overlaps in time race and must
- * not be issued.  Messages for failures: ftoep_last_error(NULL, ...). */
+ * capture.  The array's address and tables belong to the device context of that first
+ * call: a device reset (cudaDeviceReset) while the library is loaded is not supported.
+ * Calls share the array, so calls whose GPU work overlaps in time race and must not be
+ * issued.  Messages for failures: ftoep_last_error(NULL, ...). */
 ftoep_status ftoep_matvec_noalloc(const double* a, int64_t N, const double* x, double* y, int64_t nlines,
                                   int transpose, void* cuda_stream);
 
@@ -206,8 +229,7 @@ ftoep_status ftoep_matvec_noalloc(const double* a, int64_t N, const double* x, d
  * *out is left unchanged on error. */
 ftoep_status ftoep_autotune(const ftoep_problem* probs, int nprob, void* cuda_stream, ftoep_tuning* out);
 
-/* Wait for the plan's stream; returns FTOEP_ETIMEOUT if a device-side wait gave up,
- * FTOEP_ECUDA on an asynchronous CUDA error. */
+/* Wait for the plan's stream; returns FTOEP_ECUDA on an asynchronous CUDA error. */
 ftoep_status ftoep_sync(ftoep_plan p);
 
 /* Copy a NUL-terminated message for the last failure of p (or of plan creation if p is

@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -30,7 +31,7 @@ using namespace ftoep;
 namespace {
 
 constexpr int kMaxStreams = 4;
-constexpr int kNumClasses = 6;
+constexpr int kNumClasses = 7;
 constexpr int kDotBlocks = 1024;
 
 struct Prob {
@@ -44,6 +45,9 @@ struct Prob {
   int64_t foff = 0, voff = 0;
   int stream = 0;               // internal stream the problem runs on
   double cost = 0;              // scheduling estimate
+  double pair_cost = 0;         // one pair's chain (block solves and cross-block levels)
+  int group = -1;               // chain schedule: group of the problem
+  size_t zbyte = 0;             // chain schedule: offset of its pair array in the group buffer
   std::vector<double> h_a, h_dadg;
   double* a = nullptr;          // first column of the time operator (original form)
   double* dadg = nullptr;       // its derivative in gamma
@@ -123,11 +127,35 @@ struct SolveGraph {
   const void* phi = nullptr;
   int runs = 0;                   // direct runs seen before the capture
   cudaGraphExec_t exec = nullptr;
-  int64_t launches[6] = {0, 0, 0, 0, 0, 0};  // kernels per replay, per class
+  int64_t launches[kNumClasses] = {};  // kernels per replay, per class
+};
+
+// Chain schedule: problems whose pair arrays are resident together, solved by one
+// persistent launch per precision (chain.cu).
+struct ChainGroup {
+  std::vector<int> probs;          // problem indices, longest chains first
+  ChainProb* d_probs = nullptr;    // device descriptors of its problems
+  int2* d_items[2] = {nullptr, nullptr};  // per precision (0 double, 1 float): (descriptor, pair)
+  int nitems[2] = {0, 0};
+  size_t bytes = 0;                // pair arrays of the group
 };
 
 struct ftoep_plan_s {
   std::vector<Prob> probs;
+  // Fault injection on the host: with FTOEP_FAIL_ALLOC_AFTER=k in the environment at plan
+  // creation, the plan's device allocations fail (FTOEP_ENOMEM) after its first k -- the
+  // out-of-memory paths without exhausting a GPU.
+  long fail_after = -1;
+  long nalloc = 0;
+  int sched = 1;                  // 1: per-level launches, 2: persistent per-pair chains
+  std::vector<ChainGroup> groups;
+  void* gz = nullptr;             // pair arrays of the current group
+  unsigned* counters = nullptr;   // one work counter per chain launch of a solve
+  int ncounters = 0;
+  void* chain_scr[2] = {nullptr, nullptr};
+  int64_t chain_scr_el[2] = {0, 0};
+  int chain_grid[2] = {0, 0};
+  size_t chain_smem[2] = {0, 0};
   cudaStream_t stream = nullptr;  // caller's stream
   int device = 0;
   int64_t ntw = 0;
@@ -143,9 +171,9 @@ struct ftoep_plan_s {
   std::vector<void*> allocs;
   // launch counters (always on) and optional CUDA-event timing per kernel class
   bool prof_on = false;
-  int64_t launches[kNumClasses] = {0, 0, 0, 0, 0, 0};
-  double prof_ms[kNumClasses] = {0, 0, 0, 0, 0, 0};
-  int64_t prof_ops[kNumClasses] = {0, 0, 0, 0, 0, 0};
+  int64_t launches[kNumClasses] = {};
+  double prof_ms[kNumClasses] = {};
+  int64_t prof_ops[kNumClasses] = {};
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
   std::vector<cudaEvent_t> evpool;
   std::vector<SolveGraph> graphs;  // most recently used last
@@ -183,6 +211,8 @@ ftoep_status fail(ftoep_plan p, ftoep_status s, const char* fmt, ...) {
 ftoep_status dalloc(ftoep_plan pl, void** out, size_t bytes) {
   *out = nullptr;
   if (bytes == 0) return FTOEP_OK;
+  if (pl->fail_after >= 0 && pl->nalloc++ >= pl->fail_after)
+    return fail(pl, FTOEP_ENOMEM, "cudaMalloc(%zu bytes): refused by FTOEP_FAIL_ALLOC_AFTER", bytes);
   cudaError_t e = cudaMalloc(out, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -293,6 +323,8 @@ ftoep_status validate(const ftoep_problem& d, int i, const ftoep_tuning* tune) {
       return fail(pl, FTOEP_EINVAL, "tuning: fft_tile must be a power of two in [16, 4096]");
     if (tune->gemm_max_level && (!is_pow2(tune->gemm_max_level) || tune->gemm_max_level > 2048))
       return fail(pl, FTOEP_EINVAL, "tuning: gemm_max_level must be a power of two <= 2048");
+    if (tune->scheduler < 0 || tune->scheduler > FTOEP_SCHED_CHAIN)
+      return fail(pl, FTOEP_EINVAL, "tuning: scheduler must be 0 (library choice), 1 (levels) or 2 (chain)");
   }
   return FTOEP_OK;
 }
@@ -463,19 +495,37 @@ ftoep_status scan_lines(ftoep_plan pl, Ws& w, Prob& pb, const double* in, double
 // lower triangle) with right-hand side f + [c tau M_{n-1} phi] - S u0, and
 // u = u0 + tau cumsum(v).  Written in v the history terms carry the scale tau^(1-g)
 // instead of tau^-g, which keeps float arithmetic usable at large N.
-ftoep_status solve_problem(ftoep_plan pl, Ws& w, Prob& pb, const double* f, double* u, const double* u0,
-                           const double* phi) {
+//
+// A problem's solve in three pieces around its pair solves (per-level launches, or the
+// persistent chain over a group of problems):
+//   rhs_forward        right-hand side + forward sine transform -> pairs z
+//   after_first_solve  inverse transform + time sums -> u; mixed: residual of the same
+//                      rows and its forward transform -> z (the correction's right-hand side)
+//   after_correction   mixed: inverse transform of the correction, u += tau cumsum
+
+// Right-hand side of the difference form and its forward sine transform into z.
+ftoep_status rhs_forward(ftoep_plan pl, Ws& w, Prob& pb, void* z, const double* f, const double* u0,
+                         const double* phi) {
   cudaStream_t st = w.st;
-  const Prec pr = pb.prec;
-  DstArgs da = dst_args(pl, pb, pr, w.z);
+  DstArgs da = dst_args(pl, pb, pb.prec, z);
   da.f = f;
   da.u0 = u0;
   da.phi = (pb.d.kind == FTOEP_L1_HYPERBOLIC) ? phi : nullptr;
   da.wu0 = pb.wu0;
   da.wphi = pb.wphi;
   da.diff_form = 1;
-  LAUNCH(FTOEP_K_SINE, launch_dst_forward(pr, da, st));
-  TRY(solve_pairs(pl, w, pb, pr, w.z, pb.spec));
+  LAUNCH(FTOEP_K_SINE, launch_dst_forward(pb.prec, da, st));
+  return FTOEP_OK;
+}
+
+// z holds the solved v in mode space.  Double: u = u0 + tau cumsum(S^-1 v).  Mixed: the
+// same in float-float time sums, then the residual r = f + c tau M phi - E v - S u of the
+// same rows (E v in float-float, f - S u in double) and its forward transform into z.
+ftoep_status after_first_solve(ftoep_plan pl, Ws& w, Prob& pb, void* z, const double* f, double* u,
+                               const double* u0, const double* phi) {
+  cudaStream_t st = w.st;
+  const Prec pr = pb.prec;
+  DstArgs da = dst_args(pl, pb, pr, z);
   if (pr == P64) {
     da.u = u;
     da.accumulate = 0;
@@ -485,7 +535,6 @@ ftoep_status solve_problem(ftoep_plan pl, Ws& w, Prob& pb, const double* f, doub
   }
   // mixed: the solved v (physical space) in float in r, u = u0 + tau cumsum(v)
   float* r32 = (float*)w.r;
-  da.u = nullptr;
   da.u32 = r32;
   da.accumulate = 0;
   LAUNCH(FTOEP_K_SINE, launch_dst_inverse(pr, da, st));
@@ -496,7 +545,7 @@ ftoep_status solve_problem(ftoep_plan pl, Ws& w, Prob& pb, const double* f, doub
   ResidualArgs ra{};
   ra.f = f;
   ra.u0 = nullptr;
-  ra.phi = da.phi;
+  ra.phi = (pb.d.kind == FTOEP_L1_HYPERBOLIC) ? phi : nullptr;
   ra.wu0 = pb.wu0;
   ra.wphi = pb.wphi;
   ra.u = u;
@@ -509,17 +558,38 @@ ftoep_status solve_problem(ftoep_plan pl, Ws& w, Prob& pb, const double* f, doub
   ra.inv_h2 = 1.0 / (pb.h * pb.h);
   ra.lambda = pb.d.lambda;
   LAUNCH(FTOEP_K_RESIDUAL, launch_residual(ra, st));
-  // correction: same rows, zero initial data; v-correction lands in r, then u += tau cumsum
-  DstArgs dr = dst_args(pl, pb, pr, w.z);
+  // correction: same rows, zero initial data
+  DstArgs dr = dst_args(pl, pb, pr, z);
   dr.f32 = r32;
   dr.diff_form = 1;
   LAUNCH(FTOEP_K_SINE, launch_dst_forward(pr, dr, st));
-  TRY(solve_pairs(pl, w, pb, pr, w.z, pb.spec));
+  return FTOEP_OK;
+}
+
+// Mixed: z holds the solved correction; u += tau cumsum(S^-1 z).
+ftoep_status after_correction(ftoep_plan pl, Ws& w, Prob& pb, void* z, double* u) {
+  cudaStream_t st = w.st;
+  float* r32 = (float*)w.r;
+  DstArgs dr = dst_args(pl, pb, pb.prec, z);
   dr.u32 = r32;
   dr.accumulate = 0;
-  LAUNCH(FTOEP_K_SINE, launch_dst_inverse(pr, dr, st));
+  LAUNCH(FTOEP_K_SINE, launch_dst_inverse(pb.prec, dr, st));
   TRY(scan_lines(pl, w, pb, nullptr, u, nullptr, 1, 0, r32));
   return FTOEP_OK;
+}
+
+ftoep_status ensure_level_ws(ftoep_plan pl, Ws& w);
+
+// One problem with per-level launches on the stream's own pair array.
+ftoep_status solve_problem(ftoep_plan pl, Ws& w, Prob& pb, const double* f, double* u, const double* u0,
+                           const double* phi) {
+  TRY(ensure_level_ws(pl, w));
+  TRY(rhs_forward(pl, w, pb, w.z, f, u0, phi));
+  TRY(solve_pairs(pl, w, pb, pb.prec, w.z, pb.spec));
+  TRY(after_first_solve(pl, w, pb, w.z, f, u, u0, phi));
+  if (pb.prec == P64) return FTOEP_OK;
+  TRY(solve_pairs(pl, w, pb, pb.prec, w.z, pb.spec));
+  return after_correction(pl, w, pb, w.z, u);
 }
 
 // Adjoint of one problem (double): dldf = A_u^-T g and, if dgamma_out, the partial
@@ -530,6 +600,7 @@ ftoep_status adjoint_problem(ftoep_plan pl, Ws& w, Prob& pb, const double* g, co
   if (pb.bluestein && pb.M + 1 > bluestein_max_K(P64))
     return fail(pl, FTOEP_EUNSUPPORTED, "adjoint: M+1 = %lld > %d needs a double sine transform that is not built",
                 (long long)(pb.M + 1), bluestein_max_K(P64));
+  TRY(ensure_level_ws(pl, w));
   // The adjoint runs in double with the problem's own block length.
   Prob q = pb;
   q.prec = P64;
@@ -558,6 +629,17 @@ ftoep_status adjoint_problem(ftoep_plan pl, Ws& w, Prob& pb, const double* g, co
     LAUNCH(FTOEP_K_OTHER, launch_dot(dt, st));
     LAUNCH(FTOEP_K_OTHER, launch_sum(w.dpart, kDotBlocks, dgamma_out, st));
   }
+  return FTOEP_OK;
+}
+
+// Pair array and four-step scratch of a stream's per-level solves (allocated on first use
+// when the plan runs the chain schedule).
+ftoep_status ensure_level_ws(ftoep_plan pl, Ws& w) {
+  if (!w.z) {
+    ALLOC(w.z, pl->z_el * sizeof(double2));
+    CK(cudaMemsetAsync(w.z, 0, pl->z_el * sizeof(double2), w.st));
+  }
+  if (!w.scratch) ALLOC(w.scratch, pl->z_el * sizeof(double2));
   return FTOEP_OK;
 }
 
@@ -758,6 +840,109 @@ ftoep_status setup_problem(ftoep_plan pl, Prob& pb) {
   return FTOEP_OK;
 }
 
+// Work of one pair's chain, in n log2 n units: nblk block solves (length 2B) and the
+// cross-block convolutions (length 2s, s = B 2^ctz(v), v = 1 .. nblk-1).
+double chain_pair_cost(const Prob& pb) {
+  auto c = [](double n) { return n * std::log2(n); };
+  double t = pb.nblk * c(2.0 * pb.B);
+  for (int v = 1; v < pb.nblk; ++v) t += c(2.0 * (double)((int64_t)pb.B << ctz64(v)));
+  return t;
+}
+
+size_t pair_bytes(const Prob& pb) { return (size_t)pb.P * pb.Np * velem(pb.prec); }
+
+// Chain schedule set-up: per precision the kernel's shared memory, resident grid and
+// four-step scratch; problems in groups whose pair arrays fit the memory budget (longest
+// chains first), each group with its device descriptors and its item list (pairs, longest
+// chains first); one work counter per chain launch.
+ftoep_status setup_chain(ftoep_plan pl) {
+  int nsm = 0;
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, pl->device));
+  for (int pi = 0; pi < 2; ++pi) {
+    const Prec pr = pi == 0 ? P64 : P32;
+    int maxB = 0;
+    int64_t scr = 0;
+    bool any = false;
+    for (auto& pb : pl->probs) {
+      if (pb.prec != pr) continue;
+      any = true;
+      maxB = std::max(maxB, pb.B);
+      for (int v = 1; v < pb.nblk; ++v) {
+        const int64_t n = (int64_t)2 * ((int64_t)pb.B << ctz64(v));
+        if (n > nsmem_for(pr)) scr = std::max(scr, n);
+      }
+    }
+    if (!any) continue;
+    const size_t smem = chain_smem_bytes(pr, maxB);
+    const int nb = chain_blocks_per_sm(pr, smem);
+    if (nb < 1) return fail(pl, FTOEP_ECUDA, "chain kernel: no block fits an SM with %zu bytes of shared memory", smem);
+    pl->chain_smem[pi] = smem;
+    pl->chain_grid[pi] = nb * nsm;
+    pl->chain_scr_el[pi] = scr;
+    if (scr) ALLOC(pl->chain_scr[pi], (size_t)pl->chain_grid[pi] * scr * velem(pr));
+  }
+  // memory budget of one group's pair arrays: half of what is free, at most 32 GiB, at
+  // least the largest problem's
+  size_t fr = 0, tot = 0;
+  CK(cudaMemGetInfo(&fr, &tot));
+  size_t budget = std::min<size_t>(fr / 2, (size_t)32 << 30);
+  if (const char* eb = getenv("FTOEP_CHAIN_BUDGET")) {  // bytes; a smaller budget, more groups
+    const long long v = atoll(eb);
+    if (v > 0) budget = std::min<size_t>(budget, (size_t)v);
+  }
+  std::vector<int> order(pl->probs.size());
+  for (size_t i = 0; i < order.size(); ++i) {
+    order[i] = (int)i;
+    pl->probs[i].pair_cost = chain_pair_cost(pl->probs[i]);
+    budget = std::max(budget, pair_bytes(pl->probs[i]) + 256);
+  }
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return pl->probs[x].pair_cost > pl->probs[y].pair_cost; });
+  size_t gmax = 0;
+  for (int i : order) {
+    Prob& pb = pl->probs[i];
+    const size_t b = (pair_bytes(pb) + 255) / 256 * 256;
+    if (pl->groups.empty() || pl->groups.back().bytes + b > budget) pl->groups.emplace_back();
+    ChainGroup& g = pl->groups.back();
+    pb.group = (int)pl->groups.size() - 1;
+    pb.zbyte = g.bytes;
+    g.bytes += b;
+    g.probs.push_back(i);
+    gmax = std::max(gmax, g.bytes);
+  }
+  ALLOC(pl->gz, gmax);
+  CK(cudaMemset(pl->gz, 0, gmax));
+  pl->ncounters = 2 * (int)pl->groups.size();
+  ALLOC(pl->counters, (size_t)pl->ncounters * sizeof(unsigned));
+  for (auto& g : pl->groups) {
+    std::vector<ChainProb> cp(g.probs.size());
+    std::vector<int2> items[2];
+    for (size_t k = 0; k < g.probs.size(); ++k) {
+      const Prob& pb = pl->probs[g.probs[k]];
+      ChainProb& c = cp[k];
+      c.z = (char*)pl->gz + pb.zbyte;
+      c.ld = pb.Np;
+      c.c1 = pb.c1;
+      c.lamtau = pb.lamtau;
+      c.spec = pb.spec;
+      c.Sf = pb.Sf;
+      c.nblk = pb.nblk;
+      c.logB = ilog2(pb.B);
+      const int pi = pb.prec == P64 ? 0 : 1;
+      for (int64_t q = 0; q < pb.P; ++q) items[pi].push_back(make_int2((int)k, (int)q));
+    }
+    ALLOC(g.d_probs, cp.size() * sizeof(ChainProb));
+    CK(cudaMemcpy(g.d_probs, cp.data(), cp.size() * sizeof(ChainProb), cudaMemcpyHostToDevice));
+    for (int pi = 0; pi < 2; ++pi) {
+      g.nitems[pi] = (int)items[pi].size();
+      if (!g.nitems[pi]) continue;
+      ALLOC(g.d_items[pi], items[pi].size() * sizeof(int2));
+      CK(cudaMemcpy(g.d_items[pi], items[pi].data(), items[pi].size() * sizeof(int2), cudaMemcpyHostToDevice));
+    }
+  }
+  return FTOEP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -771,6 +956,10 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
   for (int i = 0; i < nprob; ++i) TRY(validate(probs[i], i, tune));
   ftoep_plan pl = new ftoep_plan_s();
   pl->stream = (cudaStream_t)cuda_stream;
+  {  // host-side fault injection (see ftoep_plan_s::fail_after)
+    const char* fa = getenv("FTOEP_FAIL_ALLOC_AFTER");
+    pl->fail_after = (fa && *fa) ? atol(fa) : -1;
+  }
   ftoep_status st = FTOEP_OK;
   auto bail = [&](ftoep_status s) {
     g_create_error = pl->err;
@@ -906,23 +1095,31 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
       return bail(FTOEP_ECUDA);
     }
   }
+  pl->sched = (tune && tune->scheduler) ? tune->scheduler : (nprob > 1 ? FTOEP_SCHED_CHAIN : FTOEP_SCHED_LEVELS);
   for (auto& w : pl->ws) {
-    if ((st = dalloc(pl, &w.z, pl->z_el * sizeof(double2))) != FTOEP_OK) return bail(st);
-    if ((st = dalloc(pl, &w.scratch, pl->z_el * sizeof(double2))) != FTOEP_OK) return bail(st);
+    // the chain schedule solves in group pair arrays: the per-level arrays of the streams
+    // are allocated on first use (adjoint), except the first stream's, which the set-up
+    // of the block inverses uses
+    if (pl->sched == FTOEP_SCHED_LEVELS || &w == &pl->ws[0]) {
+      if ((st = dalloc(pl, &w.z, pl->z_el * sizeof(double2))) != FTOEP_OK) return bail(st);
+      if (cudaMemsetAsync(w.z, 0, pl->z_el * sizeof(double2), w.st) != cudaSuccess) {
+        cudaGetLastError();
+        pl->err = "workspace clear failed";
+        return bail(FTOEP_ECUDA);
+      }
+    }
+    if (pl->sched == FTOEP_SCHED_LEVELS &&
+        (st = dalloc(pl, &w.scratch, pl->z_el * sizeof(double2))) != FTOEP_OK) return bail(st);
     if ((st = dalloc(pl, (void**)&w.zmv, pl->mv_el * sizeof(double2))) != FTOEP_OK) return bail(st);
     if ((st = dalloc(pl, (void**)&w.scratch_mv, 2 * pl->mv_el * sizeof(double2))) != FTOEP_OK) return bail(st);
     if ((st = dalloc(pl, (void**)&w.r, pl->r_el * sizeof(double))) != FTOEP_OK) return bail(st);
     if ((st = dalloc(pl, (void**)&w.prefix, pl->p_el * sizeof(double2))) != FTOEP_OK) return bail(st);
     if ((st = dalloc(pl, (void**)&w.dpart, kDotBlocks * sizeof(double))) != FTOEP_OK) return bail(st);
-    if (cudaMemsetAsync(w.z, 0, pl->z_el * sizeof(double2), w.st) != cudaSuccess) {
-      cudaGetLastError();
-      pl->err = "workspace clear failed";
-      return bail(FTOEP_ECUDA);
-    }
   }
   if ((st = dalloc(pl, (void**)&pl->dscal, (size_t)nprob * sizeof(double))) != FTOEP_OK) return bail(st);
   for (auto& pb : pl->probs)
     if ((st = setup_problem(pl, pb)) != FTOEP_OK) return bail(st);
+  if (pl->sched == FTOEP_SCHED_CHAIN && (st = setup_chain(pl)) != FTOEP_OK) return bail(st);
   if (cudaDeviceSynchronize() != cudaSuccess) {
     cudaGetLastError();
     pl->err = "plan set-up failed";
@@ -946,18 +1143,31 @@ ftoep_status ftoep_weights(ftoep_plan pl, int iprob, double* a, double* dadgamma
 
 namespace {
 
-// Every problem of the plan on its stream, forked from and joined back to the caller's.
-ftoep_status solve_all(ftoep_plan pl, const double* f, double* u, const double* u0, const double* phi, bool host) {
+// The workspace a problem runs with: its stream's, on that stream -- or, while the
+// instrumentation is on, on the caller's stream, so that the event times of the kernel
+// classes do not overlap (the workspaces stay distinct; the stream only orders them).
+Ws ws_for(ftoep_plan pl, const Prob& pb) {
+  Ws w = pl->ws[pb.stream];
+  if (pl->prof_on) w.st = pl->stream;
+  return w;
+}
+
+// Every problem of the plan on its stream, per-level launches, forked from and joined back
+// to the caller's.
+ftoep_status solve_all_levels(ftoep_plan pl, const double* f, double* u, const double* u0, const double* phi,
+                              bool host) {
   TRY(fork_streams(pl));
   for (auto& pb : pl->probs) {
-    Ws& w = pl->ws[pb.stream];
+    Ws& wr = pl->ws[pb.stream];
+    TRY(ensure_level_ws(pl, wr));
+    if (host) TRY(ensure_staging(pl, wr));
+    Ws w = ws_for(pl, pb);
     cudaStream_t st = w.st;
     const double* pf = f + pb.foff;
     double* pu = u + pb.foff;
     const double* pu0 = u0 ? u0 + pb.voff : nullptr;
     const double* pphi = phi ? phi + pb.voff : nullptr;
     if (host) {
-      TRY(ensure_staging(pl, w));
       const size_t bytes = (size_t)pb.M * pb.N * sizeof(double);
       CK(cudaMemcpyAsync(w.stage_in, pf, bytes, cudaMemcpyDefault, st));
       if (pu0) {
@@ -976,6 +1186,131 @@ ftoep_status solve_all(ftoep_plan pl, const double* f, double* u, const double* 
   }
   TRY(join_streams(pl));
   return FTOEP_OK;
+}
+
+// One persistent chain launch over the pairs of one precision of a group, on the caller's
+// stream (after zeroing its work counter).
+ftoep_status chain_launch(ftoep_plan pl, int gi, int pi, int phase) {
+  ChainGroup& g = pl->groups[gi];
+  if (!g.nitems[pi]) return FTOEP_OK;
+  const Prec pr = pi == 0 ? P64 : P32;
+  cudaStream_t st = pl->stream;
+  unsigned* counter = pl->counters + 2 * gi + phase;
+  CK(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
+  ChainArgs a{};
+  a.probs = g.d_probs;
+  a.items = g.d_items[pi];
+  a.nitems = g.nitems[pi];
+  a.counter = counter;
+  a.scratch = pl->chain_scr[pi];
+  a.scratch_per_block = pl->chain_scr_el[pi];
+  a.smem_elems = (int)(pl->chain_smem[pi] / velem(pr));
+  a.nsmem = nsmem_for(pr);
+  a.tw = tw_of(pl, pr);
+  const int grid = std::min(pl->chain_grid[pi], g.nitems[pi]);
+  LAUNCH(FTOEP_K_CHAIN, launch_chain(pr, a, grid, pl->chain_smem[pi], st));
+  return FTOEP_OK;
+}
+
+// Host buffers of one problem through its stream's staging arrays.
+struct Staged {
+  const double *f = nullptr, *u0 = nullptr, *phi = nullptr;
+  double* u = nullptr;
+};
+ftoep_status stage_inputs(ftoep_plan pl, Ws& w, const Prob& pb, const double* f, const double* u0,
+                          const double* phi, Staged* out) {
+  cudaStream_t st = w.st;
+  CK(cudaMemcpyAsync(w.stage_in, f, (size_t)pb.M * pb.N * sizeof(double), cudaMemcpyDefault, st));
+  out->f = w.stage_in;
+  out->u = w.stage_out;
+  if (u0) {
+    CK(cudaMemcpyAsync(w.stage_v0, u0, pb.M * sizeof(double), cudaMemcpyDefault, st));
+    out->u0 = w.stage_v0;
+  }
+  if (phi) {
+    CK(cudaMemcpyAsync(w.stage_v1, phi, pb.M * sizeof(double), cudaMemcpyDefault, st));
+    out->phi = w.stage_v1;
+  }
+  return FTOEP_OK;
+}
+
+// Chain schedule: per group of problems whose pair arrays are resident together --
+//   1. every problem: right-hand side + forward sine transform into its pair array
+//      (internal streams);
+//   2. one persistent chain launch per precision solves every pair of the group;
+//   3. every problem: inverse transform + time sums (double: done); mixed: residual and
+//      its forward transform;
+//   4. mixed: one chain launch solves the correction of every pair;
+//   5. mixed: inverse transform, u += tau cumsum.
+// Host buffers go through the streams' staging arrays one problem at a time: f is copied
+// in for steps 1 and 3, u is copied out after step 3 and again, updated, after step 5.
+ftoep_status solve_all_chain(ftoep_plan pl, const double* f, double* u, const double* u0, const double* phi,
+                             bool host) {
+  if (host)
+    for (auto& w : pl->ws) TRY(ensure_staging(pl, w));
+  for (size_t gi = 0; gi < pl->groups.size(); ++gi) {
+    ChainGroup& g = pl->groups[gi];
+    bool mixed = false;
+    TRY(fork_streams(pl));
+    for (int i : g.probs) {
+      Prob& pb = pl->probs[i];
+      Ws w = ws_for(pl, pb);
+      void* z = (char*)pl->gz + pb.zbyte;
+      const double* pu0 = u0 ? u0 + pb.voff : nullptr;
+      const double* pphi = phi ? phi + pb.voff : nullptr;
+      mixed |= pb.prec != P64;
+      if (host) {
+        Staged sg;
+        TRY(stage_inputs(pl, w, pb, f + pb.foff, pu0, pphi, &sg));
+        TRY(rhs_forward(pl, w, pb, z, sg.f, sg.u0, sg.phi));
+      } else {
+        TRY(rhs_forward(pl, w, pb, z, f + pb.foff, pu0, pphi));
+      }
+    }
+    TRY(join_streams(pl));
+    for (int pi = 0; pi < 2; ++pi) TRY(chain_launch(pl, (int)gi, pi, 0));
+    TRY(fork_streams(pl));
+    for (int i : g.probs) {
+      Prob& pb = pl->probs[i];
+      Ws w = ws_for(pl, pb);
+      void* z = (char*)pl->gz + pb.zbyte;
+      const double* pu0 = u0 ? u0 + pb.voff : nullptr;
+      const double* pphi = phi ? phi + pb.voff : nullptr;
+      if (host) {
+        Staged sg;
+        TRY(stage_inputs(pl, w, pb, f + pb.foff, pu0, pphi, &sg));
+        TRY(after_first_solve(pl, w, pb, z, sg.f, sg.u, sg.u0, sg.phi));
+        CK(cudaMemcpyAsync(u + pb.foff, sg.u, (size_t)pb.M * pb.N * sizeof(double), cudaMemcpyDefault, w.st));
+      } else {
+        TRY(after_first_solve(pl, w, pb, z, f + pb.foff, u + pb.foff, pu0, pphi));
+      }
+    }
+    TRY(join_streams(pl));
+    if (!mixed) continue;
+    TRY(chain_launch(pl, (int)gi, 1, 1));
+    TRY(fork_streams(pl));
+    for (int i : g.probs) {
+      Prob& pb = pl->probs[i];
+      if (pb.prec == P64) continue;
+      Ws w = ws_for(pl, pb);
+      void* z = (char*)pl->gz + pb.zbyte;
+      if (host) {
+        const size_t bytes = (size_t)pb.M * pb.N * sizeof(double);
+        CK(cudaMemcpyAsync(w.stage_out, u + pb.foff, bytes, cudaMemcpyDefault, w.st));
+        TRY(after_correction(pl, w, pb, z, w.stage_out));
+        CK(cudaMemcpyAsync(u + pb.foff, w.stage_out, bytes, cudaMemcpyDefault, w.st));
+      } else {
+        TRY(after_correction(pl, w, pb, z, u + pb.foff));
+      }
+    }
+    TRY(join_streams(pl));
+  }
+  return FTOEP_OK;
+}
+
+ftoep_status solve_all(ftoep_plan pl, const double* f, double* u, const double* u0, const double* phi, bool host) {
+  if (pl->sched == FTOEP_SCHED_CHAIN) return solve_all_chain(pl, f, u, u0, phi, host);
+  return solve_all_levels(pl, f, u, u0, phi, host);
 }
 
 constexpr size_t kMaxGraphs = 4;

@@ -202,6 +202,34 @@ struct BlockInvArgs {
 };
 int launch_block_inverse(Prec prec, const BlockInvArgs& a, cudaStream_t st);
 
+// Persistent per-pair solve (chain.cu): one launch runs the whole time recursion (block
+// solves and every cross-block level) of every listed pair, one pair per block at a time.
+struct ChainProb {
+  void* z;                 // pairs [P][ld] of the problem, precision of the launch
+  int64_t ld;
+  const void* c1;          // packed block-inverse spectra [P][2B]
+  const double2* lamtau;   // per pair lambda*tau
+  const void* spec;        // level spectra (level s at offset 2(s - Sf))
+  int64_t Sf;
+  int nblk, logB;
+};
+struct ChainArgs {
+  const ChainProb* probs;
+  const int2* items;        // (index into probs, pair), longest chains first
+  int nitems;
+  unsigned* counter;        // next item; zero at launch
+  void* scratch;            // four-step scratch, scratch_per_block elements per block
+  int64_t scratch_per_block;
+  int smem_elems;           // dynamic shared memory in elements of the launch precision
+  int nsmem;                // largest shared-memory convolution length (nsmem_for)
+  const void* tw;
+};
+// Dynamic shared memory of the chain kernel for block lengths up to maxB.
+size_t chain_smem_bytes(Prec prec, int maxB);
+// Resident blocks per SM of the chain kernel with that shared memory (0 on failure).
+int chain_blocks_per_sm(Prec prec, size_t smem);
+int launch_chain(Prec prec, const ChainArgs& a, int grid, size_t smem, cudaStream_t st);
+
 // Largest shared-memory FFT length of each precision.
 int nsmem_for(Prec prec);
 // Opt a kernel in to `bytes` of dynamic shared memory (once per kernel and size).

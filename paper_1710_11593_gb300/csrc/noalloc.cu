@@ -22,6 +22,10 @@
 // address is looked up with cudaGetSymbolAddress and the twiddle tables are written by a
 // kernel; the first call on each device should therefore come before any stream
 // capture.  No cudaMalloc, cudaFree or allocating library routine is called, ever.
+// The cached address and the twiddle tables belong to the device's context as it was at
+// set-up: a device reset (cudaDeviceReset) destroys both and is not supported while the
+// library is loaded.
+#include <cstdio>
 #include <mutex>
 
 #include "../../include/ftoep.h"
@@ -95,6 +99,26 @@ ftoep_status noalloc_setup(double2** base) {
   return FTOEP_OK;
 }
 
+// Device (or managed) memory: the kernels dereference the pointers directly.  Host
+// memory, pinned or not, is refused: this entry point stages nothing.
+bool on_device(const void* ptr) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();  // the query's own error (unknown pointer), not a pending one
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+ftoep_status launch_failed(const char* step) {
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return FTOEP_OK;
+  char buf[256];
+  snprintf(buf, sizeof(buf), "ftoep_matvec_noalloc: %s launch failed: %s", step, cudaGetErrorString(e));
+  set_global_error(buf);
+  return FTOEP_ECUDA;
+}
+
 }  // namespace
 
 extern "C" ftoep_status ftoep_matvec_noalloc(const double* a, int64_t N, const double* x, double* y,
@@ -116,6 +140,21 @@ extern "C" ftoep_status ftoep_matvec_noalloc(const double* a, int64_t N, const d
     set_global_error("ftoep_matvec_noalloc: x and y overlap");
     return FTOEP_EINVAL;
   }
+  {  // an error left by earlier work is the caller's: report it without clearing it
+    const cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) {
+      char buf[256];
+      snprintf(buf, sizeof(buf), "ftoep_matvec_noalloc: a CUDA error is pending from earlier work: %s",
+               cudaGetErrorString(e));
+      set_global_error(buf);
+      return FTOEP_ECUDA;
+    }
+  }
+  if (!on_device(a) || !on_device(x) || !on_device(y)) {
+    set_global_error("ftoep_matvec_noalloc: a, x and y must be device (or managed) memory; host buffers go "
+                     "through ftoep_matvec");
+    return FTOEP_EINVAL;
+  }
   double2* base = nullptr;
   ftoep_status s = noalloc_setup(&base);
   if (s != FTOEP_OK) return s;
@@ -135,6 +174,7 @@ extern "C" ftoep_status ftoep_matvec_noalloc(const double* a, int64_t N, const d
   sa.tw64 = base + kOffTw;
   sa.scratch64 = base + kOffSpecScratch;
   launch_spectrum(P64, sa, st);
+  if ((s = launch_failed("kernel spectrum")) != FTOEP_OK) return s;
   for (int64_t l0 = 0; l0 < nlines; l0 += 2 * kNoAllocPairs) {
     const int64_t nl = (nlines - l0 < 2 * kNoAllocPairs) ? nlines - l0 : 2 * kNoAllocPairs;
     PackArgs pa{};
@@ -147,6 +187,7 @@ extern "C" ftoep_status ftoep_matvec_noalloc(const double* a, int64_t N, const d
     pa.reverse = transpose ? 1 : 0;
     pa.mode = 0;
     launch_pack(P64, pa, st);
+    if ((s = launch_failed("packing")) != FTOEP_OK) return s;
     ConvArgs ca{};
     ca.zin = base + kOffPairs;
     ca.zout = base + kOffPairs;
@@ -160,12 +201,9 @@ extern "C" ftoep_status ftoep_matvec_noalloc(const double* a, int64_t N, const d
     ca.tw = base + kOffTw;
     ca.scratch = base + kOffScratch;
     launch_conv(P64, ca, st);
+    if ((s = launch_failed("circulant convolution")) != FTOEP_OK) return s;
     launch_unpack(P64, pa, st);
-  }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    set_global_error("ftoep_matvec_noalloc: kernel launch failed");
-    return FTOEP_ECUDA;
+    if ((s = launch_failed("unpacking")) != FTOEP_OK) return s;
   }
   return FTOEP_OK;
 }

@@ -12,6 +12,7 @@
 
 #include <cooperative_groups.h>
 
+#include "conv_body.cuh"
 #include "convert.cuh"
 #include "fft.cuh"
 #include "fftr.cuh"
@@ -22,9 +23,6 @@ namespace ftoep {
 namespace {
 
 constexpr int kThreads = 256;
-
-template <typename T>
-using Vt = typename VecOf<T>::type;
 
 // Host-side copy of the pass radix of each arithmetic type (fftr.cuh EngineTraits).
 template <typename T> struct EngineTraitsHost;
@@ -58,21 +56,6 @@ __device__ __forceinline__ double re_of(float2 v) { return (double)v.x; }
 __device__ __forceinline__ double im_of(float2 v) { return (double)v.y; }
 __device__ __forceinline__ double re_of(ff2 v) { return (double)v.xh + (double)v.xl; }
 __device__ __forceinline__ double im_of(ff2 v) { return (double)v.yh + (double)v.yl; }
-
-// Pointwise product of spectrum values with a kernel spectrum in the same storage order
-// (the op of fftr_middle): x[j] *= spec[pos0 + j].
-template <typename V>
-struct SpecMul {
-  const V* __restrict__ spec;
-  template <class X, class RR>
-  __device__ __forceinline__ void operator()(int t, int pos0, X& x, RR) const {
-    (void)t;
-    static_for<0, RR::value>([&](auto JJ) {
-      constexpr int j = decltype(JJ)::value;
-      x[j] = cmul(x[j], spec[pos0 + j]);
-    });
-  }
-};
 
 // ------------------------------------------------------------------ sine transform
 //
@@ -841,10 +824,6 @@ __global__ void sum_kernel(const double* partial, int n, double* out) {
 
 // ------------------------------------------------------------------ four-step split
 
-struct Split {
-  int logn, logn1, logn2;
-};
-inline Split split_of(int logn) { return Split{logn, logn / 2, logn - logn / 2}; }
 
 template <typename T>
 int four_step_cols(int logn1) {
@@ -928,163 +907,53 @@ void spectrum_launch(const SpecArgs& a, cudaStream_t st) {
 
 // ------------------------------------------------------------------ convolution
 
-// Read-modify-write storers of the last inverse pass (mode 0: subtract the upper half of
-// the cyclic result from the output).
-template <typename V>
-struct SubUpper {  // zo[e - s] -= v for e >= s
-  V* __restrict__ zo;
-  int s;
-  __device__ __forceinline__ V fetch(int, int e) const { return e >= s ? zo[e - s] : vzero<V>(); }
-  __device__ __forceinline__ void operator()(int, int e, const V& v, const V& f) const {
-    if (e >= s) zo[e - s] = csub(f, v);
-  }
-};
-template <typename V>
-struct SubUpperCols {  // column t: zo[(e - h1) n2 + t] -= v for e >= h1
-  V* __restrict__ zo;
-  int h1, n2;
-  __device__ __forceinline__ V fetch(int t, int e) const {
-    return e >= h1 ? zo[(int64_t)(e - h1) * n2 + t] : vzero<V>();
-  }
-  __device__ __forceinline__ void operator()(int t, int e, const V& v, const V& f) const {
-    if (e >= h1) zo[(int64_t)(e - h1) * n2 + t] = csub(f, v);
-  }
-};
-
-// One block per pair; the whole length-n transform in shared memory.  The first forward
-// pass reads the input half straight from global memory, the last forward pass, the
-// product with the kernel spectrum and the first inverse pass run fused in registers, and
-// the last inverse pass writes (mode 0: subtracts) the wanted half straight to global.
+// Per-level kernels over pairs (blockIdx.y or blockIdx.x) and column or row groups; the
+// bodies are in conv_body.cuh.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 3) conv_smem_kernel(ConvArgs A) {
   typedef Vt<T> V;
   extern __shared__ __align__(16) unsigned char smraw[];
-  V* sm = reinterpret_cast<V*>(smraw);
-  const int logn = A.logn, s = 1 << (logn - 1);
   const int64_t p = blockIdx.x;
-  const V* __restrict__ zin = (const V*)A.zin + p * A.ld_in + A.in_off;
-  V* __restrict__ zo = (V*)A.zout + p * A.ld_out + A.out_off;
-  const V* __restrict__ tw = (const V*)A.tw;
-  const SmLayout L = sm_layout<V>(logn);
-  const int np = fftr_npasses<V>(logn);
-  fftr_pass<V, true, false, true>(0, logn, 1, tw, true, [&](int, int e) { return zin[e]; }, SmPut<V>{sm, L});
-  __syncthreads();
-  if (np < 2) {  // a single pass: plain product in shared memory
-    for (int k = threadIdx.x; k < 2 * s; k += blockDim.x) {
-      const int q = sm_pos<V>(L, 0, k);
-      sm[q] = cmul(sm[q], ((const V*)A.spec)[k]);
-    }
-    __syncthreads();
-  } else {
-    fftr_passes<V, true>(sm, logn, 1, tw, 1, np - 1, false);
-    fftr_middle<V>(sm, logn, 1, SpecMul<V>{(const V*)A.spec});
-    __syncthreads();
-    fftr_passes<V, false>(sm, logn, 1, tw, 1, np - 1, false);
-  }
-  if (A.mode == 0) {
-    fftr_pass<V, false, false, false, true>(np - 1, logn, 1, tw, false, SmAt<V>{sm, L}, SubUpper<V>{zo, s});
-  } else {
-    fftr_pass<V, false>(np - 1, logn, 1, tw, false, SmAt<V>{sm, L}, [&](int, int e, const V& v) {
-      if (e < s) zo[e] = v;
-    });
-  }
+  conv_smem_body<T>(reinterpret_cast<V*>(smraw), (const V*)A.zin + p * A.ld_in + A.in_off,
+                    (V*)A.zout + p * A.ld_out + A.out_off, A.logn, A.mode, (const V*)A.spec, (const V*)A.tw);
 }
 
-// Four-step: n = n1*n2, index j = j1*n2 + j2.  Step A transforms C columns (over j1) per
-// block, applies W_n^{j2 k1} and writes the scratch; step B transforms `rows` rows (over
-// j2) per block, multiplies by the spectrum (stored in the same order), inverts the rows
-// and removes the twiddle; step C inverts the columns.  Column transforms leave k1 in
-// bit-reversed row order, which the twiddles account for.  Column kernels map consecutive
-// threads to consecutive columns (coalesced global access); the first and last passes of
-// every kernel read or write global memory directly.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) conv_col_fwd_kernel(ConvArgs A, int logn1, int logn2, int C) {
   typedef Vt<T> V;
   extern __shared__ __align__(16) unsigned char smraw[];
-  V* sm = reinterpret_cast<V*>(smraw);
-  const int n2 = 1 << logn2, logn = logn1 + logn2, n = 1 << logn;
-  const int c0 = blockIdx.x * C;
   const int64_t p = blockIdx.y;
-  const V* __restrict__ zin = (const V*)A.zin + p * A.ld_in + A.in_off + c0;
-  V* __restrict__ sc = (V*)A.scratch + p * (int64_t)n + c0;
-  const V* __restrict__ tw = (const V*)A.tw;
-  const V* __restrict__ twn = tw + (n - 2);
-  const SmLayout L = sm_layout<V>(logn1);
-  const int np = fftr_npasses<V>(logn1);
-  fftr_pass<V, true, true, true>(0, logn1, C, tw, true, [&](int t, int e) { return zin[(int64_t)e * n2 + t]; },
-                                 SmPut<V>{sm, L});
-  __syncthreads();
-  fftr_passes<V, true, true>(sm, logn1, C, tw, 1, np - 1, false);
-  fftr_pass<V, true, true>(np - 1, logn1, C, tw, false, SmAt<V>{sm, L}, [&](int t, int e, const V& v) {
-    const int k1 = brev(e, logn1);
-    sc[(int64_t)e * n2 + t] = cmul(v, twn[((int64_t)(c0 + t) * k1) & (n - 1)]);
-  });
+  const int64_t n = (int64_t)1 << (logn1 + logn2);
+  conv_col_fwd_body<T>(reinterpret_cast<V*>(smraw), (const V*)A.zin + p * A.ld_in + A.in_off,
+                       (V*)A.scratch + p * n, logn1, logn2, C, (int)blockIdx.x * C, (const V*)A.tw);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 3) conv_row_kernel(ConvArgs A, int logn1, int logn2, int rows) {
   typedef Vt<T> V;
   extern __shared__ __align__(16) unsigned char smraw[];
-  V* sm = reinterpret_cast<V*>(smraw);
-  const int n2 = 1 << logn2, logn = logn1 + logn2, n = 1 << logn;
-  const int r0 = blockIdx.x * rows;
   const int64_t p = blockIdx.y;
-  V* __restrict__ sc = (V*)A.scratch + p * (int64_t)n + (int64_t)r0 * n2;
-  const V* __restrict__ tw = (const V*)A.tw;
-  const V* __restrict__ twn = tw + (n - 2);
-  const SmLayout L = sm_layout<V>(logn2);
-  const int np = fftr_npasses<V>(logn2);
-  fftr_pass<V, true, false, true>(0, logn2, rows, tw, false, [&](int t, int e) { return sc[t * n2 + e]; },
-                                  SmPut<V>{sm, L});
-  __syncthreads();
-  fftr_passes<V, true>(sm, logn2, rows, tw, 1, np - 1, false);
-  const V* __restrict__ spec = (const V*)A.spec + (int64_t)r0 * n2;
-  fftr_middle<V>(sm, logn2, rows, [&](int t, int pos0, auto& x, auto RR) {
-    SpecMul<V>{spec + t * n2}(t, pos0, x, RR);
-  });
-  __syncthreads();
-  fftr_passes<V, false>(sm, logn2, rows, tw, 1, np - 1, false);
-  fftr_pass<V, false>(np - 1, logn2, rows, tw, false, SmAt<V>{sm, L}, [&](int t, int e, const V& v) {
-    const int k1 = brev(r0 + t, logn1);
-    sc[t * n2 + e] = cmulc(v, twn[((int64_t)e * k1) & (n - 1)]);
-  });
+  const int64_t n = (int64_t)1 << (logn1 + logn2);
+  conv_row_body<T>(reinterpret_cast<V*>(smraw), (V*)A.scratch + p * n, (const V*)A.spec, logn1, logn2, rows,
+                   (int)blockIdx.x * rows, (const V*)A.tw);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) conv_col_inv_kernel(ConvArgs A, int logn1, int logn2, int C) {
   typedef Vt<T> V;
   extern __shared__ __align__(16) unsigned char smraw[];
-  V* sm = reinterpret_cast<V*>(smraw);
-  const int n2 = 1 << logn2, logn = logn1 + logn2, n = 1 << logn, h1 = 1 << (logn1 - 1);
-  const int c0 = blockIdx.x * C;
   const int64_t p = blockIdx.y;
-  const V* __restrict__ sc = (const V*)A.scratch + p * (int64_t)n + c0;
-  V* __restrict__ zo = (V*)A.zout + p * A.ld_out + A.out_off + c0;
-  const V* __restrict__ tw = (const V*)A.tw;
-  const SmLayout L = sm_layout<V>(logn1);
-  const int np = fftr_npasses<V>(logn1);
-  fftr_pass<V, false, true, true>(0, logn1, C, tw, false, [&](int t, int e) { return sc[(int64_t)e * n2 + t]; },
-                                  SmPut<V>{sm, L});
-  __syncthreads();
-  fftr_passes<V, false, true>(sm, logn1, C, tw, 1, np - 1, false);
-  if (A.mode == 0) {
-    fftr_pass<V, false, true, false, true>(np - 1, logn1, C, tw, false, SmAt<V>{sm, L},
-                                           SubUpperCols<V>{zo, h1, n2});
-  } else {
-    fftr_pass<V, false, true>(np - 1, logn1, C, tw, false, SmAt<V>{sm, L}, [&](int t, int e, const V& v) {
-      if (e < h1) zo[(int64_t)e * n2 + t] = v;
-    });
-  }
+  const int64_t n = (int64_t)1 << (logn1 + logn2);
+  conv_col_inv_body<T>(reinterpret_cast<V*>(smraw), (const V*)A.scratch + p * n,
+                       (V*)A.zout + p * A.ld_out + A.out_off, logn1, logn2, C, (int)blockIdx.x * C, A.mode,
+                       (const V*)A.tw);
 }
 
 // Columns per block of the four-step column kernels (power of two): 128-byte row
 // segments, at most 64 KB of shared memory.
 template <typename T>
 int fourstep_cols(int logn1, int logn2) {
-  int C = 128 / (int)sizeof(Vt<T>);
-  while (C > 2 && (size_t)C * ((size_t)1 << logn1) * sizeof(Vt<T>) > 64 * 1024) C >>= 1;
-  while (C > 1 && C > (1 << logn2)) C >>= 1;
-  return C;
+  return fourstep_cols_for(logn1, logn2, (int)sizeof(Vt<T>), 64 * 1024 / (int)sizeof(Vt<T>));
 }
 // Rows per block of the row kernel: about 16 elements per thread per pass.
 template <typename T>

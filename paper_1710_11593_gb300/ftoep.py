@@ -25,11 +25,14 @@ L1_SUBDIFFUSION, L1_HYPERBOLIC = 0, 1
 SPACE_NONE, SPACE_DIRICHLET_LAPLACIAN = 0, 1
 FP64, MIXED = 0, 1
 
+SCHED_AUTO, SCHED_LEVELS, SCHED_CHAIN = 0, 1, 2
+
 EXPORTS = ("ftoep_create", "ftoep_weights", "ftoep_solve", "ftoep_matvec", "ftoep_adjoint", "ftoep_profile",
-           "ftoep_profile_read", "ftoep_sync", "ftoep_last_error", "ftoep_destroy")
-K_BLOCK_SOLVE, K_CONV_SMEM, K_CONV_FOURSTEP, K_SINE, K_OTHER, K_RESIDUAL = range(6)
+           "ftoep_profile_read", "ftoep_matvec_noalloc", "ftoep_autotune", "ftoep_sync", "ftoep_last_error",
+           "ftoep_destroy")
+K_BLOCK_SOLVE, K_CONV_SMEM, K_CONV_FOURSTEP, K_SINE, K_OTHER, K_RESIDUAL, K_CHAIN = range(7)
 KERNEL_CLASSES = {K_BLOCK_SOLVE: "block_solve", K_CONV_SMEM: "conv_smem", K_CONV_FOURSTEP: "conv_fourstep",
-                  K_SINE: "sine", K_OTHER: "other", K_RESIDUAL: "residual"}
+                  K_SINE: "sine", K_OTHER: "other", K_RESIDUAL: "residual", K_CHAIN: "chain"}
 
 
 class FtoepError(RuntimeError):
@@ -46,7 +49,7 @@ class ftoep_problem(ctypes.Structure):
 
 class ftoep_tuning(ctypes.Structure):
     _fields_ = [("leaf", ctypes.c_int), ("fft_tile", ctypes.c_int), ("gemm_max_level", ctypes.c_int),
-                ("modes_per_cta", ctypes.c_int)]
+                ("scheduler", ctypes.c_int)]
 
 
 _lib = None
@@ -77,6 +80,7 @@ def load(path: Optional[str] = None):
     lib.ftoep_sync.argtypes = [vp]
     lib.ftoep_last_error.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.ftoep_destroy.argtypes = [vp]
+    lib.ftoep_matvec_noalloc.argtypes = [vp, i64, vp, vp, i64, ci, vp]
     for name in EXPORTS:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -150,7 +154,7 @@ def ftoep_create(problems: Sequence[ProblemSpec], tuning: Optional[dict] = None,
     tp = None
     if tuning:
         tp = ctypes.pointer(ftoep_tuning(int(tuning.get("leaf", 0)), int(tuning.get("fft_tile", 0)),
-                                         int(tuning.get("gemm_max_level", 0)), int(tuning.get("modes_per_cta", 0))))
+                                         int(tuning.get("gemm_max_level", 0)), int(tuning.get("scheduler", 0))))
     h = ctypes.c_void_p()
     st = current_stream_handle() if stream is None else stream
     rc = lib.ftoep_create(ctypes.byref(h), arr, len(problems), tp, ctypes.c_void_p(st))
@@ -188,11 +192,7 @@ def ftoep_profile_read(plan: int, kclass: int):
 
 def ftoep_matvec_noalloc(a, N: int, x, y, nlines: int, transpose: bool = False, stream: Optional[int] = None):
     """Allocation-free Toeplitz product (device pointers only, N <= 32768); see ftoep.h."""
-    lib = load()
-    fn = lib.ftoep_matvec_noalloc
-    fn.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
-                   ctypes.c_void_p]
-    fn.restype = ctypes.c_int
+    fn = load().ftoep_matvec_noalloc
     st = current_stream_handle() if stream is None else stream
     _check(fn(_ptr(a), int(N), _ptr(x), _ptr(y), int(nlines), int(bool(transpose)), ctypes.c_void_p(st)), None)
 
@@ -215,7 +215,7 @@ def ftoep_autotune(problems: Sequence[ProblemSpec], stream: Optional[int] = None
     rc = lib.ftoep_autotune(arr, len(problems), ctypes.c_void_p(st), ctypes.byref(out))
     _check(rc, None)
     return {"leaf": out.leaf, "fft_tile": out.fft_tile, "gemm_max_level": out.gemm_max_level,
-            "modes_per_cta": out.modes_per_cta}
+            "scheduler": out.scheduler}
 
 
 class Plan:

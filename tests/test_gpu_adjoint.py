@@ -157,3 +157,25 @@ def test_config5_adjoint_full(torch_ft, oracle):
     # gamma-gradient: mode-1 term
     grad_ref = oracle.gamma_gradient(0, g, uh[None, :], lam_1[None, :])
     assert abs(float(gt.grad) - grad_ref) <= 1e-9 * abs(grad_ref)
+
+
+def test_autograd_backward_twice_and_plan_reuse(torch_ft):
+    """retain_graph: a second backward pass through the same graph gives the same gradients
+    (the graph keeps its plan); a second forward pass of the same problem reuses the plan."""
+    torch, ftoep, ag = torch_ft
+    M, N, g = 15, 300, 0.4
+    f = torch.from_numpy(wl.random_field((M, N), seed=21)).cuda().requires_grad_(True)
+    gt = torch.tensor(g, dtype=torch.float64, requires_grad=True)
+    ag.clear_plan_cache()
+    u = ag.fractional_solve(f, gt)
+    loss = torch.sum(u[:, -1] ** 2)
+    loss.backward(retain_graph=True)
+    g1f, g1g = f.grad.clone(), gt.grad.clone()
+    f.grad = None
+    gt.grad = None
+    loss.backward()
+    assert torch.equal(f.grad, g1f) and torch.equal(gt.grad, g1g)
+    u2 = ag.fractional_solve(f, gt)
+    assert u2.grad_fn is not None and torch.equal(u2, u)
+    assert len(ag._plans) == 1
+    ag.clear_plan_cache()
