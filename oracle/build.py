@@ -17,7 +17,10 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
-    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu11", SRC, "-o", LIB + ".tmp", "-lm"]
+    # no contraction of products into FMAs: the error-free transformations of oracle.c
+    # (two-sum, FMA residuals) need every other operation rounded as written
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-std=gnu11", SRC, "-o", LIB + ".tmp",
+           "-lm"]
     if platform.machine() not in ("aarch64", "arm64"):
         cmd.append("-lquadmath")
     subprocess.run(cmd, check=True)

@@ -18,8 +18,13 @@
  *         (mu*G_0 + 2/h^2) u_j^n - (u_{j-1}^n + u_{j+1}^n)/h^2
  *             = f_j^n + mu*[ sum_{k=1}^{n-1} (G_{n-k-1} - G_{n-k}) u_j^k + G_{n-1} u_j^0 ]
  *     (mu = tau^-g / Gamma(2-g); the u^0 coefficient follows from expanding the L1
- *     quotient, see or_initial_weights()).  The history sum is plain double; the
- *     tridiagonal level solve is done in binary128 (see thomas_const()).
+ *     quotient, see or_initial_weights()).  The paper states no precision for these
+ *     sums; in this form the history terms carry tau^-g and cancel to the size of f, so
+ *     the coefficients and the marched values are kept as double-double pairs (hi + lo)
+ *     and the history sums are accumulated with error-free products and sums (the
+ *     double-double dot product of Ogita, Rump and Oishi, "Accurate sum and dot product",
+ *     2005); each level's right-hand side and the tridiagonal level solve are done in
+ *     binary128 (see dd_history() and thomas_const()).
  *   - The hyperbolic L1 scheme of Eq. 15 / Eq. 17 (1<g<2, c = tau^-g/Gamma(3-g)) with
  *     the advection term replaced by the central second difference, spatial term at
  *     level n and f at t_{n-1/2}:
@@ -175,20 +180,49 @@ int or_initial_weights(int kind, double g, double tau, int64_t N, double* w_u0, 
 
 /* Thomas algorithm for the constant tridiagonal system
  *   diag*x_j + off*(x_{j-1} + x_{j+1}) = r_j,  j = 0..M-1, x_{-1} = x_M = 0,
- * carried out in binary128 (r and x rounded to double on the way in and out).  With
- * diag ~ 2/h^2 >> mu the matrix has condition ~ (mu + 4/h^2)/(mu + pi^2), e.g. 1.6e3 at
- * h = 1/1024, mu = 2.6e3: a double sweep loses that factor times eps at every level.
- * cp, rq: scratch of length M.  Overwrites r with x. */
-static void thomas_const(int64_t M, qreal diag, qreal off, double* r, qreal* cp, qreal* rq) {
+ * carried out in binary128.  With diag ~ 2/h^2 >> mu the matrix has condition
+ * ~ (mu + 4/h^2)/(mu + pi^2), e.g. 1.6e3 at h = 1/1024, mu = 2.6e3: a double sweep loses
+ * that factor times eps at every level.  cp: scratch of length M.  Overwrites r with x. */
+static void thomas_const(int64_t M, qreal diag, qreal off, qreal* r, qreal* cp) {
   cp[0] = off / diag;
-  rq[0] = (qreal)r[0] / diag;
+  r[0] = r[0] / diag;
   for (int64_t j = 1; j < M; ++j) {
     qreal den = diag - off * cp[j - 1];
     cp[j] = off / den;
-    rq[j] = ((qreal)r[j] - off * rq[j - 1]) / den;
+    r[j] = (r[j] - off * r[j - 1]) / den;
   }
-  for (int64_t j = M - 2; j >= 0; --j) rq[j] -= cp[j] * rq[j + 1];
-  for (int64_t j = 0; j < M; ++j) r[j] = (double)rq[j];
+  for (int64_t j = M - 2; j >= 0; --j) r[j] -= cp[j] * r[j + 1];
+}
+
+/* Double-double arithmetic (error-free transformations, Knuth / Dekker with FMA). */
+static inline void two_sum(double a, double b, double* s, double* e) {
+  const double x = a + b;
+  const double z = x - a;
+  *e = (a - (x - z)) + (b - z);
+  *s = x;
+}
+
+/* sum_{i<n} (ch_i + cl_i)(xh_i + xl_i) as an unevaluated sum hi + lo, accurate to about
+ * 2^-104 of sum |c x| + 2^-53 of the result: the hi*hi products and their running sum
+ * are error-free (FMA residual, two-sum), the small cross terms are added plainly. */
+static void dd_dot(const double* ch, const double* cl, const double* xh, const double* xl, int64_t n, qreal* out) {
+  double s = 0.0, c = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    const double a = ch[i], al = cl[i];
+    const double p = a * xh[i];
+    const double pe = fma(a, xh[i], -p);
+    double t, te;
+    two_sum(s, p, &t, &te);
+    s = t;
+    c += te + pe + (a * xl[i] + al * xh[i]);
+  }
+  *out = (qreal)s + (qreal)c;
+}
+
+/* Split a binary128 value into a double pair. */
+static inline void q_split(qreal v, double* hi, double* lo) {
+  *hi = (double)v;
+  *lo = (double)(v - (qreal)*hi);
 }
 
 /*
@@ -205,52 +239,54 @@ int or_march(int kind, int space, double g, double T, double Lx, double lambda, 
     return OR_EINVAL;
   if (!(T > 0.0) || (space == 1 && !(Lx > 0.0))) return OR_EINVAL;
   const double tau = T / (double)N;
-  const double scale = or_scale(kind, g, tau);
-  double* coef = (double*)malloc(sizeof(double) * (size_t)N);
+  /* full left-hand coefficients a_j = scale*coef_j (binary128, split into double pairs),
+   * stored reversed so that the history sum of level n runs forward in memory:
+   * rh[N-1-j] + rl[N-1-j] = a_j */
+  double* rh = (double*)malloc(sizeof(double) * (size_t)N);
+  double* rl = (double*)malloc(sizeof(double) * (size_t)N);
   double* wu0 = (double*)malloc(sizeof(double) * (size_t)N);
   double* wphi = (double*)malloc(sizeof(double) * (size_t)N);
-  double* rhs = (double*)malloc(sizeof(double) * (size_t)M);
-  qreal* cp = (qreal*)malloc(sizeof(qreal) * (size_t)M);
+  double* ulo = (double*)malloc(sizeof(double) * (size_t)N * (size_t)M);
   qreal* rq = (qreal*)malloc(sizeof(qreal) * (size_t)M);
-  if (!coef || !wu0 || !wphi || !rhs || !cp || !rq) {
-    free(coef); free(wu0); free(wphi); free(rhs); free(cp); free(rq);
+  qreal* cp = (qreal*)malloc(sizeof(qreal) * (size_t)M);
+  if (!rh || !rl || !wu0 || !wphi || !ulo || !rq || !cp) {
+    free(rh); free(rl); free(wu0); free(wphi); free(ulo); free(rq); free(cp);
     return OR_ENOMEM;
   }
-  or_time_coeffs(kind, g, N, coef);
+  const qreal qs = q_scale(kind, (qreal)g, (qreal)tau);
+  for (int64_t j = 0; j < N; ++j) q_split(qs * q_coef(kind, j, (qreal)g), &rh[N - 1 - j], &rl[N - 1 - j]);
   or_initial_weights(kind, g, tau, N, wu0, wphi);
-  /* history weights h_j = -scale*coef_j for j >= 1: the right-hand side collects
-   * sum_{k=1}^{n-1} h_{n-k} u^k, which for kind 0 is mu*(G_{n-k-1} - G_{n-k}).
-   * The level matrix is formed in binary128 from the binary128 scale. */
+  /* level matrix: a_0 + 2/h^2 on the diagonal, -1/h^2 off it (binary128) */
   qreal diag, off;
-  const qreal qscale = q_scale(kind, (qreal)g, (qreal)tau) * q_coef(kind, 0, (qreal)g);
+  const qreal a0 = qs * q_coef(kind, 0, (qreal)g);
   if (space == 1) {
     qreal h = (qreal)Lx / (qreal)(M + 1);
-    diag = qscale + QLIT(2.0) / (h * h);
+    diag = a0 + QLIT(2.0) / (h * h);
     off = QLIT(-1.0) / (h * h);
   } else {
-    diag = qscale + (qreal)lambda;
+    diag = a0 + (qreal)lambda;
     off = QLIT(0.0);
   }
   if (nthreads < 1) nthreads = 1;
   for (int64_t n = 1; n <= N; ++n) {
+    /* r_j = f_j^n - sum_{k=1}^{n-1} a_{n-k} u_j^k (+ initial-data terms) */
 #pragma omp parallel for num_threads(nthreads) schedule(static)
     for (int64_t j = 0; j < M; ++j) {
-      const double* uj = u + j * N;
-      double s = 0.0;
-      for (int64_t k = 1; k <= n - 1; ++k) s += coef[n - k] * uj[k - 1];
-      double r = f[j * N + (n - 1)] - scale * s;
-      if (u0) r += wu0[n - 1] * u0[j];
-      if (phi) r += wphi[n - 1] * phi[j];
-      rhs[j] = r;
+      qreal s = QLIT(0.0);
+      if (n > 1) dd_dot(rh + (N - n), rl + (N - n), u + j * N, ulo + j * N, n - 1, &s);
+      qreal r = (qreal)f[j * N + (n - 1)] - s;
+      if (u0) r += (qreal)wu0[n - 1] * (qreal)u0[j];
+      if (phi) r += (qreal)wphi[n - 1] * (qreal)phi[j];
+      rq[j] = r;
     }
     if (space == 1) {
-      thomas_const(M, diag, off, rhs, cp, rq);
+      thomas_const(M, diag, off, rq, cp);
     } else {
-      for (int64_t j = 0; j < M; ++j) rhs[j] = (double)((qreal)rhs[j] / diag);
+      for (int64_t j = 0; j < M; ++j) rq[j] = rq[j] / diag;
     }
-    for (int64_t j = 0; j < M; ++j) u[j * N + (n - 1)] = rhs[j];
+    for (int64_t j = 0; j < M; ++j) q_split(rq[j], &u[j * N + (n - 1)], &ulo[j * N + (n - 1)]);
   }
-  free(coef); free(wu0); free(wphi); free(rhs); free(cp); free(rq);
+  free(rh); free(rl); free(wu0); free(wphi); free(ulo); free(rq); free(cp);
   return OR_OK;
 }
 
@@ -265,43 +301,45 @@ int or_adjoint_march(int kind, int space, double g, double T, double Lx, double 
   if (check_kind(kind, g) != OR_OK || (space != 0 && space != 1) || N < 1 || M < 1 || !gin || !lam)
     return OR_EINVAL;
   const double tau = T / (double)N;
-  const double scale = or_scale(kind, g, tau);
-  double* coef = (double*)malloc(sizeof(double) * (size_t)N);
-  double* rhs = (double*)malloc(sizeof(double) * (size_t)M);
-  qreal* cp = (qreal*)malloc(sizeof(qreal) * (size_t)M);
+  /* a_j = scale*coef_j as double pairs, in natural order (the sum of level n runs over
+   * k = n+1..N with weight a_{k-n}) */
+  double* ah = (double*)malloc(sizeof(double) * (size_t)N);
+  double* al = (double*)malloc(sizeof(double) * (size_t)N);
+  double* llo = (double*)malloc(sizeof(double) * (size_t)N * (size_t)M);
   qreal* rq = (qreal*)malloc(sizeof(qreal) * (size_t)M);
-  if (!coef || !rhs || !cp || !rq) {
-    free(coef); free(rhs); free(cp); free(rq);
+  qreal* cp = (qreal*)malloc(sizeof(qreal) * (size_t)M);
+  if (!ah || !al || !llo || !rq || !cp) {
+    free(ah); free(al); free(llo); free(rq); free(cp);
     return OR_ENOMEM;
   }
-  or_time_coeffs(kind, g, N, coef);
+  const qreal qs = q_scale(kind, (qreal)g, (qreal)tau);
+  for (int64_t j = 0; j < N; ++j) q_split(qs * q_coef(kind, j, (qreal)g), &ah[j], &al[j]);
   qreal diag, off;
-  const qreal qscale = q_scale(kind, (qreal)g, (qreal)tau) * q_coef(kind, 0, (qreal)g);
+  const qreal a0 = qs * q_coef(kind, 0, (qreal)g);
   if (space == 1) {
     qreal h = (qreal)Lx / (qreal)(M + 1);
-    diag = qscale + QLIT(2.0) / (h * h);
+    diag = a0 + QLIT(2.0) / (h * h);
     off = QLIT(-1.0) / (h * h);
   } else {
-    diag = qscale + (qreal)lambda;
+    diag = a0 + (qreal)lambda;
     off = QLIT(0.0);
   }
   if (nthreads < 1) nthreads = 1;
   for (int64_t n = N; n >= 1; --n) {
 #pragma omp parallel for num_threads(nthreads) schedule(static)
     for (int64_t j = 0; j < M; ++j) {
-      const double* lj = lam + j * N;
-      double s = 0.0;
-      for (int64_t k = n + 1; k <= N; ++k) s += coef[k - n] * lj[k - 1];
-      rhs[j] = gin[j * N + (n - 1)] - scale * s;
+      qreal s = QLIT(0.0);
+      if (n < N) dd_dot(ah + 1, al + 1, lam + j * N + n, llo + j * N + n, N - n, &s);
+      rq[j] = (qreal)gin[j * N + (n - 1)] - s;
     }
     if (space == 1) {
-      thomas_const(M, diag, off, rhs, cp, rq);
+      thomas_const(M, diag, off, rq, cp);
     } else {
-      for (int64_t j = 0; j < M; ++j) rhs[j] = (double)((qreal)rhs[j] / diag);
+      for (int64_t j = 0; j < M; ++j) rq[j] = rq[j] / diag;
     }
-    for (int64_t j = 0; j < M; ++j) lam[j * N + (n - 1)] = rhs[j];
+    for (int64_t j = 0; j < M; ++j) q_split(rq[j], &lam[j * N + (n - 1)], &llo[j * N + (n - 1)]);
   }
-  free(coef); free(rhs); free(cp); free(rq);
+  free(ah); free(al); free(llo); free(rq); free(cp);
   return OR_OK;
 }
 

@@ -391,3 +391,42 @@ def test_toeplitz_matvec_vs_dense(oracle):
     T = np.tril(toeplitz(a))
     np.testing.assert_allclose(oracle.toeplitz_matvec(a, x), x @ T.T, atol=1e-12)
     np.testing.assert_allclose(oracle.toeplitz_matvec(a, x, transpose=True), x @ T, atol=1e-12)
+
+
+def _extended_scalar_march(kind, g, N, lam, f):
+    """Independent statement of the scalar march in extended precision: weights from mpmath
+    at 40 digits (Lemma 1 / Sec. 3 definitions, Eq. 4 and Eq. 17 coefficients), rounded to
+    numpy longdouble, levels solved in longdouble."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    gm, tau = mp.mpf(g), mp.mpf(1) / N
+    if kind == 0:
+        b, sc = 1 - gm, tau ** (-gm) / mp.gamma(2 - gm)
+        Gk = lambda k: (k + 1) ** b - (k ** b if k > 0 else 0)
+        c = [Gk(0)] + [-(Gk(j - 1) - Gk(j)) for j in range(1, N)]
+    else:
+        b, sc = 2 - gm, tau ** (-gm) / mp.gamma(3 - gm)
+        Mk = lambda k: mp.mpf(0) if k < 0 else (k + 1) ** b - (k ** b if k > 0 else 0)
+        c = [Mk(0), Mk(1) - 2 * Mk(0)] + [Mk(j - 2) - 2 * Mk(j - 1) + Mk(j) for j in range(2, N)]
+    a = np.array([np.longdouble(mp.nstr(sc * x, 30)) for x in c], dtype=np.longdouble)
+    u = np.zeros(N, dtype=np.longdouble)
+    for n in range(N):
+        hist = np.dot(u[:n], a[n:0:-1]) if n else np.longdouble(0)
+        u[n] = (np.longdouble(f[n]) - hist) / (a[0] + np.longdouble(lam))
+    return u.astype(np.float64)
+
+
+@pytest.mark.parametrize("kind,g,lam", [(1, 1.9, 9.55), (1, 1.45, 9.55), (0, 0.7, 9.87)])
+def test_march_accuracy_vs_extended_precision(oracle, kind, g, lam):
+    """Rounding of the direct march (the paper states no precision): in Eq. 17's form the
+    hyperbolic history terms carry tau^-g and cancel to the size of f, and the second-
+    difference weights make the discrete solution sensitive to their rounding at about
+    eps * N^g.  The oracle (double-double weights and history sums, binary128 level solve)
+    must agree with an extended-precision march from 40-digit weights far below the 1e-12
+    bar it certifies; plain double history sums miss it by four orders of magnitude here."""
+    N = 8192
+    t = (np.arange(1, N + 1) - (0.5 if kind == 1 else 0.0)) / N
+    f = 1.3 * t ** 1.7 - 0.4 * t ** 2.4
+    ref = _extended_scalar_march(kind, g, N, lam, f)
+    u = oracle.march(kind, 0, g, f[None, :], lam=lam)[0]
+    assert np.linalg.norm(u - ref) / np.linalg.norm(ref) < 2e-13
