@@ -127,9 +127,12 @@ typedef enum {
  *   inverses once at plan creation (leaf: dense forward-substitution size, power of two
  *   <= 16; levels below gemm_max_level use dense products instead of FFTs).  The solves
  *   themselves do not depend on them (up to rounding of the block inverses).
- * scheduler: an ftoep_scheduler value. */
+ * scheduler: an ftoep_scheduler value.
+ * streams: internal streams of a plan with several problems (1..8; default 4): the
+ *   per-problem phases (sine transforms, time sums, residuals; with the levels schedule
+ *   every launch) of different problems run concurrently on them. */
 typedef struct {
-  int leaf, fft_tile, gemm_max_level, scheduler;
+  int leaf, fft_tile, gemm_max_level, scheduler, streams;
 } ftoep_tuning;
 
 /* Create a plan for nprob problems (1 <= nprob).  Computes the weights a_j of every
@@ -219,14 +222,16 @@ ftoep_status ftoep_profile_read(ftoep_plan p, int kclass, double* total_ms, int6
 ftoep_status ftoep_matvec_noalloc(const double* a, int64_t N, const double* x, double* y, int64_t nlines,
                                   int transpose, void* cuda_stream);
 
-/* Autotuner (no counterpart in the paper).  Times ftoep_solve on synthetic zero fields for
- * each candidate time-block length fft_tile in {1024, 2048, 4096} (a plan per candidate,
- * one warm-up and two timed solves with CUDA events on cuda_stream, device memory freed
- * afterwards) and writes the fastest tuning to *out (other fields 0 = library choice).
- * When the problems together exceed 2^28 unknowns the candidates are timed on a sample:
- * problems taken evenly over the list sorted by M*N, up to that many unknowns.  Blocks
- * until done.  Errors: FTOEP_EINVAL (bad problems, out NULL), FTOEP_ENOMEM, FTOEP_ECUDA;
- * *out is left unchanged on error. */
+/* Autotuner (no counterpart in the paper).  Times ftoep_solve on synthetic fields for
+ * every candidate tuning -- time-block length fft_tile in {1024, 2048, 4096} x scheduler in
+ * {levels, chain} x internal streams in {2, 4, 8} (streams only for plans of several
+ * problems; a single problem runs on the caller's stream) -- with a plan per candidate,
+ * one warm-up solve, one captured solve and two timed replays (CUDA events on
+ * cuda_stream), device memory freed afterwards, and writes the fastest tuning to *out
+ * (leaf and gemm_max_level 0 = library choice).  When the problems together exceed 2^28
+ * unknowns the candidates are timed on a sample: problems taken evenly over the list sorted
+ * by M*N, up to that many unknowns.  Blocks until done.  Errors: FTOEP_EINVAL (bad problems,
+ * out NULL), FTOEP_ENOMEM, FTOEP_ECUDA; *out is left unchanged on error. */
 ftoep_status ftoep_autotune(const ftoep_problem* probs, int nprob, void* cuda_stream, ftoep_tuning* out);
 
 /* Wait for the plan's stream; returns FTOEP_ECUDA on an asynchronous CUDA error. */

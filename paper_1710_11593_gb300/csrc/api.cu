@@ -10,7 +10,7 @@
 //   mixed precision: 1-3 in float (running sums of the all-ones part in double), then the
 //   residual of the same difference-form rows (float-float Toeplitz product, spatial
 //   stencil in double), 1-3 on it, u += correction.
-// A plan with several problems runs them on up to kMaxStreams internal streams (longest
+// A plan with several problems runs them on internal streams (4 unless tuned; longest
 // first, each onto the least-loaded stream), each stream with its own workspace; the
 // caller's stream forks to them and joins them again through events.  Device-pointer
 // solves are captured once as a CUDA graph and replayed (solve_device).
@@ -30,7 +30,8 @@ using namespace ftoep;
 
 namespace {
 
-constexpr int kMaxStreams = 4;
+constexpr int kMaxStreams = 8;
+constexpr int kDefaultStreams = 4;
 constexpr int kNumClasses = 7;
 constexpr int kDotBlocks = 1024;
 
@@ -323,6 +324,8 @@ ftoep_status validate(const ftoep_problem& d, int i, const ftoep_tuning* tune) {
       return fail(pl, FTOEP_EINVAL, "tuning: fft_tile must be a power of two in [16, 4096]");
     if (tune->gemm_max_level && (!is_pow2(tune->gemm_max_level) || tune->gemm_max_level > 2048))
       return fail(pl, FTOEP_EINVAL, "tuning: gemm_max_level must be a power of two <= 2048");
+    if (tune->streams < 0 || tune->streams > kMaxStreams)
+      return fail(pl, FTOEP_EINVAL, "tuning: streams must be in [0, %d]", kMaxStreams);
     if (tune->scheduler < 0 || tune->scheduler > FTOEP_SCHED_CHAIN)
       return fail(pl, FTOEP_EINVAL, "tuning: scheduler must be 0 (library choice), 1 (levels) or 2 (chain)");
   }
@@ -1022,7 +1025,8 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
   pl->total_vec = voff;
   // streams: the caller's stream for one problem, else up to kMaxStreams own streams,
   // problems longest first onto the least-loaded one
-  const int nstreams = nprob == 1 ? 1 : std::min(nprob, kMaxStreams);
+  const int want = (tune && tune->streams) ? tune->streams : kDefaultStreams;
+  const int nstreams = nprob == 1 ? 1 : std::min(nprob, want);
   pl->ws.resize(nstreams);
   for (int s = 0; s < nstreams; ++s) {
     Ws& w = pl->ws[s];
@@ -1603,17 +1607,34 @@ ftoep_status ftoep_autotune(const ftoep_problem* probs, int nprob, void* cuda_st
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int cand[] = {1024, 2048, 4096};
+  std::vector<ftoep_tuning> cands;
+  const int ns_list[] = {2, 4, 8};
+  for (int B : {1024, 2048, 4096})
+    for (int sch : {(int)FTOEP_SCHED_LEVELS, (int)FTOEP_SCHED_CHAIN}) {
+      if (sample.size() == 1) {
+        ftoep_tuning t{};
+        t.fft_tile = B;
+        t.scheduler = sch;
+        cands.push_back(t);
+        continue;
+      }
+      for (int ns : ns_list) {
+        ftoep_tuning t{};
+        t.fft_tile = B;
+        t.scheduler = sch;
+        t.streams = ns;
+        cands.push_back(t);
+      }
+    }
   float best_ms = -1.0f;
-  int best = 0;
+  ftoep_tuning best{};
   ftoep_status status = FTOEP_OK;
-  for (int c : cand) {
-    ftoep_tuning t{};
-    t.fft_tile = c;
+  for (const ftoep_tuning& t : cands) {
     ftoep_plan pl = nullptr;
     status = ftoep_create(&pl, sample.data(), (int)sample.size(), &t, cuda_stream);
     if (status != FTOEP_OK) break;
-    status = ftoep_solve(pl, f, u, nullptr, nullptr);
+    // direct run, captured run, then two timed replays
+    for (int r = 0; r < 2 && status == FTOEP_OK; ++r) status = ftoep_solve(pl, f, u, nullptr, nullptr);
     if (status == FTOEP_OK) cudaEventRecord(e0, st);
     for (int r = 0; r < 2 && status == FTOEP_OK; ++r) status = ftoep_solve(pl, f, u, nullptr, nullptr);
     if (status == FTOEP_OK) {
@@ -1623,7 +1644,7 @@ ftoep_status ftoep_autotune(const ftoep_problem* probs, int nprob, void* cuda_st
       cudaEventElapsedTime(&ms, e0, e1);
       if (best_ms < 0.0f || ms < best_ms) {
         best_ms = ms;
-        best = c;
+        best = t;
       }
     } else {
       g_create_error = pl->err;
@@ -1637,9 +1658,7 @@ ftoep_status ftoep_autotune(const ftoep_problem* probs, int nprob, void* cuda_st
   cudaFree(f);
   cudaFree(u);
   if (status != FTOEP_OK) return status;
-  ftoep_tuning r{};
-  r.fft_tile = best;
-  *out = r;
+  *out = best;
   return FTOEP_OK;
 }
 

@@ -49,7 +49,7 @@ class ftoep_problem(ctypes.Structure):
 
 class ftoep_tuning(ctypes.Structure):
     _fields_ = [("leaf", ctypes.c_int), ("fft_tile", ctypes.c_int), ("gemm_max_level", ctypes.c_int),
-                ("scheduler", ctypes.c_int)]
+                ("scheduler", ctypes.c_int), ("streams", ctypes.c_int)]
 
 
 _lib = None
@@ -154,7 +154,8 @@ def ftoep_create(problems: Sequence[ProblemSpec], tuning: Optional[dict] = None,
     tp = None
     if tuning:
         tp = ctypes.pointer(ftoep_tuning(int(tuning.get("leaf", 0)), int(tuning.get("fft_tile", 0)),
-                                         int(tuning.get("gemm_max_level", 0)), int(tuning.get("scheduler", 0))))
+                                         int(tuning.get("gemm_max_level", 0)), int(tuning.get("scheduler", 0)),
+                                         int(tuning.get("streams", 0))))
     h = ctypes.c_void_p()
     st = current_stream_handle() if stream is None else stream
     rc = lib.ftoep_create(ctypes.byref(h), arr, len(problems), tp, ctypes.c_void_p(st))
@@ -206,8 +207,8 @@ def ftoep_destroy(plan: int):
 
 
 def ftoep_autotune(problems: Sequence[ProblemSpec], stream: Optional[int] = None) -> dict:
-    """Time the candidate block lengths on the problems (C ABI ftoep_autotune) and return the
-    fastest tuning as a dict for Plan(..., tuning=...)."""
+    """Time the candidate tunings (block length, scheduler, internal streams) on the problems
+    (C ABI ftoep_autotune) and return the fastest as a dict for Plan(..., tuning=...)."""
     lib = load()
     arr = (ftoep_problem * len(problems))(*[p.to_c() for p in problems])
     out = ftoep_tuning()
@@ -215,7 +216,60 @@ def ftoep_autotune(problems: Sequence[ProblemSpec], stream: Optional[int] = None
     rc = lib.ftoep_autotune(arr, len(problems), ctypes.c_void_p(st), ctypes.byref(out))
     _check(rc, None)
     return {"leaf": out.leaf, "fft_tile": out.fft_tile, "gemm_max_level": out.gemm_max_level,
-            "scheduler": out.scheduler}
+            "scheduler": out.scheduler, "streams": out.streams}
+
+
+def tuning_key(problems: Sequence[ProblemSpec], device: str = "") -> str:
+    """Cache key of a set of problems: the device name and the multiset of (N bucket, M
+    bucket, precision, kind, space), buckets = ceil(log2) of N and of M+1."""
+    import math
+    sig = {}
+    for p in problems:
+        k = (math.ceil(math.log2(max(1, p.N))), math.ceil(math.log2(p.M + 1)), int(p.precision), int(p.kind),
+             int(p.space))
+        sig[k] = sig.get(k, 0) + 1
+    items = ";".join(f"{a},{b},{c},{d},{e}x{n}" for (a, b, c, d, e), n in sorted(sig.items()))
+    return f"{device}|{items}"
+
+
+def tuning_cache_path() -> str:
+    return os.environ.get("FTOEP_TUNE_CACHE") or os.path.join(os.path.expanduser("~"), ".cache", "ftoep",
+                                                               "tuning.json")
+
+
+def autotune_cached(problems: Sequence[ProblemSpec], stream: Optional[int] = None, path: Optional[str] = None):
+    """The autotuner's choice for these problems, from the JSON cache when a set of the same
+    key (see tuning_key) was tuned on this device before, else from ftoep_autotune (stored
+    in the cache).  Returns (tuning dict, True if it came from the cache)."""
+    import json
+    device = ""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            device = torch.cuda.get_device_name()
+    except Exception:
+        pass
+    key = tuning_key(problems, device)
+    path = path or tuning_cache_path()
+    cache = {}
+    try:
+        with open(path) as fh:
+            cache = json.load(fh)
+    except (OSError, ValueError):
+        cache = {}
+    if key in cache:
+        return dict(cache[key]), True
+    tuning = ftoep_autotune(problems, stream)
+    cache[key] = tuning
+    try:
+        os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+        tmp = path + ".tmp"
+        with open(tmp, "w") as fh:
+            json.dump(cache, fh, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return tuning, False
 
 
 class Plan:

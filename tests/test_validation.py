@@ -63,3 +63,25 @@ def test_autotune_validates_before_timing():
     with pytest.raises(ftoep.FtoepError) as ei:
         ftoep.ftoep_autotune([_spec(gamma=1.5)], stream=0)
     assert ei.value.status == ftoep.FTOEP_EINVAL
+
+
+def test_tuning_key_buckets_and_cache_roundtrip(tmp_path, monkeypatch):
+    """The autotuner's cache key groups problems by (ceil log2 N, ceil log2 (M+1), precision,
+    kind, space) and the device; a cached entry is returned without running the autotuner."""
+    import json
+    from paper_1710_11593_gb300 import ftoep
+    a = [ftoep.ProblemSpec(0, 0.5, 1000, 63, 1, 1), ftoep.ProblemSpec(1, 1.5, 1024, 60, 1, 1)]
+    b = [ftoep.ProblemSpec(1, 1.7, 600, 50, 1, 1), ftoep.ProblemSpec(0, 0.2, 513, 33, 1, 1)]
+    c = [ftoep.ProblemSpec(0, 0.5, 1025, 63, 1, 1), ftoep.ProblemSpec(1, 1.5, 1024, 60, 1, 1)]
+    assert ftoep.tuning_key(a, "X") == ftoep.tuning_key(b, "X")
+    assert ftoep.tuning_key(a, "X") != ftoep.tuning_key(c, "X")
+    assert ftoep.tuning_key(a, "X") != ftoep.tuning_key(a, "Y")
+    path = tmp_path / "t.json"
+    key = ftoep.tuning_key(a, "")
+    want = {"leaf": 0, "fft_tile": 2048, "gemm_max_level": 0, "scheduler": 2, "streams": 8}
+    path.write_text(json.dumps({key: want}))
+    monkeypatch.setattr(ftoep, "ftoep_autotune", lambda *x, **k: (_ for _ in ()).throw(AssertionError("ran")))
+    import sys
+    monkeypatch.setitem(sys.modules, "torch", None)  # no device name: the key of the stored entry
+    got, hit = ftoep.autotune_cached(a, path=str(path))
+    assert hit and got == want
