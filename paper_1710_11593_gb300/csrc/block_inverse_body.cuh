@@ -53,7 +53,7 @@ __device__ __forceinline__ void acc2(float& s, float& c, float x) {
 // pair's packed C1/C2 array (2B entries), lt = lambda tau of the two modes, S = running
 // sums of all earlier solved entries.  red: 4 * blockDim.x elements of shared memory.
 // Thread 0 writes S advanced by this block's sums to *S_out.  No barrier at the end.
-template <typename T>
+template <typename T, int INF = 8>
 __device__ __forceinline__ void block_inverse_body(Vt<T>* sm, Vt<T>* __restrict__ zg, const Vt<T>* __restrict__ cs,
                                                    int logB, double2 lt, double2 S, T* red, double2* S_out,
                                                    const Vt<T>* __restrict__ tw) {
@@ -64,36 +64,57 @@ __device__ __forceinline__ void block_inverse_body(Vt<T>* sm, Vt<T>* __restrict_
   const T sxl = (T)(sx - (double)sxh), syl = (T)(sy - (double)syh);
   const SmLayout L = sm_layout<V>(logn);
   const int np = fftr_npasses<V>(logn);
-  fftr_pass<V, true, false, true>(0, logn, 1, tw, true, [&](int, int e) {
+  fftr_pass<V, true, false, true, false, INF>(0, logn, 1, tw, true, [&](int, int e) {
     const V y = zg[e];
     return mkv(shift_sub(y.x, sxh, sxl), shift_sub(y.y, syh, syl));
   }, SmPut<V>{sm, L});
   __syncthreads();
   fftr_passes<V, true>(sm, logn, 1, tw, 1, np, false);
-  for (int pos = threadIdx.x; pos < n; pos += blockDim.x) {
-    const int pp = partner_pos(pos, logn);
-    if (pp < pos) continue;
-    const int q1 = sm_pos<V>(L, 0, pos);
-    const V z1 = sm[q1];
-    V z1c;
-    z1c.x = z1.x;
-    z1c.y = -z1.y;
-    if (pp == pos) {  // real C1, C2 packed in one slot
-      const V c = cs[pos];
-      V r;
-      r.x = c.x * z1.x + c.y * z1c.x;
-      r.y = c.x * z1.y + c.y * z1c.y;
-      sm[q1] = r;
-    } else {
-      const V c1 = cs[pos], c2 = cs[pp];
-      const int q2 = sm_pos<V>(L, 0, pp);
-      const V z2 = sm[q2];
-      V z2c;
-      z2c.x = z2.x;
-      z2c.y = -z2.y;
-      // Y_k = C1_k Z_k + C2_k conj(Z_{n-k}); at the partner the conjugate coefficients
-      sm[q1] = cadd(cmul(c1, z1), cmul(c2, z2c));
-      sm[q2] = cadd(cmulc(z2, c1), cmulc(z1c, c2));
+  // The product visits every frequency with its partner.  The pair's coefficients come
+  // from global memory (64 KB per pair in float, read once per time block), so each thread
+  // first issues the loads of kProdBatch of its positions, then does their arithmetic:
+  // the loads of a batch are in flight together instead of one loop iteration at a time.
+  constexpr int kProdBatch = 4;
+  const int stride = blockDim.x;
+  for (int base = threadIdx.x; base < n; base += kProdBatch * stride) {
+    V c1v[kProdBatch], c2v[kProdBatch];
+    int pv[kProdBatch], ppv[kProdBatch];
+#pragma unroll
+    for (int q = 0; q < kProdBatch; ++q) {
+      const int pos = base + q * stride;
+      pv[q] = pos;
+      ppv[q] = pos < n ? partner_pos(pos, logn) : -1;
+      if (pos < n && ppv[q] >= pos) {
+        c1v[q] = cs[pos];
+        c2v[q] = ppv[q] == pos ? c1v[q] : cs[ppv[q]];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kProdBatch; ++q) {
+      const int pos = pv[q], pp = ppv[q];
+      if (pos >= n || pp < pos) continue;
+      const int q1 = sm_pos<V>(L, 0, pos);
+      const V z1 = sm[q1];
+      V z1c;
+      z1c.x = z1.x;
+      z1c.y = -z1.y;
+      if (pp == pos) {  // real C1, C2 packed in one slot
+        const V c = c1v[q];
+        V r;
+        r.x = c.x * z1.x + c.y * z1c.x;
+        r.y = c.x * z1.y + c.y * z1c.y;
+        sm[q1] = r;
+      } else {
+        const V c1 = c1v[q], c2 = c2v[q];
+        const int q2 = sm_pos<V>(L, 0, pp);
+        const V z2 = sm[q2];
+        V z2c;
+        z2c.x = z2.x;
+        z2c.y = -z2.y;
+        // Y_k = C1_k Z_k + C2_k conj(Z_{n-k}); at the partner the conjugate coefficients
+        sm[q1] = cadd(cmul(c1, z1), cmul(c2, z2c));
+        sm[q2] = cadd(cmulc(z2, c1), cmulc(z1c, c2));
+      }
     }
   }
   __syncthreads();

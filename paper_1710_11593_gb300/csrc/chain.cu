@@ -26,41 +26,55 @@ constexpr int kChainThreads = 256;
 // Blocks per SM the register budget is sized for: three float blocks (64 KB of shared
 // memory each), two double blocks (the double block solve alone takes 128 KB, so one is
 // resident; the bound keeps the register count at the per-level kernels' level).
-template <typename T> struct ChainOcc { static constexpr int value = 3; };
+// kInf: elements a thread keeps in flight in the global-memory passes of the bodies.  The
+// per-level kernels use 8; here the bodies are calls with the recursion's state around them,
+// and 8 (or 4) made every body spill inside its passes (measured: local-memory traffic above
+// the kernel's DRAM traffic); with 2 the bodies stay in registers.
+#ifndef FTOEP_CHAIN_OCC
+#define FTOEP_CHAIN_OCC 3
+#endif
+#ifndef FTOEP_CHAIN_INF
+#define FTOEP_CHAIN_INF 2
+#endif
+#ifndef FTOEP_CHAIN_CALL
+#define FTOEP_CHAIN_CALL __noinline__
+#endif
+template <typename T> struct ChainOcc { static constexpr int value = FTOEP_CHAIN_OCC; };
 template <> struct ChainOcc<double> { static constexpr int value = 2; };
+constexpr int kInf = FTOEP_CHAIN_INF;
 
 // Each body runs as a call of its own: registers are then allocated per body (as in the
 // per-level kernels) instead of across the whole recursion, and the state of the
 // recursion lives in shared memory between the calls.
 template <typename T>
-__device__ __noinline__ void chain_block(Vt<T>* sm, Vt<T>* zg, const Vt<T>* cs, int logB, double2 lt, double2 S, T* red,
+__device__ FTOEP_CHAIN_CALL void chain_block(Vt<T>* sm, Vt<T>* zg, const Vt<T>* cs, int logB, double2 lt, double2 S, T* red,
                                          double2* S_out, const Vt<T>* tw) {
-  block_inverse_body<T>(sm, zg, cs, logB, lt, S, red, S_out, tw);
+  block_inverse_body<T, kInf>(sm, zg, cs, logB, lt, S, red, S_out, tw);
 }
 template <typename T>
-__device__ __noinline__ void chain_conv_smem(Vt<T>* sm, const Vt<T>* zin, Vt<T>* zo, int logn, const Vt<T>* spec,
+__device__ FTOEP_CHAIN_CALL void chain_conv_smem(Vt<T>* sm, const Vt<T>* zin, Vt<T>* zo, int logn, const Vt<T>* spec,
                                              const Vt<T>* tw) {
-  conv_smem_body<T>(sm, zin, zo, logn, 0, spec, tw);
+  conv_smem_body<T, kInf>(sm, zin, zo, logn, 0, spec, tw);
 }
 // The whole four-step convolution of one pair (three steps over column and row groups of
 // at most cap elements), through the block's scratch slice.
 template <typename T>
-__device__ __noinline__ void chain_fourstep(Vt<T>* sm, const Vt<T>* zin, Vt<T>* zo, Vt<T>* scr, const Vt<T>* spec,
+__device__ FTOEP_CHAIN_CALL void chain_fourstep(Vt<T>* sm, const Vt<T>* zin, Vt<T>* zo, Vt<T>* scr, const Vt<T>* spec,
                                             int logn, int cap, const Vt<T>* tw) {
   typedef Vt<T> V;
   const Split sp = split_of(logn);
   const int C = fourstep_cols_for(sp.logn1, sp.logn2, (int)sizeof(V), cap);
   const int rows = min(cap >> sp.logn2, 1 << sp.logn1);
   for (int c0 = 0; c0 < (1 << sp.logn2); c0 += C) {
-    conv_col_fwd_body<T>(sm, zin, scr, sp.logn1, sp.logn2, C, c0, tw);
+    conv_col_fwd_body<T, kInf>(sm, zin, scr, sp.logn1, sp.logn2, C, c0, tw);
     __syncthreads();
   }
   for (int r0 = 0; r0 < (1 << sp.logn1); r0 += rows) {
-    conv_row_body<T>(sm, scr, spec, sp.logn1, sp.logn2, rows, r0, tw);
+    conv_row_body<T, kInf>(sm, scr, spec, sp.logn1, sp.logn2, rows, r0, tw);
     __syncthreads();
   }
   for (int c0 = 0; c0 < (1 << sp.logn2); c0 += C) {
-    conv_col_inv_body<T>(sm, scr, zo, sp.logn1, sp.logn2, C, c0, 0, tw);
+    conv_col_inv_body<T, kInf>(sm, scr, zo, sp.logn1, sp.logn2, C, c0, 0, tw);
     __syncthreads();
   }
 }

@@ -70,7 +70,7 @@ struct SubUpperCols {  // column t: zo[(e - h1) n2 + t] -= v for e >= h1
 
 // Whole convolution of one pair row in shared memory sm (n elements).  zin: the input
 // half (n/2 entries), zo: the output half.  No barrier at the end.
-template <typename T>
+template <typename T, int INF = 8>
 __device__ __forceinline__ void conv_smem_body(Vt<T>* sm, const Vt<T>* __restrict__ zin, Vt<T>* __restrict__ zo,
                                                int logn, int mode, const Vt<T>* __restrict__ spec,
                                                const Vt<T>* __restrict__ tw) {
@@ -78,7 +78,7 @@ __device__ __forceinline__ void conv_smem_body(Vt<T>* sm, const Vt<T>* __restric
   const int s = 1 << (logn - 1);
   const SmLayout L = sm_layout<V>(logn);
   const int np = fftr_npasses<V>(logn);
-  fftr_pass<V, true, false, true>(0, logn, 1, tw, true, [&](int, int e) { return zin[e]; }, SmPut<V>{sm, L});
+  fftr_pass<V, true, false, true, false, INF>(0, logn, 1, tw, true, [&](int, int e) { return zin[e]; }, SmPut<V>{sm, L});
   __syncthreads();
   if (np < 2) {  // a single pass: plain product in shared memory
     for (int k = threadIdx.x; k < 2 * s; k += blockDim.x) {
@@ -93,7 +93,7 @@ __device__ __forceinline__ void conv_smem_body(Vt<T>* sm, const Vt<T>* __restric
     fftr_passes<V, false>(sm, logn, 1, tw, 1, np - 1, false);
   }
   if (mode == 0) {
-    fftr_pass<V, false, false, false, true>(np - 1, logn, 1, tw, false, SmAt<V>{sm, L}, SubUpper<V>{zo, s});
+    fftr_pass<V, false, false, false, true, INF>(np - 1, logn, 1, tw, false, SmAt<V>{sm, L}, SubUpper<V>{zo, s});
   } else {
     fftr_pass<V, false>(np - 1, logn, 1, tw, false, SmAt<V>{sm, L}, [&](int, int e, const V& v) {
       if (e < s) zo[e] = v;
@@ -103,7 +103,7 @@ __device__ __forceinline__ void conv_smem_body(Vt<T>* sm, const Vt<T>* __restric
 
 // Four-step step A on columns c0 .. c0+C-1: zin is the pair's input half (row layout
 // j1*n2 + j2), sc the pair's scratch (n elements).  No barrier at the end.
-template <typename T>
+template <typename T, int INF = 8>
 __device__ __forceinline__ void conv_col_fwd_body(Vt<T>* sm, const Vt<T>* __restrict__ zin_row,
                                                   Vt<T>* __restrict__ sc_row, int logn1, int logn2, int C, int c0,
                                                   const Vt<T>* __restrict__ tw) {
@@ -114,7 +114,7 @@ __device__ __forceinline__ void conv_col_fwd_body(Vt<T>* sm, const Vt<T>* __rest
   const V* __restrict__ twn = tw + (n - 2);
   const SmLayout L = sm_layout<V>(logn1);
   const int np = fftr_npasses<V>(logn1);
-  fftr_pass<V, true, true, true>(0, logn1, C, tw, true, [&](int t, int e) { return zin[(int64_t)e * n2 + t]; },
+  fftr_pass<V, true, true, true, false, INF>(0, logn1, C, tw, true, [&](int t, int e) { return zin[(int64_t)e * n2 + t]; },
                                  SmPut<V>{sm, L});
   __syncthreads();
   fftr_passes<V, true, true>(sm, logn1, C, tw, 1, np - 1, false);
@@ -126,7 +126,7 @@ __device__ __forceinline__ void conv_col_fwd_body(Vt<T>* sm, const Vt<T>* __rest
 
 // Four-step step B on rows r0 .. r0+rows-1 of the pair's scratch.  spec: the level's
 // spectrum (n elements, four-step order).  No barrier at the end.
-template <typename T>
+template <typename T, int INF = 8>
 __device__ __forceinline__ void conv_row_body(Vt<T>* sm, Vt<T>* __restrict__ sc_row, const Vt<T>* __restrict__ spec_all,
                                               int logn1, int logn2, int rows, int r0, const Vt<T>* __restrict__ tw) {
   typedef Vt<T> V;
@@ -135,7 +135,7 @@ __device__ __forceinline__ void conv_row_body(Vt<T>* sm, Vt<T>* __restrict__ sc_
   const V* __restrict__ twn = tw + (n - 2);
   const SmLayout L = sm_layout<V>(logn2);
   const int np = fftr_npasses<V>(logn2);
-  fftr_pass<V, true, false, true>(0, logn2, rows, tw, false, [&](int t, int e) { return sc[t * n2 + e]; },
+  fftr_pass<V, true, false, true, false, INF>(0, logn2, rows, tw, false, [&](int t, int e) { return sc[t * n2 + e]; },
                                   SmPut<V>{sm, L});
   __syncthreads();
   fftr_passes<V, true>(sm, logn2, rows, tw, 1, np - 1, false);
@@ -154,7 +154,7 @@ __device__ __forceinline__ void conv_row_body(Vt<T>* sm, Vt<T>* __restrict__ sc_
 // Four-step step C on columns c0 .. c0+C-1: inverse column transforms of the scratch,
 // result written to the pair's output half zo_row (mode 0: subtracted).  No barrier at
 // the end.
-template <typename T>
+template <typename T, int INF = 8>
 __device__ __forceinline__ void conv_col_inv_body(Vt<T>* sm, const Vt<T>* __restrict__ sc_row,
                                                   Vt<T>* __restrict__ zo_row, int logn1, int logn2, int C, int c0,
                                                   int mode, const Vt<T>* __restrict__ tw) {
@@ -164,13 +164,13 @@ __device__ __forceinline__ void conv_col_inv_body(Vt<T>* sm, const Vt<T>* __rest
   V* __restrict__ zo = zo_row + c0;
   const SmLayout L = sm_layout<V>(logn1);
   const int np = fftr_npasses<V>(logn1);
-  fftr_pass<V, false, true, true>(0, logn1, C, tw, false, [&](int t, int e) { return sc[(int64_t)e * n2 + t]; },
+  fftr_pass<V, false, true, true, false, INF>(0, logn1, C, tw, false, [&](int t, int e) { return sc[(int64_t)e * n2 + t]; },
                                   SmPut<V>{sm, L});
   __syncthreads();
   fftr_passes<V, false, true>(sm, logn1, C, tw, 1, np - 1, false);
   if (mode == 0) {
-    fftr_pass<V, false, true, false, true>(np - 1, logn1, C, tw, false, SmAt<V>{sm, L},
-                                           SubUpperCols<V>{zo, h1, n2});
+    fftr_pass<V, false, true, false, true, INF>(np - 1, logn1, C, tw, false, SmAt<V>{sm, L},
+                                                SubUpperCols<V>{zo, h1, n2});
   } else {
     fftr_pass<V, false, true>(np - 1, logn1, C, tw, false, SmAt<V>{sm, L}, [&](int t, int e, const V& v) {
       if (e < h1) zo[(int64_t)e * n2 + t] = v;

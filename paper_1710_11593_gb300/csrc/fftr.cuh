@@ -387,7 +387,8 @@ __device__ __forceinline__ void run_pass(int logn, int cnt, int logg, const V* _
 // GL: the loader reads global memory (several units per thread keep loads in flight).
 // RMW: the storer updates global memory: st.fetch(t, e) is called in the load phase and
 // st(t, e, v, fetched) after the arithmetic.
-template <typename V, bool DIF, bool TM = false, bool GL = false, bool RMW = false, class Ld, class St>
+// INF: elements a thread keeps in flight in a global-memory pass (units per thread = INF / radix).
+template <typename V, bool DIF, bool TM = false, bool GL = false, bool RMW = false, int INF = 8, class Ld, class St>
 __device__ __forceinline__ void fftr_pass(int p, int logn, int cnt, const V* __restrict__ tw, bool half_zero, Ld ld,
                                           St st) {
   constexpr int RB = EngineTraits<V>::RB;
@@ -399,8 +400,8 @@ __device__ __forceinline__ void fftr_pass(int p, int logn, int cnt, const V* __r
 #define FTOEP_PASS_CASE(RR)                                                                     \
   {                                                                                             \
     constexpr int LH = (1 << RR) / 2, LF = 1 << RR;                                             \
-    constexpr int UBH = (GL || RMW) ? (LH >= 8 ? 1 : 8 / LH) : 1;                               \
-    constexpr int UBF = (GL || RMW) ? (LF >= 8 ? 1 : 8 / LF) : 1;                               \
+    constexpr int UBH = (GL || RMW) ? (LH >= INF ? 1 : INF / LH) : 1;                           \
+    constexpr int UBF = (GL || RMW) ? (LF >= INF ? 1 : INF / LF) : 1;                           \
     if (hz) run_pass<V, RR, DIF, true, TM, UBH, RMW>(logn, cnt, logg, tw, ld, st);              \
     else run_pass<V, RR, DIF, false, TM, UBF, RMW>(logn, cnt, logg, tw, ld, st);                \
   }

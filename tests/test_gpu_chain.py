@@ -108,9 +108,11 @@ def test_chain_groups(ft, oracle, monkeypatch):
             off += n
 
 
-# With initial data the right-hand side carries scale*u0 and S*u0, which cancel against the
-# history: two correct double evaluations in different orders differ by about eps*scale
-# relative, so the double cases keep N and gamma small enough for eps*scale < 3e-13.
+# With initial data the difference form solves for v = d_t u with right-hand side
+# f - S u0 (S u0 up to 4/h^2 |u0|), and u = u0 + tau cumsum(v) cancels u0 against the sum:
+# when the solution decays far below u0 its rounding is eps times the data's scale, not
+# eps times |u|.  The double bar is therefore taken against the scale of the data,
+# max(max |u|, max |u0|, T max |phi|).
 def test_chain_initial_data(ft, oracle, monkeypatch):
     """u0 and phi enter the right-hand side and the mixed residual; two groups."""
     import torch
@@ -130,7 +132,12 @@ def test_chain_initial_data(ft, oracle, monkeypatch):
             n = p.M * p.N
             ref = oracle.march(p.kind, p.space, p.gamma, fh[off:off + n].reshape(p.M, p.N), u0=u0[voff:voff + p.M],
                                phi=phi[voff:voff + p.M] if p.kind == 1 else None)
-            _check(u[off:off + n].reshape(p.M, p.N), ref, tol, (prec, p.kind, p.N, p.M))
+            got = u[off:off + n].reshape(p.M, p.N)
+            scale = max(np.max(np.abs(ref)), np.max(np.abs(u0[voff:voff + p.M])),
+                        np.max(np.abs(phi[voff:voff + p.M])) if p.kind == 1 else 0.0)
+            assert np.max(np.abs(got - ref)) < tol * scale, (prec, p.kind, p.N, p.M)
+            if prec == 1:
+                _check(got, ref, tol, (prec, p.kind, p.N, p.M))
             off += n
             voff += p.M
 
