@@ -64,6 +64,8 @@ struct Prob {
   double2* bspec64 = nullptr;
   float2* chirp32 = nullptr;
   float2* bspec32 = nullptr;
+  double* sinv64 = nullptr;     // sin(pi j/K), j <= K/2
+  float* sinv32 = nullptr;
   void* spec = nullptr;         // solve spectra, precision prec
   double2* spec64 = nullptr;    // solve spectra in double (adjoint of mixed problems; == spec for P64)
   double2* spec_mv = nullptr;   // product spectrum, length 2Np
@@ -431,6 +433,7 @@ DstArgs dst_args(ftoep_plan pl, const Prob& pb, Prec pr, void* z) {
     da.logP = pb.logP;
     da.chirp = pr == P64 ? (const void*)pb.chirp64 : (const void*)pb.chirp32;
     da.bspec = pr == P64 ? (const void*)pb.bspec64 : (const void*)pb.bspec32;
+    da.sinv = pr == P64 ? (const void*)pb.sinv64 : (const void*)pb.sinv32;
   }
   return da;
 }
@@ -680,12 +683,13 @@ ftoep_status join_streams(ftoep_plan pl) {
   return FTOEP_OK;
 }
 
-// Bluestein tables for the sine transform of a problem with K = M+1 not a power of two:
-// chirp c_n = exp(-i pi n^2 / L) (L = 2K, n^2 reduced mod 2L exactly) and the forward
-// transform of b_m = conj(c_|m|) wrapped to length P, in the bit-reversed order of the
-// device decimation-in-frequency FFT, divided by P.  Host long double.
+// Tables of the sine transform of a problem with K = M+1 not a power of two (folded to a
+// DFT of length K, the DFT by Bluestein): chirp c_n = exp(-i pi n^2 / K) (n^2 reduced mod
+// 2K exactly), the forward transform of b_m = conj(c_|m|) (|m| < K) wrapped to length
+// P >= 2K - 1 in the bit-reversed order of the device decimation-in-frequency FFT divided
+// by P, and the fold factors sin(pi j/K), j <= K/2.  Host long double.
 ftoep_status build_bluestein(ftoep_plan pl, Prob& pb) {
-  const int64_t K = pb.M + 1, L = 2 * K;
+  const int64_t K = pb.M + 1, L = K;
   const int logP = ilog2(2 * L - 1);
   const int64_t P = int64_t(1) << logP;
   pb.logP = logP;
@@ -733,14 +737,26 @@ ftoep_status build_bluestein(ftoep_plan pl, Prob& pb) {
     b64[k] = make_double2((double)(br[k] / P), (double)(bi[k] / P));
     b32[k] = make_float2((float)(br[k] / P), (float)(bi[k] / P));
   }
+  const int64_t Q = K / 2;
+  std::vector<double> s64(Q + 1);
+  std::vector<float> s32(Q + 1);
+  for (int64_t j = 0; j <= Q; ++j) {
+    const long double v = sinl(pi * (long double)j / (long double)K);
+    s64[j] = (double)v;
+    s32[j] = (float)v;
+  }
   ALLOC(pb.chirp64, L * sizeof(double2));
   ALLOC(pb.bspec64, P * sizeof(double2));
   ALLOC(pb.chirp32, L * sizeof(float2));
   ALLOC(pb.bspec32, P * sizeof(float2));
+  ALLOC(pb.sinv64, (Q + 1) * sizeof(double));
+  ALLOC(pb.sinv32, (Q + 1) * sizeof(float));
   CK(cudaMemcpy(pb.chirp64, c64.data(), L * sizeof(double2), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(pb.bspec64, b64.data(), P * sizeof(double2), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(pb.chirp32, c32.data(), L * sizeof(float2), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(pb.bspec32, b32.data(), P * sizeof(float2), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(pb.sinv64, s64.data(), (Q + 1) * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(pb.sinv32, s32.data(), (Q + 1) * sizeof(float), cudaMemcpyHostToDevice));
   pb.bluestein = true;
   return FTOEP_OK;
 }
@@ -1011,7 +1027,7 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
     maxtw = std::max<int64_t>(maxtw, 2 * np);
     if (pb.d.space) {
       maxtw = std::max<int64_t>(maxtw, 2 * (pb.M + 1));
-      if (!is_pow2(pb.M + 1)) maxtw = std::max<int64_t>(maxtw, int64_t(1) << ilog2(4 * (pb.M + 1) - 1));
+      if (!is_pow2(pb.M + 1)) maxtw = std::max<int64_t>(maxtw, int64_t(1) << ilog2(2 * (pb.M + 1) - 1));
     }
     pl->z_el = std::max<size_t>(pl->z_el, (size_t)pb.P * np);
     pl->mv_el = std::max<size_t>(pl->mv_el, (size_t)pb.P * np);

@@ -44,13 +44,15 @@ struct DstArgs {
   int accumulate;       // inverse: u += result
   int space;            // 0: no transform (pairs of rows), 1: sine transform
   int diff_form;        // forward: right-hand side of the difference form (-(S u0) instead of wu0*u0)
-  // Sine transform for M+1 not a power of two (Bluestein): the length-2K DFT of the odd
-  // extension as a cyclic convolution of length P = 2^logP >= 4K - 1 with the chirp.
+  // Sine transform for M+1 not a power of two: the folded half-length form (a real DFT of
+  // length K = M+1 of y_j = s_j (x_j + x_{K-j}) + (x_j - x_{K-j})/2, s_j = sin(pi j/K)),
+  // the DFT by Bluestein as a cyclic convolution of length P = 2^logP >= 2K - 1.
   int bluestein;
   int K;                // M + 1
   int logP;
-  const void* chirp;    // c_n = exp(-i pi n^2 / (2K)), n < 2K (z precision)
+  const void* chirp;    // c_n = exp(-i pi n^2 / K), n < K (z precision)
   const void* bspec;    // forward transform (this library's order) of conj(chirp) wrapped to length P, / P
+  const void* sinv;     // s_j = sin(pi j / K), j = 0 .. K/2 (z component precision)
   double inv_h2;        // 1/h^2 (space 1) for S u0
   double lambda;        // lambda (space 0) for S u0
   const void* tw;       // twiddles of the z precision

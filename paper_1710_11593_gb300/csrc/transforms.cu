@@ -377,85 +377,140 @@ __global__ void __launch_bounds__(kDstThreads) rows_inverse_kernel(DstArgs A, in
   rows_inverse<T>(A, C);
 }
 
-// Sine transform for any K = M+1 (Bluestein / chirp-z).  With W = exp(-2 pi i / L),
-// L = 2K, and c_n = W^{n^2/2}: DFT(y)_k = c_k sum_n (y_n c_n) conj(c_{k-n}), a linear
-// convolution that a cyclic one of length P >= 2L-1 reproduces exactly.  One block
-// handles C time columns (C/2 complex column pairs, one P-buffer each); the product with
-// the chirp's spectrum runs fused between the forward and inverse FFT, and the DFT comes
-// out in natural order.
+// Sine transform for any K = M+1: folded to a real DFT of length K, the DFT by Bluestein.
+//
+// Fold (one real column x_1 .. x_{K-1}):  y_0 = 0 and, for j = 1 .. K-1,
+//     y_j = s_j (x_j + x_{K-j}) + (x_j - x_{K-j})/2,   s_j = sin(pi j/K).
+// Write DFT_K(y)_m = R_m - i I_m.  Under j -> K-j the first term of y is symmetric and the
+// second antisymmetric, sin(2 pi j m/K) is antisymmetric and cos(2 pi j m/K) symmetric, and
+// 2 sin(pi j/K) cos(2 pi j m/K) = sin(pi j (2m+1)/K) - sin(pi j (2m-1)/K).  Hence, with
+// S_k = sum_j x_j sin(pi j k/K),
+//     S_{2m} = I_m,     S_{2m+1} = S_{2m-1} + R_m,   S_1 = R_0/2:
+// the even coefficients directly, the odd ones as a prefix sum over R.  Two real columns
+// (a in .x, b in .y) share one complex DFT of z = y_a + i y_b, split with the partner
+// frequency: Y_a(m) = (Z_m + conj Z_{K-m})/2, Y_b(m) = (Z_m - conj Z_{K-m})/(2i).
+// Against the odd extension of length 2K this halves the transform.
+//
+// Bluestein (chirp-z): with c_n = exp(-i pi n^2/K), Z_m = c_m sum_n (z_n c_n) conj(c_{m-n}),
+// a linear convolution that a cyclic one of length P >= 2K - 1 reproduces exactly.  One
+// block handles C time columns (C/2 column pairs, one P-buffer each); the product with the
+// chirp's spectrum runs fused between the forward and inverse FFT, and the DFT comes out in
+// natural order.  The fold pairs row j with row K-j; in mode space pair p holds modes
+// a = p+1 and K-a, which is the same pairing, so the inverse transform (DST-I is its own
+// inverse) folds each pair in registers.
+
+// s + c += x (two-sum, the rounding error of each addition kept in c) for float; plain in
+// double.
+__device__ __forceinline__ void scan_acc(float& s, float& c, float x) {
+  const float t = s + x;
+  const float bb = t - s;
+  c += (s - (t - bb)) + (x - bb);
+  s = t;
+}
+__device__ __forceinline__ void scan_acc(double& s, double&, double x) { s += x; }
+
+// Inclusive prefix sums, in place, of sm[t][0 .. Q) for every transform t < CP (both
+// components), compensated in float.  wsum: 2 * (blockDim/32) * CP entries of V.
+template <typename V, typename T>
+__device__ void block_prefix_sums(V* sm, const SmLayout& L, int CP, int Q, V* wsum) {
+  const int nt = blockDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int chunk = (Q + nt - 1) / nt;
+  for (int t = 0; t < CP; ++t) {
+    const int k0 = threadIdx.x * chunk;
+    T sx = 0, cx = 0, sy = 0, cy = 0;
+    for (int k = k0; k < k0 + chunk && k < Q; ++k) {
+      const V v = sm[sm_pos<V>(L, t, k)];
+      scan_acc(sx, cx, v.x);
+      scan_acc(sy, cy, v.y);
+    }
+    // inclusive scan of the (sum, error) pairs over the warp, then over the warps
+    T hx = sx, lx = cx, hy = sy, ly = cy;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T ax = __shfl_up_sync(0xffffffffu, hx, o), bx = __shfl_up_sync(0xffffffffu, lx, o);
+      const T ay = __shfl_up_sync(0xffffffffu, hy, o), by = __shfl_up_sync(0xffffffffu, ly, o);
+      if (lane >= o) {
+        scan_acc(hx, lx, ax);
+        lx += bx;
+        scan_acc(hy, ly, ay);
+        ly += by;
+      }
+    }
+    if (lane == 31) {
+      wsum[2 * warp] = mkv(hx, hy);
+      wsum[2 * warp + 1] = mkv(lx, ly);
+    }
+    __syncthreads();
+    // exclusive offset of this thread: earlier warps + earlier lanes of this warp
+    T ox = 0, oxl = 0, oy = 0, oyl = 0;
+    for (int w = 0; w < warp; ++w) {
+      scan_acc(ox, oxl, wsum[2 * w].x);
+      oxl += wsum[2 * w + 1].x;
+      scan_acc(oy, oyl, wsum[2 * w].y);
+      oyl += wsum[2 * w + 1].y;
+    }
+    scan_acc(ox, oxl, hx - sx);
+    oxl += lx - cx;
+    scan_acc(oy, oyl, hy - sy);
+    oyl += ly - cy;
+    for (int k = k0; k < k0 + chunk && k < Q; ++k) {
+      const int q = sm_pos<V>(L, t, k);
+      const V v = sm[q];
+      scan_acc(ox, oxl, v.x);
+      scan_acc(oy, oyl, v.y);
+      sm[q] = mkv(ox + oxl, oy + oyl);
+    }
+    __syncthreads();
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kDstThreads) dst_bluestein_kernel(DstArgs A, int C, int fwd) {
   typedef Vt<T> V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
+  __shared__ V wsum[2 * (kDstThreads / 32)];
   const int64_t col0 = (int64_t)blockIdx.x * C;
-  const int64_t M = A.M;
-  const int K = A.K, Lq = 2 * K;
+  const int K = A.K, Q = K >> 1;  // Q: odd coefficients (k = 1, 3, .. < K) and pairs
   const int logP = A.logP, P = 1 << logP, H = P >> 1;
   const int CP = C >> 1, lcp = 31 - __clz(CP);
   const SmLayout Ls = sm_layout<V>(logP);
   const V* __restrict__ chirp = (const V*)A.chirp;
+  const T* __restrict__ sinv = (const T*)A.sinv;
   const V* __restrict__ tw = (const V*)A.tw;
-  // zero [0, P/2) of every buffer; the upper half is never read (half-zero input) unless
-  // the whole transform is a single pass
+  const T half = (T)0.5;
+  // zero [0, P/2) of every buffer (the sequence occupies [0, K) and K <= P/2); the upper
+  // half is never read by the half-zero first pass unless the transform is a single pass
   const int np = fftr_npasses<V>(logP);
   const int Z = np < 2 ? P : H;
   for (int e = threadIdx.x; e < CP * Z; e += blockDim.x) sm[sm_pos<V>(Ls, e / Z, e % Z)] = vzero<V>();
   __syncthreads();
-  if (fwd) {
-    const int tot = (int)M << lcp;
-    for (int e0 = threadIdx.x; e0 < tot; e0 += 4 * (int)blockDim.x) {
-      T va[4], vb[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e = e0 + q * (int)blockDim.x;
-        if (e < tot) {
-          const int64_t j = (e >> lcp), n = col0 + 2 * ((e & (CP - 1)));
-          va[q] = dst_in<T>(A, j, n);
-          vb[q] = dst_in<T>(A, j, n + 1);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e = e0 + q * (int)blockDim.x;
-        if (e < tot) {
-          const int j = (e >> lcp), t = (e & (CP - 1));
-          const V v = mkv(va[q], vb[q]);
-          sm[sm_pos<V>(Ls, t, j + 1)] = cmul(v, chirp[j + 1]);
-          sm[sm_pos<V>(Ls, t, Lq - j - 1)] = cmul(vneg(v), chirp[Lq - j - 1]);
-        }
-      }
+  // fold: pair j = 1 .. Q of rows j and K - j (forward: physical rows j-1, K-j-1; inverse:
+  // modes j and K-j of pair j-1) for the columns (n, n+1) of transform t
+  const int tot = Q << lcp;
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int j = (e >> lcp) + 1, t = e & (CP - 1);
+    const int64_t n = col0 + 2 * t;
+    V xj, xr;  // (column n, column n+1) at j and at K - j
+    if (fwd) {
+      xj = mkv(dst_in<T>(A, j - 1, n), dst_in<T>(A, j - 1, n + 1));
+      xr = (2 * j == K) ? xj : mkv(dst_in<T>(A, K - j - 1, n), dst_in<T>(A, K - j - 1, n + 1));
+    } else {
+      const V* z = (const V*)A.z;
+      const int64_t p = j - 1;
+      const V c0 = n < A.N ? z[p * A.ld + col_of(A, n)] : vzero<V>();
+      const V c1 = n + 1 < A.N ? z[p * A.ld + col_of(A, n + 1)] : vzero<V>();
+      xj = mkv(c0.x, c1.x);
+      xr = (2 * j == K) ? xj : mkv(c0.y, c1.y);
     }
-  } else {
-    const V* z = (const V*)A.z;
-    const int tot = (int)((M + 1) / 2) << lcp;
-    for (int e0 = threadIdx.x; e0 < tot; e0 += 4 * (int)blockDim.x) {
-      V c0[4], c1[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e = e0 + q * (int)blockDim.x;
-        if (e < tot) {
-          const int64_t p = (e >> lcp), n = col0 + 2 * ((e & (CP - 1)));
-          c0[q] = n < A.N ? z[p * A.ld + col_of(A, n)] : vzero<V>();
-          c1[q] = n + 1 < A.N ? z[p * A.ld + col_of(A, n + 1)] : vzero<V>();
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e = e0 + q * (int)blockDim.x;
-        if (e < tot) {
-          const int a = (e >> lcp) + 1, t = (e & (CP - 1));
-          const int b = K - a;
-          const V va = mkv(c0[q].x, c1[q].x);
-          sm[sm_pos<V>(Ls, t, a)] = cmul(va, chirp[a]);
-          sm[sm_pos<V>(Ls, t, Lq - a)] = cmul(vneg(va), chirp[Lq - a]);
-          if (b != a) {
-            const V vb = mkv(c0[q].y, c1[q].y);
-            sm[sm_pos<V>(Ls, t, b)] = cmul(vb, chirp[b]);
-            sm[sm_pos<V>(Ls, t, Lq - b)] = cmul(vneg(vb), chirp[Lq - b]);
-          }
-        }
-      }
+    const T sj = sinv[j];
+    const V sum = cadd(xj, xr), dif = csub(xj, xr);
+    const V y1 = mkv(sj * sum.x + half * dif.x, sj * sum.y + half * dif.y);
+    sm[sm_pos<V>(Ls, t, j)] = cmul(y1, chirp[j]);
+    if (2 * j != K) {
+      const V y2 = mkv(sj * sum.x - half * dif.x, sj * sum.y - half * dif.y);
+      sm[sm_pos<V>(Ls, t, K - j)] = cmul(y2, chirp[K - j]);
     }
   }
   __syncthreads();
@@ -463,33 +518,48 @@ __global__ void __launch_bounds__(kDstThreads) dst_bluestein_kernel(DstArgs A, i
   fftr_middle<V>(sm, logP, CP, SpecMul<V>{(const V*)A.bspec});
   __syncthreads();
   fftr_passes<V, false>(sm, logP, CP, tw, 1, np, false);
-  const T scale = (T)A.dst_scale;
+  // unfold, part 1: Z_m = c_m w_m; with the partner K - m, R_m of both columns to slot m and
+  // I_m to slot H + m (m = 0 .. Q; slots K-m > Q are read only here, by the thread of m)
+  const int tq = (Q + 1) << lcp;
+  for (int e = threadIdx.x; e < tq; e += blockDim.x) {
+    const int m = e >> lcp, t = e & (CP - 1);
+    const int mp = m == 0 ? 0 : K - m;
+    const V zm = cmul(sm[sm_pos<V>(Ls, t, m)], chirp[m]);
+    const V zp = cmul(sm[sm_pos<V>(Ls, t, mp)], chirp[mp]);
+    // Y_a = (Zm + conj Zp)/2, Y_b = (Zm - conj Zp)/(2i); R = Re Y, I = -Im Y
+    const V r = mkv(half * (zm.x + zp.x), half * (zm.y + zp.y));
+    const V im = mkv(half * (zp.y - zm.y), half * (zm.x - zp.x));
+    sm[sm_pos<V>(Ls, t, H + m)] = im;
+    sm[sm_pos<V>(Ls, t, m)] = m == 0 ? mkv(half * r.x, half * r.y) : r;
+  }
+  __syncthreads();
+  // part 2: odd coefficients S_{2m+1} = R_0/2 + R_1 + .. + R_m (m < Q)
+  block_prefix_sums<V, T>(sm, Ls, CP, Q, wsum);
+  // coefficient k of the two columns of transform t
+  auto coef = [&](int t, int k) -> V {
+    return (k & 1) ? sm[sm_pos<V>(Ls, t, k >> 1)] : sm[sm_pos<V>(Ls, t, H + (k >> 1))];
+  };
+  const T scale = (T)(2.0 * A.dst_scale);  // sqrt(2/K) on the raw sums
   if (fwd) {
     V* z = (V*)A.z;
-    const int64_t P2 = (M + 1) / 2;
-    for (int e = threadIdx.x; e < ((int)P2 << lcp); e += blockDim.x) {
-      const int a = (e >> lcp) + 1, t = (e & (CP - 1));
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+      const int a = (e >> lcp) + 1, t = e & (CP - 1);
       const int b = K - a;
       const int64_t p = a - 1;
-      const V ya = cmul(sm[sm_pos<V>(Ls, t, a)], chirp[a]);
-      const V yb = cmul(sm[sm_pos<V>(Ls, t, b)], chirp[b]);
-      const bool self = a == b;
-      V c0, c1;
-      c0.x = -ya.y * scale;
-      c1.x = ya.x * scale;
-      c0.y = self ? (T)0 : -yb.y * scale;
-      c1.y = self ? (T)0 : yb.x * scale;
+      const V ya = coef(t, a);
+      const V yb = a == b ? vzero<V>() : coef(t, b);
       const int64_t n = col0 + 2 * t;
-      if (n < A.ncols) z[p * A.ld + col_of(A, n)] = c0;
-      if (n + 1 < A.ncols) z[p * A.ld + col_of(A, n + 1)] = c1;
+      if (n < A.ncols) z[p * A.ld + col_of(A, n)] = mkv(ya.x * scale, yb.x * scale);
+      if (n + 1 < A.ncols) z[p * A.ld + col_of(A, n + 1)] = mkv(ya.y * scale, yb.y * scale);
     }
   } else {
-    for (int e = threadIdx.x; e < ((int)M << lcp); e += blockDim.x) {
-      const int j = (e >> lcp) + 1, t = (e & (CP - 1));
-      const V y = cmul(sm[sm_pos<V>(Ls, t, j)], chirp[j]);
+    const int tj = (K - 1) << lcp;
+    for (int e = threadIdx.x; e < tj; e += blockDim.x) {
+      const int j = (e >> lcp) + 1, t = e & (CP - 1);
+      const V y = coef(t, j);
       const int64_t n = col0 + 2 * t;
-      dst_out<T>(A, j - 1, n, -y.y * scale);
-      dst_out<T>(A, j - 1, n + 1, y.x * scale);
+      dst_out<T>(A, j - 1, n, y.x * scale);
+      dst_out<T>(A, j - 1, n + 1, y.y * scale);
     }
   }
 }
@@ -1020,7 +1090,7 @@ void set_smem_once(const void* fn, size_t bytes) {
 }
 
 int nsmem_for(Prec prec) { return prec == P32 ? 8192 : 4096; }
-int bluestein_max_K(Prec prec) { return prec == P64 ? 2048 : 4096; }
+int bluestein_max_K(Prec prec) { return prec == P64 ? 4096 : 8192; }
 
 int launch_dst_forward(Prec prec, const DstArgs& a, cudaStream_t st) {
   if (prec == P64) dst_launch<double>(a, true, st); else dst_launch<float>(a, true, st);
