@@ -95,10 +95,8 @@ typedef enum {
 /* One problem.  T: final time (> 0).  L: length of the space interval (> 0, ignored for
  * FTOEP_SPACE_NONE).  lambda: reaction coefficient for FTOEP_SPACE_NONE (>= 0).
  * N >= 1 time steps (N <= 2^22); M >= 1 interior points (rows, for FTOEP_SPACE_NONE).
- * Sine transform sizes: any M+1 up to 4096 (double) / 8192 (mixed) -- powers of two by a
- * direct FFT, others by a chirp-z FFT; beyond: FTOEP_EUNSUPPORTED.  The adjoint runs in
- * double, so a mixed problem with M+1 above 4096 that is not a power of two has no adjoint
- * (FTOEP_EUNSUPPORTED from ftoep_adjoint). */
+ * Sine transform sizes: M+1 a power of two up to 4096 (double) / 8192 (mixed); any other
+ * M+1 (chirp-z FFT) up to 4096; beyond: FTOEP_EUNSUPPORTED. */
 typedef struct {
   int kind;       /* ftoep_kind      */
   int space;      /* ftoep_space     */

@@ -16,6 +16,7 @@
 // solves are captured once as a CUDA graph and replayed (solve_device).
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -59,13 +60,12 @@ struct Prob {
   double2* lamtau = nullptr;    // per pair lambda tau
   // sine transform for M+1 not a power of two (Bluestein tables, double and float)
   bool bluestein = false;
-  int logP = 0;
   double2* chirp64 = nullptr;
   double2* bspec64 = nullptr;
   float2* chirp32 = nullptr;
   float2* bspec32 = nullptr;
-  double* sinv64 = nullptr;     // sin(pi j/K), j <= K/2
-  float* sinv32 = nullptr;
+  double* sinv64 = nullptr;     // sin(pi j/K), j <= K/2 (double, folded form)
+  int logP64 = 0, logP32 = 0;   // chirp-z lengths of the double (folded) and float (odd) forms
   void* spec = nullptr;         // solve spectra, precision prec
   double2* spec64 = nullptr;    // solve spectra in double (adjoint of mixed problems; == spec for P64)
   double2* spec_mv = nullptr;   // product spectrum, length 2Np
@@ -430,10 +430,10 @@ DstArgs dst_args(ftoep_plan pl, const Prob& pb, Prec pr, void* z) {
   if (pb.bluestein) {
     da.bluestein = 1;
     da.K = (int)(pb.M + 1);
-    da.logP = pb.logP;
     da.chirp = pr == P64 ? (const void*)pb.chirp64 : (const void*)pb.chirp32;
     da.bspec = pr == P64 ? (const void*)pb.bspec64 : (const void*)pb.bspec32;
-    da.sinv = pr == P64 ? (const void*)pb.sinv64 : (const void*)pb.sinv32;
+    da.sinv = pr == P64 ? (const void*)pb.sinv64 : nullptr;
+    da.logP = pr == P64 ? pb.logP64 : pb.logP32;
   }
   return da;
 }
@@ -683,24 +683,12 @@ ftoep_status join_streams(ftoep_plan pl) {
   return FTOEP_OK;
 }
 
-// Tables of the sine transform of a problem with K = M+1 not a power of two (folded to a
-// DFT of length K, the DFT by Bluestein): chirp c_n = exp(-i pi n^2 / K) (n^2 reduced mod
-// 2K exactly), the forward transform of b_m = conj(c_|m|) (|m| < K) wrapped to length
-// P >= 2K - 1 in the bit-reversed order of the device decimation-in-frequency FFT divided
-// by P, and the fold factors sin(pi j/K), j <= K/2.  Host long double.
-ftoep_status build_bluestein(ftoep_plan pl, Prob& pb) {
-  const int64_t K = pb.M + 1, L = K;
-  const int logP = ilog2(2 * L - 1);
-  const int64_t P = int64_t(1) << logP;
-  pb.logP = logP;
+// Forward transform, in the bit-reversed order of the device decimation-in-frequency FFT
+// and divided by P, of b_m = conj(c_|m|) (|m| < L) wrapped to length P.  Host long double.
+std::vector<std::complex<long double>> chirp_kernel_spectrum(const std::vector<long double>& cr,
+                                                             const std::vector<long double>& ci, int64_t P) {
+  const int64_t L = (int64_t)cr.size();
   const long double pi = 3.141592653589793238462643383279502884L;
-  std::vector<long double> cr(L), ci(L);
-  for (int64_t n = 0; n < L; ++n) {
-    const int64_t r = (n * n) % (2 * L);
-    const long double ang = -pi * (long double)r / (long double)L;
-    cr[n] = cosl(ang);
-    ci[n] = sinl(ang);
-  }
   std::vector<long double> br(P, 0.0L), bi(P, 0.0L);
   for (int64_t m = 0; m < L; ++m) {
     br[m] = cr[m];
@@ -727,36 +715,65 @@ ftoep_status build_bluestein(ftoep_plan pl, Prob& pb) {
       }
     }
   }
-  std::vector<double2> c64(L), b64(P);
-  std::vector<float2> c32(L), b32(P);
+  std::vector<std::complex<long double>> out(P);
+  for (int64_t k = 0; k < P; ++k) out[k] = std::complex<long double>(br[k] / P, bi[k] / P);
+  return out;
+}
+
+// Chirp c_n = exp(-i pi n^2 / L), n < L, with n^2 reduced mod 2L exactly.  Host long double.
+void chirp_of(int64_t L, std::vector<long double>& cr, std::vector<long double>& ci) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  cr.resize(L);
+  ci.resize(L);
   for (int64_t n = 0; n < L; ++n) {
-    c64[n] = make_double2((double)cr[n], (double)ci[n]);
-    c32[n] = make_float2((float)cr[n], (float)ci[n]);
+    const int64_t r = (n * n) % (2 * L);
+    const long double ang = -pi * (long double)r / (long double)L;
+    cr[n] = cosl(ang);
+    ci[n] = sinl(ang);
   }
-  for (int64_t k = 0; k < P; ++k) {
-    b64[k] = make_double2((double)(br[k] / P), (double)(bi[k] / P));
-    b32[k] = make_float2((float)(br[k] / P), (float)(bi[k] / P));
+}
+
+// Tables of the sine transform of a problem with K = M+1 not a power of two:
+//   double (folded half-length form, a DFT of length L = K): chirp, kernel spectrum of length
+//     P >= 2K - 1, fold factors sin(pi j/K), j <= K/2;
+//   float (odd extension, a DFT of length L = 2K): chirp, kernel spectrum of length P >= 4K - 1.
+ftoep_status build_bluestein(ftoep_plan pl, Prob& pb) {
+  const int64_t K = pb.M + 1;
+  const long double pi = 3.141592653589793238462643383279502884L;
+  std::vector<long double> cr, ci;
+  {  // double, folded
+    const int64_t L = K;
+    pb.logP64 = ilog2(2 * L - 1);
+    const int64_t P = int64_t(1) << pb.logP64;
+    chirp_of(L, cr, ci);
+    const auto bs = chirp_kernel_spectrum(cr, ci, P);
+    std::vector<double2> c64(L), b64(P);
+    for (int64_t n = 0; n < L; ++n) c64[n] = make_double2((double)cr[n], (double)ci[n]);
+    for (int64_t k = 0; k < P; ++k) b64[k] = make_double2((double)bs[k].real(), (double)bs[k].imag());
+    const int64_t Q = K / 2;
+    std::vector<double> s64(Q + 1);
+    for (int64_t j = 0; j <= Q; ++j) s64[j] = (double)sinl(pi * (long double)j / (long double)K);
+    ALLOC(pb.chirp64, L * sizeof(double2));
+    ALLOC(pb.bspec64, P * sizeof(double2));
+    ALLOC(pb.sinv64, (Q + 1) * sizeof(double));
+    CK(cudaMemcpy(pb.chirp64, c64.data(), L * sizeof(double2), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(pb.bspec64, b64.data(), P * sizeof(double2), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(pb.sinv64, s64.data(), (Q + 1) * sizeof(double), cudaMemcpyHostToDevice));
   }
-  const int64_t Q = K / 2;
-  std::vector<double> s64(Q + 1);
-  std::vector<float> s32(Q + 1);
-  for (int64_t j = 0; j <= Q; ++j) {
-    const long double v = sinl(pi * (long double)j / (long double)K);
-    s64[j] = (double)v;
-    s32[j] = (float)v;
+  {  // float, odd extension
+    const int64_t L = 2 * K;
+    pb.logP32 = ilog2(2 * L - 1);
+    const int64_t P = int64_t(1) << pb.logP32;
+    chirp_of(L, cr, ci);
+    const auto bs = chirp_kernel_spectrum(cr, ci, P);
+    std::vector<float2> c32(L), b32(P);
+    for (int64_t n = 0; n < L; ++n) c32[n] = make_float2((float)cr[n], (float)ci[n]);
+    for (int64_t k = 0; k < P; ++k) b32[k] = make_float2((float)bs[k].real(), (float)bs[k].imag());
+    ALLOC(pb.chirp32, L * sizeof(float2));
+    ALLOC(pb.bspec32, P * sizeof(float2));
+    CK(cudaMemcpy(pb.chirp32, c32.data(), L * sizeof(float2), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(pb.bspec32, b32.data(), P * sizeof(float2), cudaMemcpyHostToDevice));
   }
-  ALLOC(pb.chirp64, L * sizeof(double2));
-  ALLOC(pb.bspec64, P * sizeof(double2));
-  ALLOC(pb.chirp32, L * sizeof(float2));
-  ALLOC(pb.bspec32, P * sizeof(float2));
-  ALLOC(pb.sinv64, (Q + 1) * sizeof(double));
-  ALLOC(pb.sinv32, (Q + 1) * sizeof(float));
-  CK(cudaMemcpy(pb.chirp64, c64.data(), L * sizeof(double2), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(pb.bspec64, b64.data(), P * sizeof(double2), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(pb.chirp32, c32.data(), L * sizeof(float2), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(pb.bspec32, b32.data(), P * sizeof(float2), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(pb.sinv64, s64.data(), (Q + 1) * sizeof(double), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(pb.sinv32, s32.data(), (Q + 1) * sizeof(float), cudaMemcpyHostToDevice));
   pb.bluestein = true;
   return FTOEP_OK;
 }
@@ -1027,7 +1044,7 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
     maxtw = std::max<int64_t>(maxtw, 2 * np);
     if (pb.d.space) {
       maxtw = std::max<int64_t>(maxtw, 2 * (pb.M + 1));
-      if (!is_pow2(pb.M + 1)) maxtw = std::max<int64_t>(maxtw, int64_t(1) << ilog2(2 * (pb.M + 1) - 1));
+      if (!is_pow2(pb.M + 1)) maxtw = std::max<int64_t>(maxtw, int64_t(1) << ilog2(4 * (pb.M + 1) - 1));
     }
     pl->z_el = std::max<size_t>(pl->z_el, (size_t)pb.P * np);
     pl->mv_el = std::max<size_t>(pl->mv_el, (size_t)pb.P * np);

@@ -44,15 +44,16 @@ struct DstArgs {
   int accumulate;       // inverse: u += result
   int space;            // 0: no transform (pairs of rows), 1: sine transform
   int diff_form;        // forward: right-hand side of the difference form (-(S u0) instead of wu0*u0)
-  // Sine transform for M+1 not a power of two: the folded half-length form (a real DFT of
-  // length K = M+1 of y_j = s_j (x_j + x_{K-j}) + (x_j - x_{K-j})/2, s_j = sin(pi j/K)),
-  // the DFT by Bluestein as a cyclic convolution of length P = 2^logP >= 2K - 1.
+  // Sine transform for M+1 not a power of two, a DFT of length L by Bluestein as a cyclic
+  // convolution of length P = 2^logP >= 2L - 1.  Double: the folded half-length form (L = K,
+  // the real DFT of y_j = s_j (x_j + x_{K-j}) + (x_j - x_{K-j})/2, s_j = sin(pi j/K)); float:
+  // the odd extension (L = 2K).
   int bluestein;
   int K;                // M + 1
   int logP;
-  const void* chirp;    // c_n = exp(-i pi n^2 / K), n < K (z precision)
+  const void* chirp;    // c_n = exp(-i pi n^2 / L), n < L (z precision)
   const void* bspec;    // forward transform (this library's order) of conj(chirp) wrapped to length P, / P
-  const void* sinv;     // s_j = sin(pi j / K), j = 0 .. K/2 (z component precision)
+  const void* sinv;     // double: s_j = sin(pi j / K), j = 0 .. K/2
   double inv_h2;        // 1/h^2 (space 1) for S u0
   double lambda;        // lambda (space 0) for S u0
   const void* tw;       // twiddles of the z precision

@@ -7,6 +7,7 @@
 // two components independently, so one complex FFT serves two real problems.
 #include <cstdio>
 #include <mutex>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -377,7 +378,8 @@ __global__ void __launch_bounds__(kDstThreads) rows_inverse_kernel(DstArgs A, in
   rows_inverse<T>(A, C);
 }
 
-// Sine transform for any K = M+1: folded to a real DFT of length K, the DFT by Bluestein.
+// Sine transform for any K = M+1 in double: folded to a real DFT of length K, the DFT by
+// Bluestein.
 //
 // Fold (one real column x_1 .. x_{K-1}):  y_0 = 0 and, for j = 1 .. K-1,
 //     y_j = s_j (x_j + x_{K-j}) + (x_j - x_{K-j})/2,   s_j = sin(pi j/K).
@@ -466,7 +468,7 @@ __device__ void block_prefix_sums(V* sm, const SmLayout& L, int CP, int Q, V* ws
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kDstThreads) dst_bluestein_kernel(DstArgs A, int C, int fwd) {
+__global__ void __launch_bounds__(kDstThreads) dst_bluestein_fold_kernel(DstArgs A, int C, int fwd) {
   typedef Vt<T> V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
@@ -564,6 +566,123 @@ __global__ void __launch_bounds__(kDstThreads) dst_bluestein_kernel(DstArgs A, i
   }
 }
 
+// Sine transform for any K = M+1 in float: the odd extension of length 2K by Bluestein.  With W = exp(-2 pi i / L),
+// L = 2K, and c_n = W^{n^2/2}: DFT(y)_k = c_k sum_n (y_n c_n) conj(c_{k-n}), a linear
+// convolution that a cyclic one of length P >= 2L-1 reproduces exactly.  One block
+// handles C time columns (C/2 complex column pairs, one P-buffer each); the product with
+// the chirp's spectrum runs fused between the forward and inverse FFT, and the DFT comes
+// out in natural order.
+template <typename T>
+__global__ void __launch_bounds__(kDstThreads) dst_bluestein_odd_kernel(DstArgs A, int C, int fwd) {
+  typedef Vt<T> V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const int64_t col0 = (int64_t)blockIdx.x * C;
+  const int64_t M = A.M;
+  const int K = A.K, Lq = 2 * K;
+  const int logP = A.logP, P = 1 << logP, H = P >> 1;
+  const int CP = C >> 1, lcp = 31 - __clz(CP);
+  const SmLayout Ls = sm_layout<V>(logP);
+  const V* __restrict__ chirp = (const V*)A.chirp;
+  const V* __restrict__ tw = (const V*)A.tw;
+  // zero [0, P/2) of every buffer; the upper half is never read (half-zero input) unless
+  // the whole transform is a single pass
+  const int np = fftr_npasses<V>(logP);
+  const int Z = np < 2 ? P : H;
+  for (int e = threadIdx.x; e < CP * Z; e += blockDim.x) sm[sm_pos<V>(Ls, e / Z, e % Z)] = vzero<V>();
+  __syncthreads();
+  if (fwd) {
+    const int tot = (int)M << lcp;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += 4 * (int)blockDim.x) {
+      T va[4], vb[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = e0 + q * (int)blockDim.x;
+        if (e < tot) {
+          const int64_t j = (e >> lcp), n = col0 + 2 * ((e & (CP - 1)));
+          va[q] = dst_in<T>(A, j, n);
+          vb[q] = dst_in<T>(A, j, n + 1);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = e0 + q * (int)blockDim.x;
+        if (e < tot) {
+          const int j = (e >> lcp), t = (e & (CP - 1));
+          const V v = mkv(va[q], vb[q]);
+          sm[sm_pos<V>(Ls, t, j + 1)] = cmul(v, chirp[j + 1]);
+          sm[sm_pos<V>(Ls, t, Lq - j - 1)] = cmul(vneg(v), chirp[Lq - j - 1]);
+        }
+      }
+    }
+  } else {
+    const V* z = (const V*)A.z;
+    const int tot = (int)((M + 1) / 2) << lcp;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += 4 * (int)blockDim.x) {
+      V c0[4], c1[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = e0 + q * (int)blockDim.x;
+        if (e < tot) {
+          const int64_t p = (e >> lcp), n = col0 + 2 * ((e & (CP - 1)));
+          c0[q] = n < A.N ? z[p * A.ld + col_of(A, n)] : vzero<V>();
+          c1[q] = n + 1 < A.N ? z[p * A.ld + col_of(A, n + 1)] : vzero<V>();
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = e0 + q * (int)blockDim.x;
+        if (e < tot) {
+          const int a = (e >> lcp) + 1, t = (e & (CP - 1));
+          const int b = K - a;
+          const V va = mkv(c0[q].x, c1[q].x);
+          sm[sm_pos<V>(Ls, t, a)] = cmul(va, chirp[a]);
+          sm[sm_pos<V>(Ls, t, Lq - a)] = cmul(vneg(va), chirp[Lq - a]);
+          if (b != a) {
+            const V vb = mkv(c0[q].y, c1[q].y);
+            sm[sm_pos<V>(Ls, t, b)] = cmul(vb, chirp[b]);
+            sm[sm_pos<V>(Ls, t, Lq - b)] = cmul(vneg(vb), chirp[Lq - b]);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  fftr_passes<V, true>(sm, logP, CP, tw, 0, np - 1, true);
+  fftr_middle<V>(sm, logP, CP, SpecMul<V>{(const V*)A.bspec});
+  __syncthreads();
+  fftr_passes<V, false>(sm, logP, CP, tw, 1, np, false);
+  const T scale = (T)A.dst_scale;
+  if (fwd) {
+    V* z = (V*)A.z;
+    const int64_t P2 = (M + 1) / 2;
+    for (int e = threadIdx.x; e < ((int)P2 << lcp); e += blockDim.x) {
+      const int a = (e >> lcp) + 1, t = (e & (CP - 1));
+      const int b = K - a;
+      const int64_t p = a - 1;
+      const V ya = cmul(sm[sm_pos<V>(Ls, t, a)], chirp[a]);
+      const V yb = cmul(sm[sm_pos<V>(Ls, t, b)], chirp[b]);
+      const bool self = a == b;
+      V c0, c1;
+      c0.x = -ya.y * scale;
+      c1.x = ya.x * scale;
+      c0.y = self ? (T)0 : -yb.y * scale;
+      c1.y = self ? (T)0 : yb.x * scale;
+      const int64_t n = col0 + 2 * t;
+      if (n < A.ncols) z[p * A.ld + col_of(A, n)] = c0;
+      if (n + 1 < A.ncols) z[p * A.ld + col_of(A, n + 1)] = c1;
+    }
+  } else {
+    for (int e = threadIdx.x; e < ((int)M << lcp); e += blockDim.x) {
+      const int j = (e >> lcp) + 1, t = (e & (CP - 1));
+      const V y = cmul(sm[sm_pos<V>(Ls, t, j)], chirp[j]);
+      const int64_t n = col0 + 2 * t;
+      dst_out<T>(A, j - 1, n, -y.y * scale);
+      dst_out<T>(A, j - 1, n + 1, y.x * scale);
+    }
+  }
+}
+
 // Columns per block (even, C/2 a power of two): as many column pairs (<= 4) as keep the
 // block's shared memory within 64 KB (three blocks per SM), at least one pair.
 template <typename T>
@@ -587,10 +706,17 @@ int dst_pairs_per_block(int logK2) {
 template <typename T>
 void dst_launch(const DstArgs& a, bool fwd, cudaStream_t st) {
   if (a.space && a.bluestein) {
+    // double: the folded half-length form; float: the odd extension (the folded form's odd
+    // coefficients are prefix sums of FFT outputs, whose rounding accumulates like a random
+    // walk across them -- harmless in double, too large against the float solve's correction)
     const int C = dst_cols<T>(a.logP);
     const size_t smem = (size_t)(C / 2) * ((size_t)1 << a.logP) * sizeof(Vt<T>);
-    set_smem((const void*)dst_bluestein_kernel<T>, smem);
-    dst_bluestein_kernel<T><<<(unsigned)((a.ncols + C - 1) / C), kDstThreads, smem, st>>>(a, C, fwd ? 1 : 0);
+    const void* fn = std::is_same<T, double>::value ? (const void*)dst_bluestein_fold_kernel<T>
+                                                    : (const void*)dst_bluestein_odd_kernel<T>;
+    set_smem(fn, smem);
+    const unsigned grid = (unsigned)((a.ncols + C - 1) / C);
+    if (std::is_same<T, double>::value) dst_bluestein_fold_kernel<T><<<grid, kDstThreads, smem, st>>>(a, C, fwd ? 1 : 0);
+    else dst_bluestein_odd_kernel<T><<<grid, kDstThreads, smem, st>>>(a, C, fwd ? 1 : 0);
     return;
   }
   if (!a.space) {
@@ -1090,7 +1216,7 @@ void set_smem_once(const void* fn, size_t bytes) {
 }
 
 int nsmem_for(Prec prec) { return prec == P32 ? 8192 : 4096; }
-int bluestein_max_K(Prec prec) { return prec == P64 ? 4096 : 8192; }
+int bluestein_max_K(Prec prec) { return 4096; }
 
 int launch_dst_forward(Prec prec, const DstArgs& a, cudaStream_t st) {
   if (prec == P64) dst_launch<double>(a, true, st); else dst_launch<float>(a, true, st);

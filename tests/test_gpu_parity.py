@@ -195,10 +195,9 @@ def test_degenerate_sizes(ft, oracle, kind, gamma, M, N, prec):
 @pytest.mark.parametrize("kind,gamma,M,N,prec", [
     (0, 0.7, 8191, 40, 1),  # largest power-of-two M+1, mixed
     (1, 1.4, 4095, 40, 0),  # largest power-of-two M+1, double
-    (0, 0.6, 4094, 30, 1),  # chirp-z M+1 = 4095, mixed
+    (0, 0.6, 4094, 30, 1),  # largest chirp-z M+1 = 4095, mixed
     (1, 1.6, 2046, 30, 0),  # chirp-z M+1 = 2047, double
-    (1, 1.3, 8190, 24, 1),  # largest chirp-z M+1 = 8191 (prime), mixed: P = 16384
-    (0, 0.45, 4094, 24, 0),  # largest chirp-z M+1 = 4095, double: P = 8192
+    (0, 0.45, 4094, 24, 0),  # largest chirp-z M+1 = 4095, double (folded form): P = 8192
 ])
 def test_largest_sine_transforms(ft, oracle, kind, gamma, M, N, prec):
     f = wl.random_field((M, N), seed=M + N)

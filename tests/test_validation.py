@@ -30,7 +30,7 @@ def _spec(**kw):
     (dict(N=(1 << 22) + 1), ftoep.FTOEP_EUNSUPPORTED, "N > 2^22"),
     (dict(M=8192, precision=1), ftoep.FTOEP_EUNSUPPORTED, "M+1 = 8193"),   # above the power-of-two mixed limit
     (dict(M=4096, precision=0), ftoep.FTOEP_EUNSUPPORTED, "M+1 = 4097"),   # chirp-z double limit 4096
-    (dict(M=8200, precision=1), ftoep.FTOEP_EUNSUPPORTED, "M+1 = 8201"),   # chirp-z mixed limit 8192
+    (dict(M=4200, precision=1), ftoep.FTOEP_EUNSUPPORTED, "M+1 = 4201"),   # chirp-z mixed limit 4096
 ])
 def test_invalid_problem_rejected(kw, status, msg):
     with pytest.raises(ftoep.FtoepError) as ei:
