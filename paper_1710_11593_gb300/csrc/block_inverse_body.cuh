@@ -53,7 +53,9 @@ __device__ __forceinline__ void acc2(float& s, float& c, float x) {
 // pair's packed C1/C2 array (2B entries), lt = lambda tau of the two modes, S = running
 // sums of all earlier solved entries.  red: 4 * blockDim.x elements of shared memory.
 // Thread 0 writes S advanced by this block's sums to *S_out.  No barrier at the end.
-template <typename T, int INF = 8>
+// ASYNC: the block's right-hand side arrives by cp.async into shared memory and the first
+// pass (with the shift by the all-ones part) runs there.
+template <typename T, int INF = 8, bool ASYNC = false>
 __device__ __forceinline__ void block_inverse_body(Vt<T>* sm, Vt<T>* __restrict__ zg, const Vt<T>* __restrict__ cs,
                                                    int logB, double2 lt, double2 S, T* red, double2* S_out,
                                                    const Vt<T>* __restrict__ tw) {
@@ -64,10 +66,19 @@ __device__ __forceinline__ void block_inverse_body(Vt<T>* sm, Vt<T>* __restrict_
   const T sxl = (T)(sx - (double)sxh), syl = (T)(sy - (double)syh);
   const SmLayout L = sm_layout<V>(logn);
   const int np = fftr_npasses<V>(logn);
-  fftr_pass<V, true, false, true, false, INF>(0, logn, 1, tw, true, [&](int, int e) {
-    const V y = zg[e];
-    return mkv(shift_sub(y.x, sxh, sxl), shift_sub(y.y, syh, syl));
-  }, SmPut<V>{sm, L});
+  if constexpr (ASYNC) {
+    for (int e = threadIdx.x; e < B; e += blockDim.x) async_copy(&sm[sm_pos<V>(L, 0, e)], zg + e);
+    async_wait_all();
+    fftr_pass<V, true>(0, logn, 1, tw, true, [&](int, int e) {
+      const V y = sm[sm_pos<V>(L, 0, e)];
+      return mkv(shift_sub(y.x, sxh, sxl), shift_sub(y.y, syh, syl));
+    }, SmPut<V>{sm, L});
+  } else {
+    fftr_pass<V, true, false, true, false, INF>(0, logn, 1, tw, true, [&](int, int e) {
+      const V y = zg[e];
+      return mkv(shift_sub(y.x, sxh, sxl), shift_sub(y.y, syh, syl));
+    }, SmPut<V>{sm, L});
+  }
   __syncthreads();
   fftr_passes<V, true>(sm, logn, 1, tw, 1, np, false);
   // The product visits every frequency with its partner.  The pair's coefficients come

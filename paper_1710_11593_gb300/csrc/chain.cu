@@ -42,6 +42,12 @@ constexpr int kChainThreads = 256;
 template <typename T> struct ChainOcc { static constexpr int value = FTOEP_CHAIN_OCC; };
 template <> struct ChainOcc<double> { static constexpr int value = 2; };
 constexpr int kInf = FTOEP_CHAIN_INF;
+// kAsync: the first pass of every body takes its input by cp.async into shared memory (one
+// block per pair has no other blocks' loads to hide its own latency behind).
+#ifndef FTOEP_CHAIN_ASYNC
+#define FTOEP_CHAIN_ASYNC 1
+#endif
+constexpr bool kAsync = FTOEP_CHAIN_ASYNC != 0;
 
 // Each body runs as a call of its own: registers are then allocated per body (as in the
 // per-level kernels) instead of across the whole recursion, and the state of the
@@ -49,12 +55,12 @@ constexpr int kInf = FTOEP_CHAIN_INF;
 template <typename T>
 __device__ FTOEP_CHAIN_CALL void chain_block(Vt<T>* sm, Vt<T>* zg, const Vt<T>* cs, int logB, double2 lt, double2 S, T* red,
                                          double2* S_out, const Vt<T>* tw) {
-  block_inverse_body<T, kInf>(sm, zg, cs, logB, lt, S, red, S_out, tw);
+  block_inverse_body<T, kInf, kAsync>(sm, zg, cs, logB, lt, S, red, S_out, tw);
 }
 template <typename T>
 __device__ FTOEP_CHAIN_CALL void chain_conv_smem(Vt<T>* sm, const Vt<T>* zin, Vt<T>* zo, int logn, const Vt<T>* spec,
                                              const Vt<T>* tw) {
-  conv_smem_body<T, kInf>(sm, zin, zo, logn, 0, spec, tw);
+  conv_smem_body<T, kInf, kAsync>(sm, zin, zo, logn, 0, spec, tw);
 }
 // The whole four-step convolution of one pair (three steps over column and row groups of
 // at most cap elements), through the block's scratch slice.
@@ -66,15 +72,15 @@ __device__ FTOEP_CHAIN_CALL void chain_fourstep(Vt<T>* sm, const Vt<T>* zin, Vt<
   const int C = fourstep_cols_for(sp.logn1, sp.logn2, (int)sizeof(V), cap);
   const int rows = min(cap >> sp.logn2, 1 << sp.logn1);
   for (int c0 = 0; c0 < (1 << sp.logn2); c0 += C) {
-    conv_col_fwd_body<T, kInf>(sm, zin, scr, sp.logn1, sp.logn2, C, c0, tw);
+    conv_col_fwd_body<T, kInf, kAsync>(sm, zin, scr, sp.logn1, sp.logn2, C, c0, tw);
     __syncthreads();
   }
   for (int r0 = 0; r0 < (1 << sp.logn1); r0 += rows) {
-    conv_row_body<T, kInf>(sm, scr, spec, sp.logn1, sp.logn2, rows, r0, tw);
+    conv_row_body<T, kInf, kAsync>(sm, scr, spec, sp.logn1, sp.logn2, rows, r0, tw);
     __syncthreads();
   }
   for (int c0 = 0; c0 < (1 << sp.logn2); c0 += C) {
-    conv_col_inv_body<T, kInf>(sm, scr, zo, sp.logn1, sp.logn2, C, c0, 0, tw);
+    conv_col_inv_body<T, kInf, kAsync>(sm, scr, zo, sp.logn1, sp.logn2, C, c0, 0, tw);
     __syncthreads();
   }
 }

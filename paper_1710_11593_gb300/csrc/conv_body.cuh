@@ -30,6 +30,24 @@ namespace {
 template <typename T>
 using Vt = typename VecOf<T>::type;
 
+// Asynchronous global -> shared copy of one element (cp.async, 8 or 16 bytes): the data
+// does not pass through registers, so a block can have a whole group's loads in flight.
+template <typename V>
+__device__ __forceinline__ void async_copy(V* sdst, const V* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  if constexpr (sizeof(V) == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc) : "memory");
+  }
+}
+// Wait for this thread's copies, then for the block's.
+__device__ __forceinline__ void async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+}
+
 // Pointwise product of spectrum values with a kernel spectrum in the same storage order
 // (the op of fftr_middle): x[j] *= spec[pos0 + j].
 template <typename V>
@@ -70,7 +88,9 @@ struct SubUpperCols {  // column t: zo[(e - h1) n2 + t] -= v for e >= h1
 
 // Whole convolution of one pair row in shared memory sm (n elements).  zin: the input
 // half (n/2 entries), zo: the output half.  No barrier at the end.
-template <typename T, int INF = 8>
+// ASYNC: the input arrives by cp.async into shared memory and the first pass runs there
+// (instead of the first pass reading global memory into registers).
+template <typename T, int INF = 8, bool ASYNC = false>
 __device__ __forceinline__ void conv_smem_body(Vt<T>* sm, const Vt<T>* __restrict__ zin, Vt<T>* __restrict__ zo,
                                                int logn, int mode, const Vt<T>* __restrict__ spec,
                                                const Vt<T>* __restrict__ tw) {
@@ -78,7 +98,14 @@ __device__ __forceinline__ void conv_smem_body(Vt<T>* sm, const Vt<T>* __restric
   const int s = 1 << (logn - 1);
   const SmLayout L = sm_layout<V>(logn);
   const int np = fftr_npasses<V>(logn);
-  fftr_pass<V, true, false, true, false, INF>(0, logn, 1, tw, true, [&](int, int e) { return zin[e]; }, SmPut<V>{sm, L});
+  if constexpr (ASYNC) {
+    for (int e = threadIdx.x; e < s; e += blockDim.x) async_copy(&sm[sm_pos<V>(L, 0, e)], zin + e);
+    async_wait_all();
+    fftr_pass<V, true>(0, logn, 1, tw, true, SmAt<V>{sm, L}, SmPut<V>{sm, L});
+  } else {
+    fftr_pass<V, true, false, true, false, INF>(0, logn, 1, tw, true, [&](int, int e) { return zin[e]; },
+                                                SmPut<V>{sm, L});
+  }
   __syncthreads();
   if (np < 2) {  // a single pass: plain product in shared memory
     for (int k = threadIdx.x; k < 2 * s; k += blockDim.x) {
@@ -103,7 +130,7 @@ __device__ __forceinline__ void conv_smem_body(Vt<T>* sm, const Vt<T>* __restric
 
 // Four-step step A on columns c0 .. c0+C-1: zin is the pair's input half (row layout
 // j1*n2 + j2), sc the pair's scratch (n elements).  No barrier at the end.
-template <typename T, int INF = 8>
+template <typename T, int INF = 8, bool ASYNC = false>
 __device__ __forceinline__ void conv_col_fwd_body(Vt<T>* sm, const Vt<T>* __restrict__ zin_row,
                                                   Vt<T>* __restrict__ sc_row, int logn1, int logn2, int C, int c0,
                                                   const Vt<T>* __restrict__ tw) {
@@ -114,8 +141,18 @@ __device__ __forceinline__ void conv_col_fwd_body(Vt<T>* sm, const Vt<T>* __rest
   const V* __restrict__ twn = tw + (n - 2);
   const SmLayout L = sm_layout<V>(logn1);
   const int np = fftr_npasses<V>(logn1);
-  fftr_pass<V, true, true, true, false, INF>(0, logn1, C, tw, true, [&](int t, int e) { return zin[(int64_t)e * n2 + t]; },
-                                 SmPut<V>{sm, L});
+  if constexpr (ASYNC) {  // input half: rows e < n1/2 of the C columns
+    const int lc = 31 - __clz(C);
+    for (int i = threadIdx.x; i < (C << (logn1 - 1)); i += blockDim.x) {
+      const int t = i & (C - 1), e = i >> lc;
+      async_copy(&sm[sm_pos<V>(L, t, e)], zin + (int64_t)e * n2 + t);
+    }
+    async_wait_all();
+    fftr_pass<V, true, true>(0, logn1, C, tw, true, SmAt<V>{sm, L}, SmPut<V>{sm, L});
+  } else {
+    fftr_pass<V, true, true, true, false, INF>(0, logn1, C, tw, true,
+                                               [&](int t, int e) { return zin[(int64_t)e * n2 + t]; }, SmPut<V>{sm, L});
+  }
   __syncthreads();
   fftr_passes<V, true, true>(sm, logn1, C, tw, 1, np - 1, false);
   fftr_pass<V, true, true>(np - 1, logn1, C, tw, false, SmAt<V>{sm, L}, [&](int t, int e, const V& v) {
@@ -126,7 +163,7 @@ __device__ __forceinline__ void conv_col_fwd_body(Vt<T>* sm, const Vt<T>* __rest
 
 // Four-step step B on rows r0 .. r0+rows-1 of the pair's scratch.  spec: the level's
 // spectrum (n elements, four-step order).  No barrier at the end.
-template <typename T, int INF = 8>
+template <typename T, int INF = 8, bool ASYNC = false>
 __device__ __forceinline__ void conv_row_body(Vt<T>* sm, Vt<T>* __restrict__ sc_row, const Vt<T>* __restrict__ spec_all,
                                               int logn1, int logn2, int rows, int r0, const Vt<T>* __restrict__ tw) {
   typedef Vt<T> V;
@@ -135,8 +172,15 @@ __device__ __forceinline__ void conv_row_body(Vt<T>* sm, Vt<T>* __restrict__ sc_
   const V* __restrict__ twn = tw + (n - 2);
   const SmLayout L = sm_layout<V>(logn2);
   const int np = fftr_npasses<V>(logn2);
-  fftr_pass<V, true, false, true, false, INF>(0, logn2, rows, tw, false, [&](int t, int e) { return sc[t * n2 + e]; },
-                                  SmPut<V>{sm, L});
+  if constexpr (ASYNC) {
+    for (int i = threadIdx.x; i < (rows << logn2); i += blockDim.x)
+      async_copy(&sm[sm_pos<V>(L, i >> logn2, i & (n2 - 1))], sc + i);
+    async_wait_all();
+    fftr_pass<V, true>(0, logn2, rows, tw, false, SmAt<V>{sm, L}, SmPut<V>{sm, L});
+  } else {
+    fftr_pass<V, true, false, true, false, INF>(0, logn2, rows, tw, false, [&](int t, int e) { return sc[t * n2 + e]; },
+                                                SmPut<V>{sm, L});
+  }
   __syncthreads();
   fftr_passes<V, true>(sm, logn2, rows, tw, 1, np - 1, false);
   const V* __restrict__ spec = spec_all + (int64_t)r0 * n2;
@@ -154,7 +198,7 @@ __device__ __forceinline__ void conv_row_body(Vt<T>* sm, Vt<T>* __restrict__ sc_
 // Four-step step C on columns c0 .. c0+C-1: inverse column transforms of the scratch,
 // result written to the pair's output half zo_row (mode 0: subtracted).  No barrier at
 // the end.
-template <typename T, int INF = 8>
+template <typename T, int INF = 8, bool ASYNC = false>
 __device__ __forceinline__ void conv_col_inv_body(Vt<T>* sm, const Vt<T>* __restrict__ sc_row,
                                                   Vt<T>* __restrict__ zo_row, int logn1, int logn2, int C, int c0,
                                                   int mode, const Vt<T>* __restrict__ tw) {
@@ -164,8 +208,18 @@ __device__ __forceinline__ void conv_col_inv_body(Vt<T>* sm, const Vt<T>* __rest
   V* __restrict__ zo = zo_row + c0;
   const SmLayout L = sm_layout<V>(logn1);
   const int np = fftr_npasses<V>(logn1);
-  fftr_pass<V, false, true, true, false, INF>(0, logn1, C, tw, false, [&](int t, int e) { return sc[(int64_t)e * n2 + t]; },
-                                  SmPut<V>{sm, L});
+  if constexpr (ASYNC) {
+    const int lc = 31 - __clz(C);
+    for (int i = threadIdx.x; i < (C << logn1); i += blockDim.x) {
+      const int t = i & (C - 1), e = i >> lc;
+      async_copy(&sm[sm_pos<V>(L, t, e)], sc + (int64_t)e * n2 + t);
+    }
+    async_wait_all();
+    fftr_pass<V, false, true>(0, logn1, C, tw, false, SmAt<V>{sm, L}, SmPut<V>{sm, L});
+  } else {
+    fftr_pass<V, false, true, true, false, INF>(0, logn1, C, tw, false,
+                                                [&](int t, int e) { return sc[(int64_t)e * n2 + t]; }, SmPut<V>{sm, L});
+  }
   __syncthreads();
   fftr_passes<V, false, true>(sm, logn1, C, tw, 1, np - 1, false);
   if (mode == 0) {
