@@ -199,3 +199,33 @@ def gamma_gradient(kind: int, gamma: float, u: np.ndarray, lam: np.ndarray, T: f
     N = u.shape[-1]
     da = toeplitz_column_dgamma(kind, gamma, N, T)
     return -float(np.sum(lam * toeplitz_matvec(da, u)))
+
+
+# ----------------------------------------------------------------- Scheme 1 (two-sided ODE)
+
+def two_sided_column(gamma: float, N: int, T: float = 1.0) -> np.ndarray:
+    """First column of the symmetric Toeplitz matrix A of Scheme 1 (Eq. 7-9: the left L1
+    formula of Eq. 4 plus the right one of Eq. 5, plus u, on u_1 .. u_{N-1} with
+    u_0 = u_N = 0): a_0 = 1 + 2 mu G_0, a_d = mu (G_d - G_{d-1}) = mu W_d, d = 1 .. N-2,
+    mu = tau^-g/Gamma(2-g).  G in binary128, rounded to double."""
+    n = N - 1
+    Gk = G(gamma, max(n, 1) + 1)
+    mu = scale(0, gamma, T / N)
+    a = np.empty(n)
+    a[0] = 1.0 + 2.0 * mu * Gk[0]
+    a[1:] = mu * (Gk[1:n] - Gk[0:n - 1])
+    return a
+
+
+def two_sided_matrix(gamma: float, N: int, T: float = 1.0) -> np.ndarray:
+    """The dense (N-1) x (N-1) matrix A of Eq. 9."""
+    a = two_sided_column(gamma, N, T)
+    idx = np.arange(N - 1)
+    return a[np.abs(idx[:, None] - idx[None, :])]
+
+
+def two_sided_solve(gamma: float, f: np.ndarray, T: float = 1.0) -> np.ndarray:
+    """u = A^-1 f for Scheme 1 by Gaussian elimination on the dense matrix (the paper's
+    "Gauss method"), f = (f_1 .. f_{N-1})."""
+    f = _c64(f)
+    return np.linalg.solve(two_sided_matrix(gamma, f.shape[0] + 1, T), f)

@@ -176,6 +176,19 @@ def config_batched(nprob: int = 512, seed: int = 1234, n_range=(2 ** 10, 2 ** 17
     return probs
 
 
+def two_sided_example1(N: int, gamma: float):
+    """Example 1 of the paper (two-sided ODE, Eq. 2 on (0,1), u(0) = u(1) = 0), exact
+    u = t(1-t) on the interior grid t_n = n/N, n = 1 .. N-1, and its source
+    f = D_left^g u + D_right^g u + u.  Both Caputo derivatives in closed form:
+    D_left^g (t - t^2) = L(t) with L(s) = s^(1-g)/Gamma(2-g) - 2 s^(2-g)/Gamma(3-g), and the
+    right derivative (Eq. 6) is the left one of the reflected function, L(1-t).
+    Returns (t, f, u)."""
+    t = np.arange(1, N, dtype=np.float64) / N
+    L = lambda s: s ** (1 - gamma) / math.gamma(2 - gamma) - 2 * s ** (2 - gamma) / math.gamma(3 - gamma)
+    u = t * (1 - t)
+    return t, L(t) + L(1 - t) + u, u
+
+
 def noise(shape, sigma: float, seed: int) -> np.ndarray:
     return np.random.default_rng(seed).standard_normal(shape) * sigma
 

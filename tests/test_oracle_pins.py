@@ -430,3 +430,52 @@ def test_march_accuracy_vs_extended_precision(oracle, kind, g, lam):
     ref = _extended_scalar_march(kind, g, N, lam, f)
     u = oracle.march(kind, 0, g, f[None, :], lam=lam)[0]
     assert np.linalg.norm(u - ref) / np.linalg.norm(ref) < 2e-13
+
+
+# ----------------------------------------------------------------- Scheme 1 (Table 1, Theorem 1)
+
+def _table1_rows():
+    rows = []
+    with open(os.path.join(HERE, "golden", "table1.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                a, b, c = line.split()
+                rows.append((int(a), float(b), float(c)))
+    return rows
+
+
+@pytest.mark.parametrize("N,g,printed", _table1_rows())
+def test_table1_scheme1(oracle, N, g, printed):
+    """Example 1 / Table 1: Scheme 1 (Eq. 7-9) solved densely, L2 error sqrt(tau sum e_i^2)
+    against u = t(1-t); the printed values are the errors truncated to 5 digits."""
+    t, f, u = wl.two_sided_example1(N, g)
+    x = oracle.two_sided_solve(g, f)
+    err = math.sqrt(np.sum((x - u) ** 2) / N)
+    assert abs(_trunc5(err) - printed) <= 1e-9 * printed, (err, printed)
+
+
+@pytest.mark.parametrize("g", [0.1, 0.5, 0.9])
+def test_scheme1_order(oracle, g):
+    """Scheme 1 converges at O(tau^(2-g)) (Sec. 2): the observed rate between N = 2048 and
+    4096 is within 0.2 of 2-g (Table 1's last rates: 1.84, 1.50, 1.10)."""
+    errs = []
+    for N in (2048, 4096):
+        t, f, u = wl.two_sided_example1(N, g)
+        errs.append(math.sqrt(np.sum((oracle.two_sided_solve(g, f) - u) ** 2) / N))
+    assert abs(_rate(errs[0], errs[1]) - (2 - g)) < 0.2
+
+
+def test_scheme1_matrix_theorem1(oracle):
+    """Theorem 1: A is symmetric Toeplitz, and row i's diagonal-dominance margin
+    A_ii - sum_{j != i} |A_ij| equals 1 + mu (G_{i-1} + G_{N-1-i}) > 0 (the proof's telescoped
+    sums), with G from 60-digit decimal arithmetic."""
+    N, g = 40, 0.35
+    A = oracle.two_sided_matrix(g, N)
+    assert np.array_equal(A, A.T)
+    assert all(np.array_equal(np.diag(A, k), np.full(N - 1 - k, A[0, k])) for k in range(N - 1))
+    mu = float(d_scale(0, g, 1.0 / N))
+    Gd = [float(d_G(k, g)) for k in range(N)]
+    for i in range(1, N):
+        margin = A[i - 1, i - 1] - (np.sum(np.abs(A[i - 1])) - abs(A[i - 1, i - 1]))
+        want = 1 + mu * (Gd[i - 1] + Gd[N - 1 - i])
+        assert abs(margin - want) < 1e-12 * (1 + 2 * mu), (i, margin, want)
