@@ -222,6 +222,24 @@ ftoep_status ftoep_profile_read(ftoep_plan p, int kclass, double* total_ms, int6
 ftoep_status ftoep_matvec_noalloc(const double* a, int64_t N, const double* x, double* y, int64_t nlines,
                                   int transpose, void* cuda_stream);
 
+/* Scheme 1 (Sec. 2, Eq. 7-9): the two-sided fractional ODE
+ *     D_left^g u + D_right^g u + u = f  on (0, T),  u(0) = u(T) = 0,  0 < gamma < 1,
+ * with the left L1 formula (Eq. 4) and the right one (Eq. 5) on tau = T/N: the symmetric
+ * positive definite Toeplitz system A u = f of Eq. 9 of order N-1 (Theorem 1; first column
+ * a_0 = 1 + 2 mu G_0, a_d = mu (G_d - G_{d-1}), mu = tau^-g / Gamma(2-g)), solved by the
+ * conjugate gradient method of Sec. 2.3 with every product A w by circulant embedding
+ * (Eq. 10, the input padded with zeros) and FFTs -- the paper's fast CG.  Double precision.
+ * f, u: N-1 doubles (values at t_1 .. t_{N-1}), host or device; u holds the initial guess on
+ * entry (zeros if none) and the solution on exit.  Stops when the recursively updated
+ * residual satisfies ||r||_2 <= tol ||f||_2, or after maxit iterations.  *iters (nullable):
+ * iterations done; *relres (nullable): ||f - A u||_2 / ||f||_2 of the returned u, from a fresh
+ * product.  Allocates its device workspace and frees it before returning; ordered on
+ * cuda_stream (a cudaStream_t, NULL = legacy default stream) and blocks until done.
+ * Errors: FTOEP_EINVAL (gamma outside (0,1), N outside [2, 2^24], T <= 0, tol <= 0,
+ * maxit < 1, f or u NULL), FTOEP_ENOMEM, FTOEP_ECUDA.  Message: ftoep_last_error(NULL, ...). */
+ftoep_status ftoep_two_sided_cg(double gamma, double T, int64_t N, const double* f, double* u, double tol,
+                                int maxit, int* iters, double* relres, void* cuda_stream);
+
 /* Autotuner (no counterpart in the paper).  Times ftoep_solve on synthetic fields for
  * every candidate tuning -- time-block length fft_tile in {1024, 2048, 4096} x scheduler in
  * {levels, chain} x internal streams in {2, 4, 8} (streams only for plans of several

@@ -120,6 +120,33 @@ thread_local std::string g_create_error;
 namespace ftoep {
 // Message for ftoep_last_error(NULL, ...) from entry points that have no plan.
 void set_global_error(const char* msg) { g_create_error = msg; }
+
+// Twiddle tables W_n^k = exp(-2 pi i k/n) for every power of two n = 2 .. maxtw at offset
+// n-2 (layout of fft.cuh), in double, float and float-float, from one long-double table.
+void host_twiddles(int64_t maxtw, std::vector<double2>* h64, std::vector<float2>* h32, std::vector<float4>* hff) {
+  const size_t tot = (size_t)2 * maxtw - 2;
+  if (h64) h64->resize(tot);
+  if (h32) h32->resize(tot);
+  if (hff) hff->resize(tot);
+  std::vector<double2> big(maxtw);
+  std::vector<float4> bigff(maxtw);
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  for (int64_t k = 0; k < maxtw; ++k) {
+    long double ang = -two_pi * (long double)k / (long double)maxtw;
+    const long double c = cosl(ang), sn = sinl(ang);
+    big[k] = make_double2((double)c, (double)sn);
+    const float ch = (float)c, sh = (float)sn;
+    bigff[k] = make_float4(ch, (float)(c - (long double)ch), sh, (float)(sn - (long double)sh));
+  }
+  for (int64_t n = 2; n <= maxtw; n <<= 1) {
+    const int64_t stride = maxtw / n;
+    for (int64_t k = 0; k < n; ++k) {
+      if (h64) (*h64)[(n - 2) + k] = big[k * stride];
+      if (h32) (*h32)[(n - 2) + k] = make_float2((float)big[k * stride].x, (float)big[k * stride].y);
+      if (hff) (*hff)[(n - 2) + k] = bigff[k * stride];
+    }
+  }
+}
 }  // namespace ftoep
 
 // A solve captured as a CUDA graph for one set of device pointers (see ftoep_solve).
@@ -1100,27 +1127,10 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
   {
     pl->ntw = maxtw;
     const size_t tot = (size_t)2 * maxtw - 2;
-    std::vector<double2> h64(tot);
-    std::vector<float2> h32(tot);
-    std::vector<float4> hff(tot);
-    std::vector<double2> big(maxtw);
-    const long double two_pi = 6.283185307179586476925286766559005768L;
-    std::vector<float4> bigff(maxtw);
-    for (int64_t k = 0; k < maxtw; ++k) {
-      long double ang = -two_pi * (long double)k / (long double)maxtw;
-      const long double c = cosl(ang), sn = sinl(ang);
-      big[k] = make_double2((double)c, (double)sn);
-      const float ch = (float)c, sh = (float)sn;
-      bigff[k] = make_float4(ch, (float)(c - (long double)ch), sh, (float)(sn - (long double)sh));
-    }
-    for (int64_t n = 2; n <= maxtw; n <<= 1) {
-      const int64_t stride = maxtw / n;
-      for (int64_t k = 0; k < n; ++k) {
-        h64[(n - 2) + k] = big[k * stride];
-        h32[(n - 2) + k] = make_float2((float)big[k * stride].x, (float)big[k * stride].y);
-        hff[(n - 2) + k] = bigff[k * stride];
-      }
-    }
+    std::vector<double2> h64;
+    std::vector<float2> h32;
+    std::vector<float4> hff;
+    host_twiddles(maxtw, &h64, &h32, &hff);
     if ((st = dalloc(pl, (void**)&pl->tw64, tot * sizeof(double2))) != FTOEP_OK) return bail(st);
     if ((st = dalloc(pl, (void**)&pl->tw32, tot * sizeof(float2))) != FTOEP_OK) return bail(st);
     if ((st = dalloc(pl, &pl->twff, tot * sizeof(float4))) != FTOEP_OK) return bail(st);

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace ftoep {
 
 // ---------------------------------------------------------------- host math (weights.cpp)
@@ -15,6 +17,12 @@ void scheme_weights(int kind, double gamma, double tau, int64_t n, double* a, do
 void initial_weights(int kind, double gamma, double tau, int64_t n, double* wu0, double* wphi);
 // first column e_j (j < n) of the time operator acting on v_k = (u^k - u^{k-1})/tau
 void difference_weights(int kind, double gamma, double tau, int64_t n, double* e);
+
+// Twiddle tables W_n^k for n = 2 .. maxtw (powers of two) at offset n-2, host side
+// (api.cu); any output may be NULL.
+void host_twiddles(int64_t maxtw, std::vector<double2>* h64, std::vector<float2>* h32, std::vector<float4>* hff);
+// Message for ftoep_last_error(NULL, ...) (api.cu).
+void set_global_error(const char* msg);
 
 // ---------------------------------------------------------------- kernel launchers
 // Storage precision of the complex work arrays: 0 = double2, 1 = float2,

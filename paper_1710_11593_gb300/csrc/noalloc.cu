@@ -31,10 +31,6 @@
 #include "../../include/ftoep.h"
 #include "internal.h"
 
-namespace ftoep {
-void set_global_error(const char* msg);
-}
-
 using namespace ftoep;
 
 namespace {

@@ -28,8 +28,8 @@ FP64, MIXED = 0, 1
 SCHED_AUTO, SCHED_LEVELS, SCHED_CHAIN = 0, 1, 2
 
 EXPORTS = ("ftoep_create", "ftoep_weights", "ftoep_solve", "ftoep_matvec", "ftoep_adjoint", "ftoep_profile",
-           "ftoep_profile_read", "ftoep_matvec_noalloc", "ftoep_autotune", "ftoep_sync", "ftoep_last_error",
-           "ftoep_destroy")
+           "ftoep_profile_read", "ftoep_matvec_noalloc", "ftoep_autotune", "ftoep_two_sided_cg", "ftoep_sync",
+           "ftoep_last_error", "ftoep_destroy")
 K_BLOCK_SOLVE, K_CONV_SMEM, K_CONV_FOURSTEP, K_SINE, K_OTHER, K_RESIDUAL, K_CHAIN = range(7)
 KERNEL_CLASSES = {K_BLOCK_SOLVE: "block_solve", K_CONV_SMEM: "conv_smem", K_CONV_FOURSTEP: "conv_fourstep",
                   K_SINE: "sine", K_OTHER: "other", K_RESIDUAL: "residual", K_CHAIN: "chain"}
@@ -81,6 +81,8 @@ def load(path: Optional[str] = None):
     lib.ftoep_last_error.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.ftoep_destroy.argtypes = [vp]
     lib.ftoep_matvec_noalloc.argtypes = [vp, i64, vp, vp, i64, ci, vp]
+    lib.ftoep_two_sided_cg.argtypes = [ctypes.c_double, ctypes.c_double, i64, dp, dp, ctypes.c_double, ci,
+                                       ctypes.POINTER(ci), ctypes.POINTER(ctypes.c_double), vp]
     for name in EXPORTS:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -196,6 +198,28 @@ def ftoep_matvec_noalloc(a, N: int, x, y, nlines: int, transpose: bool = False, 
     fn = load().ftoep_matvec_noalloc
     st = current_stream_handle() if stream is None else stream
     _check(fn(_ptr(a), int(N), _ptr(x), _ptr(y), int(nlines), int(bool(transpose)), ctypes.c_void_p(st)), None)
+
+
+def two_sided_cg(f, gamma: float, T: float = 1.0, u=None, tol: float = 1e-12, maxit: int = 100000,
+                 stream: Optional[int] = None):
+    """Scheme 1 (two-sided ODE) by the fast conjugate gradient method (C ABI
+    ftoep_two_sided_cg).  f: values at t_1 .. t_{N-1} (N = len(f) + 1), numpy or torch, host
+    or device; u: initial guess (zeros if None), overwritten.  Returns (u, iterations,
+    relative residual)."""
+    n = _numel(f)
+    if u is None:
+        if isinstance(f, np.ndarray):
+            u = np.zeros_like(f)
+        else:
+            import torch
+            u = torch.zeros_like(f)
+    it = ctypes.c_int()
+    rr = ctypes.c_double()
+    st = current_stream_handle() if stream is None else stream
+    rc = load().ftoep_two_sided_cg(float(gamma), float(T), n + 1, _ptr(f), _ptr(u), float(tol), int(maxit),
+                                   ctypes.byref(it), ctypes.byref(rr), ctypes.c_void_p(st))
+    _check(rc, None)
+    return u, it.value, rr.value
 
 
 def ftoep_sync(plan: int):

@@ -1,0 +1,92 @@
+"""Scheme 1 (the two-sided fractional ODE, Sec. 2) by the fast conjugate gradient method
+on the GPU (ftoep_two_sided_cg), against the oracle's dense Gaussian elimination.
+
+* N = 32 .. 4096, gamma in {0.1, 0.5, 0.9}: the CG solution (tolerance 1e-13) equals the
+  dense solve to 1e-10 relative, and its error against u = t(1-t) reproduces every printed
+  value of Table 1 (truncated to 5 digits).
+* N = 2^16, 2^18, 2^20 (beyond the dense solve): the returned relative residual is below the
+  tolerance, and the residual of sampled rows computed here in O(N) from the oracle's first
+  column agrees; the error against t(1-t) falls at the order 2 - gamma from 2^16 to 2^18.
+* Host buffers take the same path.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1710_11593_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def ft():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_11593_gb300 import ftoep
+    ftoep.load()
+    return ftoep
+
+
+def _trunc5(x):
+    e = math.floor(math.log10(x))
+    return math.floor(x / 10 ** (e - 4)) * 10 ** (e - 4)
+
+
+def _table1():
+    rows = []
+    with open(os.path.join(HERE, "golden", "table1.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                a, b, c = line.split()
+                rows.append((int(a), float(b), float(c)))
+    return rows
+
+
+@pytest.mark.parametrize("N,g,printed", _table1())
+def test_fast_cg_vs_dense_and_table1(ft, oracle, N, g, printed):
+    import torch
+    t, f, u_exact = wl.two_sided_example1(N, g)
+    u, iters, rel = ft.two_sided_cg(torch.from_numpy(f).cuda(), g, tol=1e-13)
+    u = u.cpu().numpy()
+    ref = oracle.two_sided_solve(g, f)
+    assert np.linalg.norm(u - ref) / np.linalg.norm(ref) < 1e-10, iters
+    assert rel < 1e-12 and 0 < iters < N
+    err = math.sqrt(np.sum((u - u_exact) ** 2) / N)
+    assert abs(_trunc5(err) - printed) <= 1e-9 * printed, (err, printed)
+
+
+def test_fast_cg_large(ft, oracle):
+    import torch
+    g = 0.5
+    errs = []
+    for N, tol in ((2 ** 16, 1e-13), (2 ** 18, 1e-13), (2 ** 20, 1e-12)):
+        t, f, u_exact = wl.two_sided_example1(N, g)
+        u, iters, rel = ft.two_sided_cg(torch.from_numpy(f).cuda(), g, tol=tol)
+        u = u.cpu().numpy()
+        assert rel < 10 * tol, (N, rel, iters)
+        a = oracle.two_sided_column(g, N)
+        rng = np.random.default_rng(N)
+        for i in rng.integers(0, N - 1, 24):
+            row = a[np.abs(np.arange(N - 1) - i)]
+            assert abs(f[i] - row @ u) < 20 * tol * np.linalg.norm(f), (N, i)
+        errs.append(math.sqrt(np.sum((u - u_exact) ** 2) / N))
+    # discretisation error at O(tau^(2-g)) from N = 2^16 to 2^18 (CG error far below it)
+    rate = math.log2(errs[0] / errs[1]) / 2
+    assert abs(rate - (2 - g)) < 0.1, errs
+
+
+def test_fast_cg_host_buffers_and_initial_guess(ft, oracle):
+    N, g = 1000, 0.3
+    t, f, u_exact = wl.two_sided_example1(N, g)
+    u0 = np.full(N - 1, 0.1)
+    u, iters, rel = ft.two_sided_cg(f, g, u=u0.copy(), tol=1e-13)
+    ref = oracle.two_sided_solve(g, f)
+    assert isinstance(u, np.ndarray) and np.linalg.norm(u - ref) / np.linalg.norm(ref) < 1e-10
+    # a converged solution as the guess: no iteration needed
+    u2, iters2, rel2 = ft.two_sided_cg(f, g, u=ref.copy(), tol=1e-10)
+    assert iters2 == 0 and rel2 < 1e-10

@@ -85,3 +85,20 @@ def test_tuning_key_buckets_and_cache_roundtrip(tmp_path, monkeypatch):
     monkeypatch.setitem(sys.modules, "torch", None)  # no device name: the key of the stored entry
     got, hit = ftoep.autotune_cached(a, path=str(path))
     assert hit and got == want
+
+
+@pytest.mark.parametrize("kw", [dict(gamma=1.2), dict(gamma=0.0), dict(N=1), dict(tol=0.0), dict(maxit=0),
+                                dict(T=-1.0)])
+def test_two_sided_cg_validates_before_any_device_work(kw):
+    """Argument checks of ftoep_two_sided_cg return FTOEP_EINVAL before touching CUDA."""
+    import numpy as np
+    from paper_1710_11593_gb300 import ftoep
+    args = dict(gamma=0.5, T=1.0, N=10, tol=1e-10, maxit=10)
+    args.update(kw)
+    f = np.ones(max(1, args["N"] - 1))
+    u = np.zeros_like(f)
+    lib = ftoep.load()
+    import ctypes
+    rc = lib.ftoep_two_sided_cg(args["gamma"], args["T"], args["N"], f.ctypes.data, u.ctypes.data, args["tol"],
+                                args["maxit"], None, None, None)
+    assert rc == ftoep.FTOEP_EINVAL
