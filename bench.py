@@ -25,6 +25,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -40,7 +42,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["diffusion", "wave", "scalar", "batched"])
+    ap.add_argument("--workload", default="batched", choices=["diffusion", "wave", "scalar", "batched", "twosided"])
     ap.add_argument("--nprob", type=int, default=512, help="batched workload: number of problems")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
                     help="default: fp64 for diffusion/scalar, mixed for wave")
@@ -694,12 +696,60 @@ def run_ours(args):
     return 0
 
 
+def run_twosided(args):
+    """Scheme 1 (two-sided ODE, Example 1, gamma 0.5) by the fast conjugate gradient method:
+    one step = one solve to relative residual 1e-12 from a zero guess, f resident in HBM."""
+    import torch
+    from paper_1710_11593_gb300 import ftoep, workloads as wl
+    rk = Ranks()
+    torch.cuda.set_device(rk.local)
+    ftoep.load()
+    N = args.N or 2 ** 20
+    g, tol = 0.5, 1e-12
+    t, fh, uex = wl.two_sided_example1(N, g)
+    f = torch.from_numpy(fh).cuda()
+    u = torch.zeros_like(f)
+    for _ in range(args.warmup):
+        u.zero_()
+        ft_u, iters, rel = ftoep.two_sided_cg(f, g, u=u, tol=tol)
+    torch.cuda.synchronize()
+    rk.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u.zero_()
+        _, iters, rel = ftoep.two_sided_cg(f, g, u=u, tol=tol)
+    torch.cuda.synchronize()
+    sec = rk.max((time.perf_counter() - t0) / args.steps)
+    err = float(np.sqrt(np.sum((u.cpu().numpy() - uex) ** 2) / N))
+    cpu = None
+    if rk.rank == 0 and not args.no_cpu_baseline:
+        from oracle import oracle as orc
+        n0 = 4096
+        _, f0, _ = wl.two_sided_example1(n0, g)
+        c0 = time.perf_counter()
+        orc.two_sided_solve(g, f0)
+        dt = time.perf_counter() - c0
+        cpu = {"value": (n0 - 1) / dt, "unit": "unknowns/s", "cores": orc.default_threads(), "kind": "oracle",
+               "sample": f"dense Gaussian elimination of Scheme 1 at N = {n0} ({dt:.2f} s)"}
+    if rk.rank == 0:
+        print(json.dumps({"metric": "Scheme 1 unknowns/s (fast CG to 1e-12 relative residual)",
+                          "value": rk.world * (N - 1) / sec, "unit": "unknowns/s", "n_gpus": rk.world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": {"workload": f"two_sided_example1_g0.5_N{N}", "tol": tol},
+                          "iterations": iters, "relres": rel, "l2_error_vs_exact": err, "cpu_baseline": cpu}))
+    rk.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "twosided":
+        return run_twosided(args)
     return run_ours(args)
 
 

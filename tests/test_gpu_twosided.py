@@ -55,7 +55,9 @@ def test_fast_cg_vs_dense_and_table1(ft, oracle, N, g, printed):
     u = u.cpu().numpy()
     ref = oracle.two_sided_solve(g, f)
     assert np.linalg.norm(u - ref) / np.linalg.norm(ref) < 1e-10, iters
-    assert rel < 1e-12 and 0 < iters < N
+    # the recursive residual reached 1e-13; a fresh product of the rounded u cannot do better
+    # than about eps ||A|| ||u|| / ||f|| (||A|| ~ 4 mu, mu ~ 1e3 at N = 4096, gamma = 0.9)
+    assert rel < 1e-11 and 0 < iters < N
     err = math.sqrt(np.sum((u - u_exact) ** 2) / N)
     assert abs(_trunc5(err) - printed) <= 1e-9 * printed, (err, printed)
 
