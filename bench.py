@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-singles", action="store_true", help="batched: skip the single-problem lines")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) leg (profiling runs)")
+    ap.add_argument("--no-tune", action="store_true", help="batched: library default tuning instead of the autotuner's")
     ap.add_argument("--scheduler", type=int, default=0, choices=[0, 1, 2],
                     help="single workloads: 0 library choice, 1 per-level launches, 2 persistent chain")
     ap.add_argument("--M", type=int, default=None, help="override the workload's interior points (profiling cases)")
@@ -492,7 +493,10 @@ def run_batched(args):
     units = sum(p.M * p.N for p in probs)
     f = batch_field(probs)
     u = torch.empty_like(f)
-    plan = ftoep.Plan(specs)
+    # the autotuner's choice for this batch: the user's cache or the table shipped with the
+    # package (written by paper_1710_11593_gb300/tune_table.py on a GB300), else a search
+    tuning, cached = (None, None) if args.no_tune else ftoep.autotune_cached(specs)
+    plan = ftoep.Plan(specs, tuning=tuning)
     ms, launches, clk = timed(plan, f, u, args.steps, args.warmup, rk, local)
     prof = class_profile(plan, f, u)
     ms = rk.max(ms)
@@ -540,13 +544,20 @@ def run_batched(args):
         e2e = {"unavailable": str(exc)[:200]}
     if plan is not None:
         plan.close()
+    # the library's default tuning on the same batch, for comparison with the tuned step
+    default = None
+    if tuning is not None:
+        with ftoep.Plan(specs) as dplan:
+            dms, _, _ = timed(dplan, f, u, max(1, min(args.steps, 5)), 2, rk, local, clocks=False)
+        default = {"ms_per_step": rk.max(dms), "tuned_speedup": rk.max(dms) / ms}
     compare = None
     if not args.no_compare:
         other = "fp64" if precision == "mixed" else "mixed"
         specs2 = [ftoep.ProblemSpec(p.kind, p.gamma, p.N, p.M, p.space,
                                     ftoep.FP64 if other == "fp64" else ftoep.MIXED) for p in probs]
         u2 = torch.empty_like(f)
-        with ftoep.Plan(specs2) as plan2:
+        tuning2 = None if args.no_tune else ftoep.autotune_cached(specs2)[0]
+        with ftoep.Plan(specs2, tuning=tuning2) as plan2:
             # two warm-up solves: the first runs directly, the second captures the graph, so
             # the timed solve is a replay like the timed steps of the main leg
             ms2, launches2, _ = timed(plan2, f, u2, 1, 2, rk, local, clocks=False)
@@ -567,7 +578,7 @@ def run_batched(args):
                 fl2[kk] = fl2.get(kk, 0.0) + vv
         solve_flops = fl2["chain"] + fl2["sine"]
         compare = {"precision": other, "value": world * units / (ms2 * 1e-3), "ms_per_step": ms2,
-                   "gpu_launches": launches2,
+                   "gpu_launches": launches2, "tuning": tuning2,
                    "mixed_speedup_vs_fp64": (ms2 / ms) if other == "fp64" else (ms / ms2),
                    "mixed_rel_err_vs_fp64_gpu_worst_problem": worst}
         if other == "fp64":
@@ -595,10 +606,10 @@ def run_batched(args):
                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f32+f64", "data": "synthetic",
                "config": {"workload": wname, "nprob": len(probs), "unknowns": units, "precision": precision,
-                          "scheduler": "chain",
+                          "tuning": tuning or "library default", "tuning_from_cache": cached,
                           "l2": f"inputs larger than L2 (f = {units * 8 / 1e9:.1f} GB)"},
                "roofline": roof, "kernel_time_share": shares, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-               "gpu_launches": launches, "compare": compare, "singles": singles}
+               "gpu_launches": launches, "default_tuning": default, "compare": compare, "singles": singles}
         print(json.dumps(out))
     rk.close()
     return 0

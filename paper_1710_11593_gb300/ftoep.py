@@ -256,6 +256,14 @@ def tuning_key(problems: Sequence[ProblemSpec], device: str = "") -> str:
     return f"{device}|{items}"
 
 
+SHIPPED_TUNING = os.path.join(HERE, "tuned_gb300.json")
+TUNING_FIELDS = ("leaf", "fft_tile", "gemm_max_level", "scheduler", "streams")
+
+
+def _tuning_fields(entry: dict) -> dict:
+    return {k: int(entry.get(k, 0)) for k in TUNING_FIELDS}
+
+
 def tuning_cache_path() -> str:
     return os.environ.get("FTOEP_TUNE_CACHE") or os.path.join(os.path.expanduser("~"), ".cache", "ftoep",
                                                                "tuning.json")
@@ -282,7 +290,14 @@ def autotune_cached(problems: Sequence[ProblemSpec], stream: Optional[int] = Non
     except (OSError, ValueError):
         cache = {}
     if key in cache:
-        return dict(cache[key]), True
+        return _tuning_fields(cache[key]), True
+    try:  # the table shipped with the package (tune_table.py), read-only
+        with open(SHIPPED_TUNING) as fh:
+            shipped = json.load(fh)
+        if key in shipped:
+            return _tuning_fields(shipped[key]), True
+    except (OSError, ValueError):
+        pass
     tuning = ftoep_autotune(problems, stream)
     cache[key] = tuning
     try:
