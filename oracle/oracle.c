@@ -31,6 +31,12 @@
  *         c*M_0 u^n + c(M_1-2M_0) u^{n-1} + c sum_{k=1}^{n-2} W_{n-k} u^k
  *             + c(M_{n-2}-M_{n-1}) u^0 - c*tau*M_{n-1} phi - (u_xx)_h^n = f^{n-1/2}
  *     with W_j = M_{j-2} - 2M_{j-1} + M_j and M_{-1} = 0.
+ *   - kind 2: the same hyperbolic time discretization (Eq. 15) with the spatial term
+ *     taken as the average of levels n and n-1, the Crank-Nicolson form of the scheme
+ *     that Eq. 15 is taken from (Sun and Wu, cited in Sec. 3 for Eq. 15):
+ *         [same time terms as kind 1] - (u_xx)_h^{n-1/2} = f^{n-1/2},
+ *         (u_xx)_h^{n-1/2} = ((u_xx)_h^n + (u_xx)_h^{n-1})/2,  u^{n-1} = u^0 at n = 1,
+ *     which moves half of the spatial operator to the previous level: O(tau^(3-g) + h^2).
  *   - the scalar problem D^g u = -lambda u + f on the same time grid (no space).
  *   - the transposed (adjoint) system, marched backwards in time.
  *   - the orthonormal sine projection of one spatial mode, and a dense Toeplitz
@@ -66,7 +72,9 @@ typedef __float128 qreal;
 #define OR_EINVAL 1
 #define OR_ENOMEM 2
 
-/* kind: 0 = sub-diffusion L1 (0<g<1), 1 = hyperbolic L1 (1<g<2). */
+/* kind: 0 = sub-diffusion L1 (0<g<1), 1 = hyperbolic L1 (1<g<2), 2 = hyperbolic L1 with
+ * the spatial term averaged over levels n and n-1 (1<g<2).  Kinds 1 and 2 share every
+ * time weight; kind_time() maps a kind to the family of its weights. */
 /* space: 0 = scalar (D^g u = -lambda u + f), 1 = Dirichlet Laplacian on (0, L). */
 
 /* k^beta in binary128, with 0^beta = 0 for beta > 0. */
@@ -90,15 +98,36 @@ static qreal q_M(int64_t k, qreal g) {
 
 /* Scale of the time stencil: mu = tau^-g/Gamma(2-g) (Lemma 2) or
  * c = tau^-g/Gamma(3-g) (Eq. 17), in binary128. */
+static int kind_time(int kind);
+
 static qreal q_scale(int kind, qreal g, qreal tau) {
+  kind = kind_time(kind);
   qreal p = QEXP(-g * QLOG(tau));
   return kind == 0 ? p / QTGAMMA(QLIT(2.0) - g) : p / QTGAMMA(QLIT(3.0) - g);
 }
 
 static int check_kind(int kind, double g) {
   if (kind == 0) return (g > 0.0 && g < 1.0) ? OR_OK : OR_EINVAL;
-  if (kind == 1) return (g > 1.0 && g < 2.0) ? OR_OK : OR_EINVAL;
+  if (kind == 1 || kind == 2) return (g > 1.0 && g < 2.0) ? OR_OK : OR_EINVAL;
   return OR_EINVAL;
+}
+
+static int kind_time(int kind) { return kind == 2 ? 1 : kind; }
+
+/* Weight of the level-n spatial operator in the level-n row: 1, or 1/2 for kind 2 (the
+ * other half acts on level n-1). */
+static qreal space_weight(int kind) { return kind == 2 ? QLIT(0.5) : QLIT(1.0); }
+
+/* (S w)_j for the spatial operator S of the left-hand side: -(w_{j-1} - 2w_j + w_{j+1})/h^2
+ * (space 1, zero boundary values) or lambda w_j (space 0), of the double-pair field
+ * wh + wl at stride `stride` (row j at j*stride), in binary128. */
+static qreal apply_space(int space, int64_t M, int64_t j, const double* wh, const double* wl, int64_t stride,
+                         qreal inv_h2, qreal lambda) {
+  const qreal c = (qreal)wh[j * stride] + (qreal)(wl ? wl[j * stride] : 0.0);
+  if (space == 0) return lambda * c;
+  const qreal lft = j > 0 ? (qreal)wh[(j - 1) * stride] + (qreal)(wl ? wl[(j - 1) * stride] : 0.0) : QLIT(0.0);
+  const qreal rgt = j + 1 < M ? (qreal)wh[(j + 1) * stride] + (qreal)(wl ? wl[(j + 1) * stride] : 0.0) : QLIT(0.0);
+  return (QLIT(2.0) * c - lft - rgt) * inv_h2;
 }
 
 /* G_k for k = 0..K-1, rounded to double. */
@@ -121,6 +150,7 @@ int or_M(double g, int64_t K, double* out) {
  *   kind 1 (Eq. 17):    j = 0: M_0;  j = 1: M_1 - 2 M_0;  j >= 2: W_j = M_{j-2} - 2M_{j-1} + M_j
  * The full left-hand coefficient is scale * coef[j]. */
 static qreal q_coef(int kind, int64_t j, qreal g) {
+  kind = kind_time(kind);
   if (kind == 0) {
     if (j == 0) return q_G(0, g);
     return -(q_G(j - 1, g) - q_G(j, g));
@@ -166,6 +196,7 @@ int or_time_coeffs_dgamma(int kind, double g, double tau, int64_t N, double* out
 int or_initial_weights(int kind, double g, double tau, int64_t N, double* w_u0, double* w_phi) {
   if (check_kind(kind, g) != OR_OK || N < 1 || !w_u0 || !w_phi) return OR_EINVAL;
   qreal s = q_scale(kind, (qreal)g, (qreal)tau);
+  kind = kind_time(kind);
   for (int64_t n = 1; n <= N; ++n) {
     if (kind == 0) {
       w_u0[n - 1] = (double)(s * q_G(n - 1, (qreal)g));
@@ -256,20 +287,25 @@ int or_march(int kind, int space, double g, double T, double Lx, double lambda, 
   const qreal qs = q_scale(kind, (qreal)g, (qreal)tau);
   for (int64_t j = 0; j < N; ++j) q_split(qs * q_coef(kind, j, (qreal)g), &rh[N - 1 - j], &rl[N - 1 - j]);
   or_initial_weights(kind, g, tau, N, wu0, wphi);
-  /* level matrix: a_0 + 2/h^2 on the diagonal, -1/h^2 off it (binary128) */
-  qreal diag, off;
+  /* level matrix: a_0 + sw*2/h^2 on the diagonal, -sw/h^2 off it (binary128), sw the
+   * weight of the level-n spatial operator (1/2 for kind 2, whose other half acts on
+   * level n-1 and moves to the right-hand side) */
+  qreal diag, off, inv_h2 = QLIT(0.0);
   const qreal a0 = qs * q_coef(kind, 0, (qreal)g);
+  const qreal sw = space_weight(kind);
   if (space == 1) {
     qreal h = (qreal)Lx / (qreal)(M + 1);
-    diag = a0 + QLIT(2.0) / (h * h);
-    off = QLIT(-1.0) / (h * h);
+    inv_h2 = QLIT(1.0) / (h * h);
+    diag = a0 + sw * QLIT(2.0) * inv_h2;
+    off = -sw * inv_h2;
   } else {
-    diag = a0 + (qreal)lambda;
+    diag = a0 + sw * (qreal)lambda;
     off = QLIT(0.0);
   }
   if (nthreads < 1) nthreads = 1;
   for (int64_t n = 1; n <= N; ++n) {
-    /* r_j = f_j^n - sum_{k=1}^{n-1} a_{n-k} u_j^k (+ initial-data terms) */
+    /* r_j = f_j^n - sum_{k=1}^{n-1} a_{n-k} u_j^k (+ initial-data terms)
+     *       [kind 2: - (1/2) (S u^{n-1})_j, u^0 the initial value] */
 #pragma omp parallel for num_threads(nthreads) schedule(static)
     for (int64_t j = 0; j < M; ++j) {
       qreal s = QLIT(0.0);
@@ -277,6 +313,12 @@ int or_march(int kind, int space, double g, double T, double Lx, double lambda, 
       qreal r = (qreal)f[j * N + (n - 1)] - s;
       if (u0) r += (qreal)wu0[n - 1] * (qreal)u0[j];
       if (phi) r += (qreal)wphi[n - 1] * (qreal)phi[j];
+      if (kind == 2) {
+        if (n > 1)
+          r -= (QLIT(1.0) - sw) * apply_space(space, M, j, u + (n - 2), ulo + (n - 2), N, inv_h2, (qreal)lambda);
+        else if (u0)
+          r -= (QLIT(1.0) - sw) * apply_space(space, M, j, u0, NULL, 1, inv_h2, (qreal)lambda);
+      }
       rq[j] = r;
     }
     if (space == 1) {
@@ -314,22 +356,28 @@ int or_adjoint_march(int kind, int space, double g, double T, double Lx, double 
   }
   const qreal qs = q_scale(kind, (qreal)g, (qreal)tau);
   for (int64_t j = 0; j < N; ++j) q_split(qs * q_coef(kind, j, (qreal)g), &ah[j], &al[j]);
-  qreal diag, off;
+  qreal diag, off, inv_h2 = QLIT(0.0);
   const qreal a0 = qs * q_coef(kind, 0, (qreal)g);
+  const qreal sw = space_weight(kind);
   if (space == 1) {
     qreal h = (qreal)Lx / (qreal)(M + 1);
-    diag = a0 + QLIT(2.0) / (h * h);
-    off = QLIT(-1.0) / (h * h);
+    inv_h2 = QLIT(1.0) / (h * h);
+    diag = a0 + sw * QLIT(2.0) * inv_h2;
+    off = -sw * inv_h2;
   } else {
-    diag = a0 + (qreal)lambda;
+    diag = a0 + sw * (qreal)lambda;
     off = QLIT(0.0);
   }
   if (nthreads < 1) nthreads = 1;
   for (int64_t n = N; n >= 1; --n) {
+    /* kind 2: the level-(n+1) row holds (1/2) S u^n, so the transposed row n holds
+     * (1/2) S lam^{n+1} (S symmetric) */
 #pragma omp parallel for num_threads(nthreads) schedule(static)
     for (int64_t j = 0; j < M; ++j) {
       qreal s = QLIT(0.0);
       if (n < N) dd_dot(ah + 1, al + 1, lam + j * N + n, llo + j * N + n, N - n, &s);
+      if (kind == 2 && n < N)
+        s += (QLIT(1.0) - sw) * apply_space(space, M, j, lam + n, llo + n, N, inv_h2, (qreal)lambda);
       rq[j] = (qreal)gin[j * N + (n - 1)] - s;
     }
     if (space == 1) {

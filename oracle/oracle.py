@@ -9,7 +9,9 @@ of what the paper defines (Liu, Cheng, Li, Wang, arXiv 1710.11593):
 * ``time_coeffs``, ``scale``: the left-hand coefficients of Eq. 19/20 (kind 0) and of
   Eq. 17 (kind 1), first column of the lower-triangular Toeplitz time operator.
 * ``march``: the direct time-marching procedure of Eq. 20 (and its hyperbolic and
-  scalar analogues), O(M N^2), with a Thomas solve per level.
+  scalar analogues), O(M N^2), with a Thomas solve per level.  Kind 2 is the hyperbolic
+  time discretization of Eq. 15 with the spatial term averaged over levels n and n-1
+  (the Crank-Nicolson form of the scheme Eq. 15 is taken from).
 * ``adjoint_march``: the transposed system, marched backwards.
 * ``sine_project`` / ``march_mode``: one orthonormal sine mode, marched as a scalar
   problem with the mode's eigenvalue (used for sampled-mode checks).
@@ -31,6 +33,7 @@ _lib = None
 
 SUBDIFFUSION = 0
 HYPERBOLIC = 1
+HYPERBOLIC_CN = 2
 SPACE_NONE = 0
 SPACE_DIRICHLET = 1
 

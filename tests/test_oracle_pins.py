@@ -238,6 +238,56 @@ def test_hyperbolic_initial_data(oracle):
     assert errs[-1] < 1e-2 and all(r > 0.8 for r in rates), (errs, rates)
 
 
+def _cn_errors(oracle, kind, g, lam, Ns, u0=None, phi=None, space=0, M=1):
+    """Max error at the time levels of u = t^3 (+ 1 + 2t with u0 = 1, phi = 2), f at
+    t_{n-1/2}.  space 1: the discrete eigenvector sin(pi x_j) with its eigenvalue, so the
+    semi-discrete solution is exact and only the time error remains."""
+    errs = []
+    dc, dp = wl.caputo_power(3.0, g)
+    for N in Ns:
+        th = wl.time_points(1, N)
+        t = wl.time_points(0, N)
+        base = (1.0 + 2.0 * th if u0 is not None else 0.0)
+        ex = (1.0 + 2.0 * t if u0 is not None else 0.0) + t ** 3
+        if space == 0:
+            f = (dc * th ** dp + lam * (base + th ** 3))[None, :]
+            u = oracle.march(kind, 0, g, f, lam=lam, u0=u0, phi=phi)[0]
+            errs.append(np.max(np.abs(u - ex)))
+        else:
+            x = wl.space_points(M)
+            lam1 = oracle.mode_eigenvalue(1, M)
+            sx = np.sin(np.pi * x)
+            f = np.outer(sx, dc * th ** dp + lam1 * th ** 3)
+            u = oracle.march(kind, 1, g, f)
+            errs.append(np.max(np.abs(u - np.outer(sx, t ** 3))))
+    return errs
+
+
+@pytest.mark.parametrize("g", [1.5, 1.8])
+def test_crank_nicolson_order(oracle, g):
+    """Kind 2 (spatial term averaged over levels n and n-1) reaches the O(tau^(3-g)) order
+    of the time discretization Eq. 15; kind 1 (spatial term at level n) stays first order.
+    u = t^3, scalar (lambda = 5) and the discrete sine eigenvector (M = 15)."""
+    Ns = (512, 1024, 2048)
+    for space in (0, 1):
+        e2 = _cn_errors(oracle, 2, g, 5.0, Ns, space=space, M=15)
+        e1 = _cn_errors(oracle, 1, g, 5.0, Ns, space=space, M=15)
+        r2, r1 = _rate(e2[-2], e2[-1]), _rate(e1[-2], e1[-1])
+        assert abs(r2 - (3.0 - g)) < 0.06, (space, e2, r2)
+        assert abs(r1 - 1.0) < 0.1, (space, e1, r1)
+        assert e2[-1] < e1[-1] / 2
+
+
+def test_crank_nicolson_initial_data(oracle):
+    """u = 1 + 2t + t^3 (u^0 = 1, phi = 2): the time discretization is exact on 1 + 2t, so
+    with correct u^0 and phi terms (including the level-1 average with u^0) the error is
+    the error of u = t^3 alone."""
+    Ns = (128, 512)
+    a = _cn_errors(oracle, 2, 1.5, 5.0, Ns)
+    b = _cn_errors(oracle, 2, 1.5, 5.0, Ns, u0=np.array([1.0]), phi=np.array([2.0]))
+    np.testing.assert_allclose(b, a, rtol=1e-6)
+
+
 # ----------------------------------------------------------------- dense brute force
 
 def _dense_system(kind, space, g, M, N, lam=1.0):
@@ -254,25 +304,31 @@ def _dense_system(kind, space, g, M, N, lam=1.0):
         K = (np.diag(np.full(M, 2.0)) - np.diag(np.ones(M - 1), 1) - np.diag(np.ones(M - 1), -1)) / h ** 2
     else:
         K = lam * np.eye(M)
-    A = np.kron(np.eye(M), T) + np.kron(K, np.eye(N))
+    # the spatial operator at level n (kinds 0, 1), or averaged over levels n and n-1
+    # (kind 2: half on the diagonal block, half on the block below it)
+    Ts = np.eye(N) if kind != 2 else 0.5 * (np.eye(N) + np.eye(N, k=-1))
+    A = np.kron(np.eye(M), T) + np.kron(K, Ts)
     if kind == 0:
         wu0 = np.array([float(s * d_G(n - 1, g)) for n in range(1, N + 1)])
         wphi = np.zeros(N)
     else:
         wu0 = np.array([float(s * (d_M(n - 1, g) - d_M(n - 2, g))) for n in range(1, N + 1)])
         wphi = np.array([float(s * Decimal(tau) * d_M(n - 1, g)) for n in range(1, N + 1)])
-    return A, wu0, wphi
+    return A, wu0, wphi, K
 
 
-@pytest.mark.parametrize("kind,space,g", [(0, 1, 0.3), (0, 0, 0.8), (1, 1, 1.4), (1, 0, 1.8)])
+@pytest.mark.parametrize("kind,space,g", [(0, 1, 0.3), (0, 0, 0.8), (1, 1, 1.4), (1, 0, 1.8), (2, 1, 1.6),
+                                          (2, 0, 1.2)])
 def test_march_vs_dense_solve(oracle, kind, space, g):
     M, N = 6, 20
     rng = np.random.default_rng(7)
     f = rng.standard_normal((M, N))
     u0 = rng.standard_normal(M)
-    phi = rng.standard_normal(M) if kind == 1 else None
-    A, wu0, wphi = _dense_system(kind, space, g, M, N, lam=2.5)
+    phi = rng.standard_normal(M) if kind in (1, 2) else None
+    A, wu0, wphi, K = _dense_system(kind, space, g, M, N, lam=2.5)
     rhs = f + np.outer(u0, wu0) + (np.outer(phi, wphi) if phi is not None else 0.0)
+    if kind == 2:  # the level-1 row averages the spatial operator with u^0
+        rhs[:, 0] -= 0.5 * K @ u0
     ref = np.linalg.solve(A, rhs.reshape(-1)).reshape(M, N)
     u = oracle.march(kind, space, g, f, lam=2.5, u0=u0, phi=phi)
     np.testing.assert_allclose(u, ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
@@ -325,7 +381,7 @@ def test_sine_project_orthonormal(oracle):
     np.testing.assert_allclose(lap, oracle.mode_eigenvalue(3, M) * v, rtol=1e-12)
 
 
-@pytest.mark.parametrize("kind,g", [(0, 0.7), (1, 1.5)])
+@pytest.mark.parametrize("kind,g", [(0, 0.7), (1, 1.5), (2, 1.7)])
 def test_per_mode_march_matches_full_march(oracle, kind, g):
     M, N = 15, 48
     rng = np.random.default_rng(11)
@@ -339,7 +395,7 @@ def test_per_mode_march_matches_full_march(oracle, kind, g):
 
 # ----------------------------------------------------------------- adjoint and gradient
 
-@pytest.mark.parametrize("kind,g", [(0, 0.6), (1, 1.3)])
+@pytest.mark.parametrize("kind,g", [(0, 0.6), (1, 1.3), (2, 1.6)])
 def test_adjoint_dot_product(oracle, kind, g):
     M, N = 9, 64
     rng = np.random.default_rng(5)
