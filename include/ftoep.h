@@ -18,6 +18,11 @@
  *   FTOEP_L1_HYPERBOLIC (1 < g < 2): Eq. 15/17 at t_{n-1/2} with c = tau^-g/Gamma(3-g),
  *       a_0 = c, a_1 = c(M_1 - 2M_0), a_j = c(M_{j-2} - 2M_{j-1} + M_j),
  *       M_k = (k+1)^(2-g) - k^(2-g); spatial term taken at level n.
+ *   FTOEP_L1_HYPERBOLIC_CN (1 < g < 2): the same time terms (Eq. 15, the same first
+ *       column a) with the spatial term averaged over levels n and n-1,
+ *       (u_xx^n + u_xx^{n-1})/2, u^0 = u0: the Crank-Nicolson form of the scheme that
+ *       Eq. 15 is taken from (Sun and Wu, cited for Eq. 15), O(tau^(3-g) + h^2).  In the
+ *       difference form below only the diagonal changes: E + lambda_m tau (1 - I/2).
  *   Space: central second difference with Dirichlet zeros (Eq. 19).
  * With the unknowns of one spatial point ordered in time (the reordering of Sec. 3,
  * "U_i = (U_i^1, ..., U_i^N)"), the time operator is lower-triangular Toeplitz with
@@ -76,7 +81,8 @@ typedef enum {
 
 typedef enum {
   FTOEP_L1_SUBDIFFUSION = 0, /* 0 < gamma < 1, Eq. 4/19                                 */
-  FTOEP_L1_HYPERBOLIC = 1    /* 1 < gamma < 2, Eq. 15/17                                */
+  FTOEP_L1_HYPERBOLIC = 1,   /* 1 < gamma < 2, Eq. 15/17                                */
+  FTOEP_L1_HYPERBOLIC_CN = 2 /* 1 < gamma < 2, Eq. 15 time terms, spatial term averaged */
 } ftoep_kind;
 
 typedef enum {

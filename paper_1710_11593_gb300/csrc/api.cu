@@ -38,6 +38,8 @@ constexpr int kDotBlocks = 1024;
 
 struct Prob {
   ftoep_problem d{};
+  int tk = 0;                   // family of the time weights: 0 (L1, Eq. 4/19) or 1 (Eq. 15/17)
+  double sw = 1.0;              // share of the spatial operator on the level-n diagonal (1/2: Crank-Nicolson)
   int64_t N = 0, M = 0, Np = 0, P = 0;
   int logNp = 0, logK2 = 0;
   double tau = 0, h = 0, scale = 0;
@@ -56,7 +58,7 @@ struct Prob {
   double* e = nullptr;          // first column in the difference form (solve kernel)
   double* wu0 = nullptr;
   double* wphi = nullptr;
-  double2* invdiag = nullptr;   // per pair 1/(e_0 + lambda tau)
+  double2* invdiag = nullptr;   // per pair 1/(e_0 + sw lambda tau)
   double2* lamtau = nullptr;    // per pair lambda tau
   // sine transform for M+1 not a power of two (Bluestein tables, double and float)
   bool bluestein = false;
@@ -324,7 +326,7 @@ ftoep_status validate(const ftoep_problem& d, int i, const ftoep_tuning* tune) {
   ftoep_plan pl = nullptr;
   if (d.kind == FTOEP_L1_SUBDIFFUSION) {
     if (!(d.gamma > 0.0 && d.gamma < 1.0)) return fail(pl, FTOEP_EINVAL, "problem %d: gamma %g not in (0,1)", i, d.gamma);
-  } else if (d.kind == FTOEP_L1_HYPERBOLIC) {
+  } else if (d.kind == FTOEP_L1_HYPERBOLIC || d.kind == FTOEP_L1_HYPERBOLIC_CN) {
     if (!(d.gamma > 1.0 && d.gamma < 2.0)) return fail(pl, FTOEP_EINVAL, "problem %d: gamma %g not in (1,2)", i, d.gamma);
   } else {
     return fail(pl, FTOEP_EINVAL, "problem %d: unknown kind %d", i, d.kind);
@@ -543,7 +545,7 @@ ftoep_status rhs_forward(ftoep_plan pl, Ws& w, Prob& pb, void* z, const double* 
   DstArgs da = dst_args(pl, pb, pb.prec, z);
   da.f = f;
   da.u0 = u0;
-  da.phi = (pb.d.kind == FTOEP_L1_HYPERBOLIC) ? phi : nullptr;
+  da.phi = (pb.tk == 1) ? phi : nullptr;
   da.wu0 = pb.wu0;
   da.wphi = pb.wphi;
   da.diff_form = 1;
@@ -578,7 +580,9 @@ ftoep_status after_first_solve(ftoep_plan pl, Ws& w, Prob& pb, void* z, const do
   ResidualArgs ra{};
   ra.f = f;
   ra.u0 = nullptr;
-  ra.phi = (pb.d.kind == FTOEP_L1_HYPERBOLIC) ? phi : nullptr;
+  ra.phi = (pb.tk == 1) ? phi : nullptr;
+  ra.cn = pb.sw != 1.0;
+  ra.uprev0 = u0;  // Crank-Nicolson: the level before the first is u0 (zero if NULL)
   ra.wu0 = pb.wu0;
   ra.wphi = pb.wphi;
   ra.u = u;
@@ -847,10 +851,10 @@ ftoep_status setup_problem(ftoep_plan pl, Prob& pb) {
   const int64_t N = pb.N, Np = pb.Np;
   pb.h_a.resize(Np);
   pb.h_dadg.resize(Np);
-  scheme_weights(pb.d.kind, pb.d.gamma, pb.tau, Np, pb.h_a.data(), pb.h_dadg.data());
+  scheme_weights(pb.tk, pb.d.gamma, pb.tau, Np, pb.h_a.data(), pb.h_dadg.data());
   std::vector<double> wu0(N), wphi(N), he(Np);
-  initial_weights(pb.d.kind, pb.d.gamma, pb.tau, N, wu0.data(), wphi.data());
-  difference_weights(pb.d.kind, pb.d.gamma, pb.tau, Np, he.data());
+  initial_weights(pb.tk, pb.d.gamma, pb.tau, N, wu0.data(), wphi.data());
+  difference_weights(pb.tk, pb.d.gamma, pb.tau, Np, he.data());
   std::vector<double2> invd(pb.P), lt(pb.P);
   for (int64_t p = 0; p < pb.P; ++p) {
     double lam[2];
@@ -864,7 +868,10 @@ ftoep_status setup_problem(ftoep_plan pl, Prob& pb) {
         lam[q] = pb.d.lambda;
       }
     }
-    invd[p] = make_double2(1.0 / (he[0] + lam[0] * pb.tau), 1.0 / (he[0] + lam[1] * pb.tau));
+    // difference form per mode: E + lambda tau (1 - (1 - sw) I); only the diagonal
+    // carries sw (the Crank-Nicolson average puts half of the level-n spatial term on
+    // level n-1, whose u^{n-1} = u^n - tau v^n)
+    invd[p] = make_double2(1.0 / (he[0] + pb.sw * lam[0] * pb.tau), 1.0 / (he[0] + pb.sw * lam[1] * pb.tau));
     lt[p] = make_double2(lam[0] * pb.tau, lam[1] * pb.tau);
   }
   ALLOC(pb.a, Np * sizeof(double));
@@ -1050,7 +1057,9 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
     pb.logK2 = pb.d.space ? ilog2(2 * (pb.M + 1)) : 0;
     pb.tau = pb.d.T / (double)pb.N;
     pb.h = pb.d.space ? pb.d.L / (double)(pb.M + 1) : 1.0;
-    pb.scale = scheme_scale(pb.d.kind, pb.d.gamma, pb.tau);
+    pb.tk = pb.d.kind == FTOEP_L1_SUBDIFFUSION ? 0 : 1;
+    pb.sw = pb.d.kind == FTOEP_L1_HYPERBOLIC_CN ? 0.5 : 1.0;
+    pb.scale = scheme_scale(pb.tk, pb.d.gamma, pb.tau);
     const int Bdef = 4096;
     const int Ldef = 16;
     int B = (tune && tune->fft_tile) ? tune->fft_tile : Bdef;

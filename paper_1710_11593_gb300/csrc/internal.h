@@ -119,6 +119,8 @@ struct ResidualArgs {
   int64_t ld, N, M;
   int space;
   double inv_h2, lambda;
+  int cn;                // Crank-Nicolson: S acts on (u^n + u^{n-1})/2
+  const double* uprev0;  // with cn: u0, the level before the first (NULL = zero)
 };
 int launch_residual(const ResidualArgs& a, cudaStream_t st);
 

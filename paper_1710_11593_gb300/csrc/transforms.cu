@@ -951,6 +951,15 @@ __global__ void residual_kernel(ResidualArgs A) {
     const int64_t row = j0 - 1 + k;
     u[k] = (row >= 0 && row < M) ? A.u[row * N + n] : 0.0;
   }
+  if (A.cn) {  // the spatial operator acts on (u^n + u^{n-1})/2, u^0 the initial value
+#pragma unroll
+    for (int k = 0; k < kResRows + 2; ++k) {
+      const int64_t row = j0 - 1 + k;
+      double up = 0.0;
+      if (row >= 0 && row < M) up = n > 0 ? A.u[row * N + n - 1] : (A.uprev0 ? A.uprev0[row] : 0.0);
+      u[k] = 0.5 * (u[k] + up);
+    }
+  }
 #pragma unroll
   for (int k = 0; k < kResRows; ++k) {
     const int64_t row = j0 + k;

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libftoep.so")
 FTOEP_OK, FTOEP_EINVAL, FTOEP_ENOMEM, FTOEP_ECUDA, FTOEP_ETIMEOUT, FTOEP_EUNSUPPORTED = range(6)
 STATUS_NAMES = {0: "FTOEP_OK", 1: "FTOEP_EINVAL", 2: "FTOEP_ENOMEM", 3: "FTOEP_ECUDA", 4: "FTOEP_ETIMEOUT",
                 5: "FTOEP_EUNSUPPORTED"}
-L1_SUBDIFFUSION, L1_HYPERBOLIC = 0, 1
+L1_SUBDIFFUSION, L1_HYPERBOLIC, L1_HYPERBOLIC_CN = 0, 1, 2
 SPACE_NONE, SPACE_DIRICHLET_LAPLACIAN = 0, 1
 FP64, MIXED = 0, 1
 

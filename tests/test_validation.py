@@ -18,7 +18,9 @@ def _spec(**kw):
     (dict(kind=0, gamma=0.0), ftoep.FTOEP_EINVAL, "not in (0,1)"),
     (dict(kind=1, gamma=0.5), ftoep.FTOEP_EINVAL, "not in (1,2)"),
     (dict(kind=1, gamma=2.0), ftoep.FTOEP_EINVAL, "not in (1,2)"),
-    (dict(kind=2, gamma=0.5), ftoep.FTOEP_EINVAL, "unknown kind"),
+    (dict(kind=2, gamma=0.5), ftoep.FTOEP_EINVAL, "not in (1,2)"),
+    (dict(kind=2, gamma=2.0), ftoep.FTOEP_EINVAL, "not in (1,2)"),
+    (dict(kind=3, gamma=1.5), ftoep.FTOEP_EINVAL, "unknown kind"),
     (dict(space=2), ftoep.FTOEP_EINVAL, "unknown space"),
     (dict(precision=3), ftoep.FTOEP_EINVAL, "unknown precision"),
     (dict(N=0), ftoep.FTOEP_EINVAL, "must be >= 1"),
