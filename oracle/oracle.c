@@ -391,6 +391,76 @@ int or_adjoint_march(int kind, int space, double g, double T, double Lx, double 
   return OR_OK;
 }
 
+/*
+ * Advection schemes of Sec. 3, direct method (time order; at every level a forward sweep in
+ * space from the inflow boundary u(0, t) = 0, a = 1).  Cost O(M N^2).
+ *   scheme 2 (0 < g < 1, Eq. 12/13): the L1 quotient at x_{i-1/2} as the average of the L1
+ *     formulas of nodes i and i-1 (scale c = tau^-g/(2 Gamma(2-g)), i.e. half the scale of
+ *     Eq. 4), the derivative (U_i - U_{i-1})/h, f at (x_{i-1/2}, t_n):
+ *        c L1[U_i]^n + c L1[U_{i-1}]^n + (U_i^n - U_{i-1}^n)/h = f_{i-1/2}^n,
+ *     L1[U]^n = sum_{k=1}^{n} l_{n-k} U^k - G_{n-1} U^0 (l_0 = 1, l_j = G_j - G_{j-1}).
+ *   scheme 3 (1 < g < 2, Eq. 16/17): the time terms of Eq. 17 at node i (scale
+ *     c = tau^-g/Gamma(3-g), the hyperbolic first column and initial-data weights) with the
+ *     derivative (U_i^n - U_{i-1}^n)/h at level n, f at (x_i, t_{n-1/2}).
+ * Nodes x_i = i h, h = Lx/M, i = 1..M, U_0 = 0.  f, u: [M][N]; u0, phi: length M or NULL
+ * (phi used by scheme 3 only).  Level values in binary128; history sums by the double-double
+ * dot product (as or_march).
+ */
+int or_advection_march(int scheme, double g, double T, double Lx, int64_t N, int64_t M, const double* f,
+                       const double* u0, const double* phi, double* u) {
+  if (!((scheme == 2 && g > 0.0 && g < 1.0) || (scheme == 3 && g > 1.0 && g < 2.0))) return OR_EINVAL;
+  if (N < 1 || M < 1 || !f || !u || !(T > 0.0) || !(Lx > 0.0)) return OR_EINVAL;
+  const int kind = scheme == 2 ? 0 : 1;
+  const double tau = T / (double)N;
+  const qreal h = (qreal)Lx / (qreal)M;
+  double* rh = (double*)malloc(sizeof(double) * (size_t)N);
+  double* rl = (double*)malloc(sizeof(double) * (size_t)N);
+  double* wu0 = (double*)malloc(sizeof(double) * (size_t)N);
+  double* wphi = (double*)malloc(sizeof(double) * (size_t)N);
+  double* ulo = (double*)malloc(sizeof(double) * (size_t)N * (size_t)M);
+  qreal* hist = (qreal*)malloc(sizeof(qreal) * (size_t)M);
+  if (!rh || !rl || !wu0 || !wphi || !ulo || !hist) {
+    free(rh); free(rl); free(wu0); free(wphi); free(ulo); free(hist);
+    return OR_ENOMEM;
+  }
+  /* a_j = scale * coef_j (reversed, double pairs), scale halved for scheme 2 */
+  const qreal qs = q_scale(kind, (qreal)g, (qreal)tau) * (scheme == 2 ? QLIT(0.5) : QLIT(1.0));
+  for (int64_t j = 0; j < N; ++j) q_split(qs * q_coef(kind, j, (qreal)g), &rh[N - 1 - j], &rl[N - 1 - j]);
+  or_initial_weights(kind, g, tau, N, wu0, wphi);  /* full scale; halved below for scheme 2 */
+  const qreal a0 = qs * q_coef(kind, 0, (qreal)g);
+  const qreal ih = QLIT(1.0) / h;
+  for (int64_t n = 1; n <= N; ++n) {
+    for (int64_t i = 0; i < M; ++i) {
+      qreal s = QLIT(0.0);
+      if (n > 1) dd_dot(rh + (N - n), rl + (N - n), u + i * N, ulo + i * N, n - 1, &s);
+      hist[i] = s;
+    }
+    qreal prev = QLIT(0.0), prev_hist = QLIT(0.0), prev_u0 = QLIT(0.0);  /* node 0: U = 0 */
+    for (int64_t i = 0; i < M; ++i) {
+      qreal r = (qreal)f[i * N + (n - 1)] - hist[i];
+      const qreal ui0 = u0 ? (qreal)u0[i] : QLIT(0.0);
+      qreal x;
+      if (scheme == 2) {
+        /* + c G_{n-1} (U_i^0 + U_{i-1}^0): the initial-data term of both L1 formulas */
+        r += QLIT(0.5) * (qreal)wu0[n - 1] * (ui0 + prev_u0);
+        r += (ih - a0) * prev - prev_hist;
+        x = r / (a0 + ih);
+      } else {
+        r += (qreal)wu0[n - 1] * ui0;
+        if (phi) r += (qreal)wphi[n - 1] * (qreal)phi[i];
+        r += ih * prev;
+        x = r / (a0 + ih);
+      }
+      q_split(x, &u[i * N + (n - 1)], &ulo[i * N + (n - 1)]);
+      prev = x;
+      prev_hist = hist[i];
+      prev_u0 = ui0;
+    }
+  }
+  free(rh); free(rl); free(wu0); free(wphi); free(ulo); free(hist);
+  return OR_OK;
+}
+
 /* Orthonormal sine coefficient of mode m (1..M) of every time column:
  *   out[n] = sqrt(2/(M+1)) * sum_{j=1}^{M} f_j^n sin(m*pi*j/(M+1)).
  * The sine values are taken in binary128 and rounded; the sum is plain double. */

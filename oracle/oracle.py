@@ -57,8 +57,10 @@ def _load():
         lib.or_adjoint_march.argtypes = [cint, cint, dbl, dbl, dbl, dbl, i64, i64, _dp, _dp, cint]
         lib.or_sine_project.argtypes = [i64, i64, _dp, i64, _dp]
         lib.or_toeplitz_matvec.argtypes = [_dp, i64, _dp, _dp, i64, cint]
+        lib.or_advection_march.argtypes = [cint, dbl, dbl, dbl, i64, i64, _dp, _dp, _dp, _dp]
         for name in ("or_G", "or_M", "or_time_coeffs", "or_time_coeffs_dgamma", "or_initial_weights",
-                     "or_march", "or_adjoint_march", "or_sine_project", "or_toeplitz_matvec"):
+                     "or_march", "or_adjoint_march", "or_sine_project", "or_toeplitz_matvec",
+                     "or_advection_march"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -202,6 +204,25 @@ def gamma_gradient(kind: int, gamma: float, u: np.ndarray, lam: np.ndarray, T: f
     N = u.shape[-1]
     da = toeplitz_column_dgamma(kind, gamma, N, T)
     return -float(np.sum(lam * toeplitz_matvec(da, u)))
+
+
+# ----------------------------------------------------------------- Schemes 2 and 3 (advection)
+
+def advection_march(scheme: int, gamma: float, f: np.ndarray, T: float = 1.0, L: float = 1.0, u0=None,
+                    phi=None) -> np.ndarray:
+    """Direct method of the advection schemes of Sec. 3 (time order, a forward sweep in
+    space per level from u(0, t) = 0): scheme 2 (0 < g < 1, Eq. 12/13, the box scheme: L1 at
+    x_{i-1/2} as the average of nodes i and i-1, f at (x_{i-1/2}, t_n)) and scheme 3
+    (1 < g < 2, Eq. 16/17 with the upwind derivative at level n, f at (x_i, t_{n-1/2})).
+    Nodes x_i = i L/M, i = 1..M.  f: [M][N] -> u: [M][N]."""
+    f = _c64(f)
+    M, N = f.shape
+    u = np.zeros_like(f)
+    u0 = None if u0 is None else _c64(u0)
+    phi = None if phi is None else _c64(phi)
+    rc = _load().or_advection_march(scheme, gamma, T, L, N, M, _ptr(f), _ptr(u0), _ptr(phi), _ptr(u))
+    _check(rc, "advection_march")
+    return u
 
 
 # ----------------------------------------------------------------- Scheme 1 (two-sided ODE)

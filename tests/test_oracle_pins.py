@@ -535,3 +535,100 @@ def test_scheme1_matrix_theorem1(oracle):
         margin = A[i - 1, i - 1] - (np.sum(np.abs(A[i - 1])) - abs(A[i - 1, i - 1]))
         want = 1 + mu * (Gd[i - 1] + Gd[N - 1 - i])
         assert abs(margin - want) < 1e-12 * (1 + 2 * mu), (i, margin, want)
+
+
+# ----------------------------------------------------------------- Schemes 2 and 3 (advection)
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(HERE, "golden", name)) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def _printed_match(value, printed):
+    """value agrees with a 5-significant-digit printed number (rounded or truncated)."""
+    e = math.floor(math.log10(abs(printed)))
+    return abs(value - printed) <= 1.0001 * 10.0 ** (e - 4)
+
+
+def _example2_error(oracle, g, M, N):
+    """Scheme 2 on Example 2 (u = t sin pi x, f at (x_{i-1/2}, t_n)): sqrt(h sum_{i<M} e_i^2) at t = 1."""
+    h = 1.0 / M
+    xm = (np.arange(1, M + 1) - 0.5) * h
+    t = wl.time_points(0, N)
+    f = np.outer(np.sin(np.pi * xm), t ** (1 - g) / math.gamma(2 - g)) + np.outer(np.pi * np.cos(np.pi * xm), t)
+    u = oracle.advection_march(2, g, f)
+    e = u[:-1, -1] - np.sin(np.pi * np.arange(1, M) * h)
+    return math.sqrt(h * np.sum(e ** 2))
+
+
+def _example3_error(oracle, g, M, N):
+    """Scheme 3 on Example 3 (u = t^3 x (1-x), f at (x_i, t_{n-1/2})): same norm."""
+    h = 1.0 / M
+    x = np.arange(1, M + 1) * h
+    th = wl.time_points(1, N)
+    f = np.outer(x - x * x, 6 * th ** (3 - g) / math.gamma(4 - g)) + np.outer(1 - 2 * x, th ** 3)
+    u = oracle.advection_march(3, g, f)
+    e = u[:-1, -1] - (x - x * x)[:-1]
+    return math.sqrt(h * np.sum(e ** 2))
+
+
+@pytest.mark.parametrize("row", _read_golden("table5.txt"))
+def test_table5_scheme2(oracle, row):
+    """All 12 direct-method values of Table 5 (the printed values are 10 x the norm)."""
+    M, g, printed = int(row[0]), float(row[1]), float(row[2])
+    assert _printed_match(10.0 * _example2_error(oracle, g, M, 1024), printed)
+
+
+@pytest.mark.parametrize("row", _read_golden("table7.txt"))
+def test_table7_scheme3(oracle, row):
+    """Table 7's direct-method values; the one misprinted entry against its fast-method twin."""
+    M, g, direct, fast = int(row[0]), float(row[1]), float(row[2]), float(row[3])
+    err = _example3_error(oracle, g, M, M)
+    if (M, g) == (8, 1.9):
+        assert _printed_match(err, fast) and not _printed_match(err, direct)
+    else:
+        assert _printed_match(err, direct)
+
+
+def _dense_advection(scheme, g, M, N):
+    """Space-time matrix of scheme 2 or 3 (unknown (i, n) at i*N + n), decimal coefficients."""
+    tau = 1.0 / N
+    kind = 0 if scheme == 2 else 1
+    s = d_scale(kind, g, tau) * (Decimal("0.5") if scheme == 2 else 1)
+    a = [float(s * d_coef(kind, j, g)) for j in range(N)]
+    T = np.zeros((N, N))
+    for n in range(N):
+        for k in range(n + 1):
+            T[n, k] = a[n - k]
+    h = 1.0 / M
+    I_M, I_N, S = np.eye(M), np.eye(N), np.eye(M, k=-1)
+    A = np.kron(I_M, T) + (np.kron(I_M, I_N) - np.kron(S, I_N)) / h
+    if scheme == 2:
+        A += np.kron(S, T)
+    return A, s
+
+
+@pytest.mark.parametrize("scheme,g", [(2, 0.3), (2, 0.8), (3, 1.2), (3, 1.8)])
+def test_advection_march_vs_dense_solve(oracle, scheme, g):
+    M, N = 6, 24
+    rng = np.random.default_rng(scheme * 10 + int(10 * g))
+    f = rng.standard_normal((M, N))
+    u0 = rng.standard_normal(M)
+    phi = rng.standard_normal(M) if scheme == 3 else None
+    A, s = _dense_advection(scheme, g, M, N)
+    rhs = f.copy()
+    if scheme == 2:  # c G_{n-1} (u0_i + u0_{i-1}) from both L1 formulas
+        wu0 = np.array([float(s * d_G(n - 1, g)) for n in range(1, N + 1)])
+        rhs += np.outer(u0 + np.concatenate([[0.0], u0[:-1]]), wu0)
+    else:
+        tau = Decimal(1) / N
+        wu0 = np.array([float(s * (d_M(n - 1, g) - d_M(n - 2, g))) for n in range(1, N + 1)])
+        wphi = np.array([float(s * tau * d_M(n - 1, g)) for n in range(1, N + 1)])
+        rhs += np.outer(u0, wu0) + np.outer(phi, wphi)
+    ref = np.linalg.solve(A, rhs.reshape(-1)).reshape(M, N)
+    u = oracle.advection_march(scheme, g, f, u0=u0, phi=phi)
+    np.testing.assert_allclose(u, ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
