@@ -31,6 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "M·N unknowns/sec at ≤1e-6 rel err: mixed-precision batched vs plain FP64"
+SOLVER_NAMES = {1: "half-split", 2: "inverse series"}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (profiling recipe); probe measured 1.19 (DFMA loop)
 # FP32 from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -53,6 +54,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="batched: library default tuning instead of the autotuner's")
     ap.add_argument("--scheduler", type=int, default=0, choices=[0, 1, 2],
                     help="single workloads: 0 library choice, 1 per-level launches, 2 persistent chain")
+    ap.add_argument("--solver", type=int, default=0, choices=[0, 1, 2],
+                    help="single workloads: 0 library choice, 1 half-split, 2 inverse series")
     ap.add_argument("--M", type=int, default=None, help="override the workload's interior points (profiling cases)")
     ap.add_argument("--N", type=int, default=None, help="override the workload's time steps (profiling cases)")
     return ap.parse_args()
@@ -98,11 +101,14 @@ def flop_model(p, precision):
     return work_model(p, precision)[0]
 
 
-def work_model(p, precision):
+def work_model(p, precision, solver=1):
     """(flops, bytes) of one solve per kernel class.  Bytes are the compulsory HBM bytes
     of each class's algorithm: every array the class reads or writes crosses HBM once
     (z pairs 8 B per complex float / 16 B double, fields 8 B per double, 4 B per float);
-    the four-step scratch round trips are not counted (they are the implementation's)."""
+    the four-step scratch round trips are not counted (they are the implementation's).
+    solver 2 (inverse series): each solve is one convolution of length n = 2 Np per pair
+    (two FFTs, the partner product: 8 flops per point), reading z and the pair's packed
+    spectrum (n complex) and writing z; the half-split classes are then empty."""
     Np = 16
     while Np < p.N:
         Np *= 2
@@ -112,11 +118,17 @@ def work_model(p, precision):
     ncols = nblk * B
     nsolve = 1 if precision == "fp64" else 2
     zb = 16 if precision == "fp64" else 8  # bytes per complex of the solve
+    inverse = inverse_b = 0.0
+    if solver == 2:
+        n = 2 * Np
+        inverse = nsolve * P * (2 * 5 * n * math.log2(n) + 8 * n)
+        inverse_b = nsolve * P * (2 * Np * zb + n * zb)
+        nblk = 1  # no block solves or cross-block levels in the flops below
     # block solve = causal convolution with the block inverse: FFT and inverse FFT of length
     # 2B per pair plus two complex products per point; reads z, writes z, reads the
     # Hermitian-packed C1/C2 array (2B complex per pair)
-    block = nsolve * nblk * (2 * P * B) * (10 * math.log2(2 * B) + 14)
-    block_b = nsolve * nblk * P * (2 * B * zb + (2 * B) * zb)
+    block = 0.0 if solver == 2 else nsolve * nblk * (2 * P * B) * (10 * math.log2(2 * B) + 14)
+    block_b = 0.0 if solver == 2 else nsolve * nblk * P * (2 * B * zb + (2 * B) * zb)
     conv_smem = conv_4 = 0.0
     smem_b = four_b = 0.0
     nsmem = 4096 if precision == "fp64" else 8192
@@ -140,8 +152,9 @@ def work_model(p, precision):
         sine = 2 * nsolve * (ncols / 2) * 5 * K2 * math.log2(K2)
         fb = 8  # double field in, out (fp64) / f double, v float, r float (mixed)
         sine_b = nsolve * (p.M * p.N * (fb + (fb if precision == "fp64" else 4)) + 2 * P * ncols * zb)
-    flops = {"block_solve": block, "conv_smem": conv_smem, "conv_fourstep": conv_4, "sine": sine}
-    byts = {"block_solve": block_b, "conv_smem": smem_b, "conv_fourstep": four_b, "sine": sine_b}
+    flops = {"block_solve": block, "conv_smem": conv_smem, "conv_fourstep": conv_4, "sine": sine, "inverse": inverse}
+    byts = {"block_solve": block_b, "conv_smem": smem_b, "conv_fourstep": four_b, "sine": sine_b,
+            "inverse": inverse_b}
     # the persistent per-pair solve runs the block solves and every cross-block level
     flops["chain"] = block + conv_smem + conv_4
     byts["chain"] = block_b + smem_b + four_b
@@ -463,10 +476,11 @@ def run_single(name, precision, steps, warmup, rk, local, tuning=None):
         prof = class_profile(plan, f, u)
         plan.solve(f, u)
         plan.sync()
+        solver = plan.solver(0)
     ms = rk.max(ms)
-    fl, by = work_model(p, precision)
+    fl, by = work_model(p, precision, solver)
     out = {"workload": wname, "precision": precision, "ms_per_step": ms, "value": p.M * p.N / (ms * 1e-3),
-           "unit": "unknowns/s", "gpu_launches": launches,
+           "unit": "unknowns/s", "gpu_launches": launches, "solver": SOLVER_NAMES[solver],
            "roofline": roofline_of(fl, by, prof, ms, precision),
            "kernel_time_share": {k: v[0] / max(1e-9, sum(x[0] for x in prof.values())) for k, v in prof.items()},
            "rel_err_vs_oracle_prefix": oracle_prefix_error(p, u, min(p.N, 1024)),
@@ -504,8 +518,9 @@ def run_batched(args):
     busy = sum(x[0] for x in prof.values())
     shares = {k: v[0] / max(1e-9, busy) for k, v in prof.items()}
     fl, by = {}, {}
-    for p in probs:
-        f1, b1 = work_model(p, precision)
+    solvers = [plan.solver(i) for i in range(len(probs))]
+    for p, sv in zip(probs, solvers):
+        f1, b1 = work_model(p, precision, sv)
         for k in f1:
             fl[k] = fl.get(k, 0.0) + f1[k]
             by[k] = by.get(k, 0.0) + b1[k]
@@ -561,6 +576,7 @@ def run_batched(args):
             # two warm-up solves: the first runs directly, the second captures the graph, so
             # the timed solve is a replay like the timed steps of the main leg
             ms2, launches2, _ = timed(plan2, f, u2, 1, 2, rk, local, clocks=False)
+            solvers2 = [plan2.solver(i) for i in range(len(probs))]
         ms2 = rk.max(ms2)
         fp64u = u2 if other == "fp64" else u
         mixu = u if other == "fp64" else u2
@@ -573,10 +589,10 @@ def run_batched(args):
             worst = max(worst, float(torch.linalg.norm(a - b) / torch.linalg.norm(b)))
             off += n
         fl2 = {}
-        for p in probs:
-            for kk, vv in work_model(p, other)[0].items():
+        for p, sv in zip(probs, solvers2):
+            for kk, vv in work_model(p, other, sv)[0].items():
                 fl2[kk] = fl2.get(kk, 0.0) + vv
-        solve_flops = fl2["chain"] + fl2["sine"]
+        solve_flops = fl2["chain"] + fl2["sine"] + fl2["inverse"]
         compare = {"precision": other, "value": world * units / (ms2 * 1e-3), "ms_per_step": ms2,
                    "gpu_launches": launches2, "tuning": tuning2,
                    "mixed_speedup_vs_fp64": (ms2 / ms) if other == "fp64" else (ms / ms2),
@@ -600,13 +616,17 @@ def run_batched(args):
                "sample": f"first min(N,2048) levels of the first 8 problems, {tot_s:.1f} s; O(M N^2) direct marching"}
     singles = None
     if not args.no_singles:
-        singles = [run_single("diffusion", "fp64", 10, 3, rk, local), run_single("wave", "mixed", 5, 3, rk, local)]
+        # config 2 (double) and config 3 (mixed) with the library's choices, and config 2 by the
+        # inverse-series solve on request (its time and its prefix error beside the default's)
+        singles = [run_single("diffusion", "fp64", 10, 3, rk, local), run_single("wave", "mixed", 5, 3, rk, local),
+                   run_single("diffusion", "fp64", 10, 3, rk, local, tuning={"solver": 2})]
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f32+f64", "data": "synthetic",
                "config": {"workload": wname, "nprob": len(probs), "unknowns": units, "precision": precision,
                           "tuning": tuning or "library default", "tuning_from_cache": cached,
+                          "solvers": {SOLVER_NAMES[k]: solvers.count(k) for k in sorted(set(solvers))},
                           "l2": f"inputs larger than L2 (f = {units * 8 / 1e9:.1f} GB)"},
                "roofline": roof, "kernel_time_share": shares, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                "gpu_launches": launches, "default_tuning": default, "compare": compare, "singles": singles}
@@ -630,7 +650,7 @@ def run_ours(args):
     spec = ftoep.ProblemSpec(p.kind, p.gamma, p.N, p.M, p.space, prec, lam=p.lam)
     f = wl.materialize_torch(p.source, p.kind, p.N, p.M, device="cuda")
     u = torch.empty_like(f)
-    tuning = {"scheduler": args.scheduler} if args.scheduler else None
+    tuning = {"scheduler": args.scheduler, "solver": args.solver} if (args.scheduler or args.solver) else None
     plan = ftoep.Plan([spec], tuning=tuning)
     ms, launches, clk = timed(plan, f, u, args.steps, args.warmup, rk, local)
     prof = class_profile(plan, f, u)
@@ -639,7 +659,8 @@ def run_ours(args):
     value = rk.value(units, ms)
     tot_ms = sum(x[0] for x in prof.values())
     shares = {k: v[0] / max(1e-9, tot_ms) for k, v in prof.items()}
-    fl, by = work_model(p, precision)
+    solver = plan.solver(0)
+    fl, by = work_model(p, precision, solver)
     roof = roofline_of(fl, by, prof, ms, precision)
 
     # end to end: same solve through the C ABI with pinned HOST buffers (copies inside)
@@ -698,7 +719,8 @@ def run_ours(args):
                "data": "synthetic",
                "config": {"workload": wname, "M": p.M, "N": p.N, "gamma": p.gamma, "precision": precision,
                           "l2": f"inputs larger than L2 (f = {f.numel() * 8 / 1e9:.2f} GB)",
-                          "block": B, "scheduler": args.scheduler or "library choice"},
+                          "block": B, "scheduler": args.scheduler or "library choice",
+                          "solver": SOLVER_NAMES[solver]},
                "roofline": roof, "kernel_time_share": shares, "cpu_baseline": cpu, "e2e": e2e,
                "clocks": clk, "gpu_launches": launches, "compare": compare,
                "max_abs_err_vs_exact": disc}

@@ -123,8 +123,27 @@ typedef enum {
                              at plan creation, at most 32 GiB of pair arrays)              */
 } ftoep_scheduler;
 
-/* Optional tuning (NULL or 0 fields = library choice; ftoep_autotune picks fft_tile and
- * scheduler).
+/* Solver of the per-mode lower-triangular Toeplitz systems (ftoep_tuning.solver). */
+typedef enum {
+  FTOEP_SOLVER_AUTO = 0,      /* library choice: HALFSPLIT (its error follows the size of each
+                                 time block's own values; see INVERSE)                       */
+  FTOEP_SOLVER_HALFSPLIT = 1, /* time blocks of B levels solved by the block inverse, then the
+                                 recursive half-split updates between blocks (Sec. 3: the
+                                 fast direct method of the reordered systems)                 */
+  FTOEP_SOLVER_INVERSE = 2    /* the inverse-series solve: x = h_m * y over the whole padded
+                                 length, h_m = T_m^-1 e_1 computed once per plan (by the
+                                 half-split solve of a unit impulse, in double); each solve is
+                                 one causal convolution of length 2 Np per mode pair.  Its
+                                 rounding is normwise over the whole time axis (one FFT): the
+                                 error of every level is about eps log2(2 Np) |h_m| |y| /
+                                 |x| of the largest values, where the half split's stays
+                                 with the size of each block's own values -- for a growing
+                                 hyperbolic or mixed-precision solution the early levels lose
+                                 relative accuracy                                           */
+} ftoep_solver;
+
+/* Optional tuning (NULL or 0 fields = library choice; ftoep_autotune picks fft_tile,
+ * scheduler, streams and solver).
  * fft_tile: the time block length B (power of two, 16..4096; default 4096, capped at N
  *   rounded up to a power of two).  Every block of B levels is solved by a causal
  *   convolution with the per-mode inverse of the block operator (one FFT of length 2B);
@@ -136,9 +155,15 @@ typedef enum {
  * scheduler: an ftoep_scheduler value.
  * streams: internal streams of a plan with several problems (1..8; default 4): the
  *   per-problem phases (sine transforms, time sums, residuals; with the levels schedule
- *   every launch) of different problems run concurrently on them. */
+ *   every launch) of different problems run concurrently on them.
+ * solver: an ftoep_solver value.  INVERSE applies to problems with more than one time block
+ *   and 2 Np above the shared-memory convolution length (8192 mixed, 4096 double); it costs
+ *   P * 2 Np complex values of the solve precision per problem (P = ceil(M/2) mode pairs)
+ *   and one double half-split solve at plan creation.  A mixed problem with INVERSE solves
+ *   both float solves (first and correction) with it; its adjoint (double) uses the
+ *   half-split.  ftoep_problem_solver reports the solver each problem got. */
 typedef struct {
-  int leaf, fft_tile, gemm_max_level, scheduler, streams;
+  int leaf, fft_tile, gemm_max_level, scheduler, streams, solver;
 } ftoep_tuning;
 
 /* Create a plan for nprob problems (1 <= nprob).  Computes the weights a_j of every
@@ -190,7 +215,8 @@ typedef enum {
   FTOEP_K_SINE = 3,           /* sine transforms along space                                */
   FTOEP_K_OTHER = 4,          /* packing, time sums, reductions, spectra                    */
   FTOEP_K_RESIDUAL = 5,       /* mixed path: float-float residual product and residual      */
-  FTOEP_K_CHAIN = 6           /* persistent per-pair solve (block solves and every level)   */
+  FTOEP_K_CHAIN = 6,          /* persistent per-pair solve (block solves and every level)   */
+  FTOEP_K_INVERSE = 7         /* inverse-series solve (one convolution of length 2 Np)       */
 } ftoep_kernel_class;
 
 /* Instrumentation (no counterpart in the paper).  ftoep_profile waits for the stream,
@@ -246,10 +272,56 @@ ftoep_status ftoep_matvec_noalloc(const double* a, int64_t N, const double* x, d
 ftoep_status ftoep_two_sided_cg(double gamma, double T, int64_t N, const double* f, double* u, double tol,
                                 int maxit, int* iters, double* relres, void* cuda_stream);
 
+/* Restarted GMRES(restart) of Sec. 3.2 (the method the paper accelerates with circulant
+ * products) on the space-time system of problem iprob of the plan, with zero initial data:
+ * the reordered system of Eq. 21 (I_M (x) T + K (x) I_N; T lower-triangular Toeplitz with the
+ * plan's first column a (ftoep_weights), K the spatial operator: -(second difference) with
+ * Dirichlet zeros, or lambda I without space; for FTOEP_L1_HYPERBOLIC_CN averaged over levels
+ * n and n-1).  Every product: T by circulant embedding (Eq. be1, the input padded with zeros)
+ * and FFTs, K by a stencil; Arnoldi with classical Gram-Schmidt applied twice; double
+ * precision.  A comparison path for ftoep_solve (the direct solve of the same system).
+ * f: right-hand side [M][N] (the problem's field layout), u: initial guess in, solution out;
+ * host or device memory.  restart in [1, 64]; stops when the true residual of an iterate
+ * (checked at every restart) or the Arnoldi estimate satisfies ||r||_2 <= tol ||f||_2, or
+ * after maxit Arnoldi steps.  *iters (nullable): Arnoldi steps done; *relres (nullable):
+ * ||f - A u||_2 / ||f||_2 of the returned u from a fresh product.  Allocates (restart + 1) M N
+ * doubles of device workspace and frees it before returning (on an error path it is freed at
+ * ftoep_destroy); runs on the plan's stream and blocks until done.  Errors: FTOEP_EINVAL
+ * (plan NULL, iprob out of range, f or u NULL, restart outside [1, 64], tol <= 0, maxit < 1),
+ * FTOEP_ENOMEM, FTOEP_ECUDA. */
+ftoep_status ftoep_gmres(ftoep_plan p, int iprob, const double* f, double* u, int restart, double tol, int maxit,
+                         int* iters, double* relres);
+
+/* Advection schemes of Sec. 3 by the fast procedure (space order, Figure 2):
+ *   scheme 2 (0 < gamma < 1, Eq. 12/13): D^g u + u_x = f with the L1 quotient at x_{i-1/2} as
+ *     the average of the L1 formulas (Eq. 4, scale tau^-g/(2 Gamma(2-g))) of nodes i and i-1,
+ *     u_x by (U_i - U_{i-1})/h, f at (x_{i-1/2}, t_n): per node the lower-triangular Toeplitz
+ *     system A-tilde U_i = B U_{i-1} + F_i (A-tilde = c L1 + I/h, B = I/h - c L1);
+ *   scheme 3 (1 < gamma < 2, Eq. 16/17): the time terms of Eq. 17 at node i with u_x by the
+ *     upwind difference at level n, f at (x_i, t_{n-1/2}): A-tilde U_i = U_{i-1}/h + F_i
+ *     (A-tilde = c W + I/h).
+ * Grid: tau = T/N, h = L/M, nodes x_i = i h (i = 1..M), inflow value u(0, t) = 0 (a = 1).
+ * Each node's system is solved by the library's solve of one scalar problem (lambda = 2/h,
+ * resp. 1/h; precision FTOEP_FP64 or FTOEP_MIXED), the product B U_{i-1} by circulant
+ * embedding; M sequential steps.  f, u: [M][N] doubles (row i-1 = node x_i), u0: length M or
+ * NULL, phi: length M or NULL (scheme 3 only); host or device memory.  The initial-data
+ * weights are those of Eq. 4 (the u0 weight G_{n-1}) and Eq. 17.  Creates and destroys an
+ * internal plan; ordered on cuda_stream and blocks until done.  Errors: FTOEP_EINVAL (scheme
+ * not 2 or 3, gamma outside the scheme's range, N or M < 1, T or L <= 0, NULL f or u, bad
+ * precision), FTOEP_ENOMEM, FTOEP_ECUDA; message by ftoep_last_error(NULL, ...). */
+ftoep_status ftoep_advection_sweep(int scheme, double gamma, double T, double L, int64_t N, int64_t M,
+                                   const double* f, const double* u0, const double* phi, double* u, int precision,
+                                   void* cuda_stream);
+
+/* The solver a plan uses for problem iprob (FTOEP_SOLVER_HALFSPLIT or
+ * FTOEP_SOLVER_INVERSE), after the library's choice.  Errors: FTOEP_EINVAL. */
+ftoep_status ftoep_problem_solver(ftoep_plan p, int iprob, int* solver);
+
 /* Autotuner (no counterpart in the paper).  Times ftoep_solve on synthetic fields for
- * every candidate tuning -- time-block length fft_tile in {1024, 2048, 4096} x scheduler in
- * {levels, chain} x internal streams in {2, 4, 8} (streams only for plans of several
- * problems; a single problem runs on the caller's stream) -- with a plan per candidate,
+ * every candidate tuning -- time-block length fft_tile in {1024, 2048, 4096} of the
+ * half-split solver (the inverse-series solve is the caller's accuracy choice) x scheduler in {levels, chain} x internal streams in
+ * {2, 4, 8} (streams only for plans of several problems; a single problem runs on the
+ * caller's stream) -- with a plan per candidate,
  * one warm-up solve, one captured solve and two timed replays (CUDA events on
  * cuda_stream), device memory freed afterwards, and writes the fastest tuning to *out
  * (leaf and gemm_max_level 0 = library choice).  When the problems together exceed 2^28

@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libftoep.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["api.cu", "transforms.cu", "block_solve.cu", "block_inverse.cu", "chain.cu", "twosided.cu", "noalloc.cu"]
+CU_SOURCES = ["api.cu", "transforms.cu", "block_solve.cu", "block_inverse.cu", "chain.cu", "full_inverse.cu", "gmres.cu",
+              "twosided.cu", "noalloc.cu"]
 CPP_SOURCES = ["weights.cpp"]
 
 

@@ -33,7 +33,7 @@ namespace {
 
 constexpr int kMaxStreams = 8;
 constexpr int kDefaultStreams = 4;
-constexpr int kNumClasses = 7;
+constexpr int kNumClasses = 8;
 constexpr int kDotBlocks = 1024;
 
 struct Prob {
@@ -76,6 +76,9 @@ struct Prob {
   // block inverse spectra (block_inverse.cu): precision of the solve, and double (adjoint)
   void* c1 = nullptr;
   void* c2 = nullptr;
+  // inverse-series solve: packed spectra of the whole inverse columns [P][2Np] (solve precision)
+  bool finv = false;
+  void* cinv = nullptr;
   double2* c1_64 = nullptr;
   double2* c2_64 = nullptr;
 };
@@ -196,6 +199,7 @@ struct ftoep_plan_s {
   void* twff = nullptr;           // float-float twiddles (ff2)
   std::vector<Ws> ws;
   size_t z_el = 0, mv_el = 0, r_el = 0, p_el = 0, v_el = 0;
+  size_t scr_el = 0;  // solve scratch (double2): the largest P*Np, and 2 Np of an inverse-series problem
   double* dscal = nullptr;        // device scalars (nprob)
   cudaEvent_t fork = nullptr;
   int64_t total_field = 0, total_vec = 0;
@@ -357,6 +361,8 @@ ftoep_status validate(const ftoep_problem& d, int i, const ftoep_tuning* tune) {
       return fail(pl, FTOEP_EINVAL, "tuning: gemm_max_level must be a power of two <= 2048");
     if (tune->streams < 0 || tune->streams > kMaxStreams)
       return fail(pl, FTOEP_EINVAL, "tuning: streams must be in [0, %d]", kMaxStreams);
+    if (tune->solver < 0 || tune->solver > FTOEP_SOLVER_INVERSE)
+      return fail(pl, FTOEP_EINVAL, "tuning: solver %d unknown", tune->solver);
     if (tune->scheduler < 0 || tune->scheduler > FTOEP_SCHED_CHAIN)
       return fail(pl, FTOEP_EINVAL, "tuning: scheduler must be 0 (library choice), 1 (levels) or 2 (chain)");
   }
@@ -403,6 +409,24 @@ ftoep_status build_product_spectrum(ftoep_plan pl, Ws& w, Prob& pb, const double
 // In-place difference-form solve of the pair array z (right-hand side in, v out).
 ftoep_status solve_pairs(ftoep_plan pl, Ws& w, Prob& pb, Prec pr, void* z, const void* spec) {
   cudaStream_t st = w.st;
+  if (pb.finv && pr == pb.prec) {  // inverse-series solve: one convolution of length 2 Np per pair
+    // pairs in chunks whose scratch (2 Np values each) fits the stream's scratch
+    const int64_t n = 2 * pb.Np;
+    const int64_t chunk = std::max<int64_t>(1, (int64_t)(pl->scr_el * sizeof(double2) / ((size_t)n * velem(pr))));
+    for (int64_t p0 = 0; p0 < pb.P; p0 += chunk) {
+      FinvArgs fa{};
+      fa.z = (char*)z + (size_t)p0 * pb.Np * velem(pr);
+      fa.ld = pb.Np;
+      fa.N = pb.N;
+      fa.npairs = std::min<int64_t>(chunk, pb.P - p0);
+      fa.logn = pb.logNp + 1;
+      fa.cs = (const char*)pb.cinv + (size_t)p0 * n * velem(pr);
+      fa.tw = tw_of(pl, pr);
+      fa.scratch = w.scratch;
+      LAUNCH(FTOEP_K_INVERSE, launch_full_inverse(pr, fa, st));
+    }
+    return FTOEP_OK;
+  }
   CK(cudaMemsetAsync(w.prefix, 0, (size_t)pb.P * sizeof(double2), st));
   const void* c1 = pr == pb.prec ? pb.c1 : (const void*)pb.c1_64;
   const void* c2 = pr == pb.prec ? pb.c2 : (const void*)pb.c2_64;
@@ -638,9 +662,13 @@ ftoep_status adjoint_problem(ftoep_plan pl, Ws& w, Prob& pb, const double* g, co
     return fail(pl, FTOEP_EUNSUPPORTED, "adjoint: M+1 = %lld > %d needs a double sine transform that is not built",
                 (long long)(pb.M + 1), bluestein_max_K(P64));
   TRY(ensure_level_ws(pl, w));
-  // The adjoint runs in double with the problem's own block length.
+  // The adjoint runs in double with the problem's own block length (and the double block
+  // inverse spectra: c1/c2 of a mixed problem are float).
   Prob q = pb;
   q.prec = P64;
+  q.c1 = pb.c1_64;
+  q.c2 = pb.c2_64;
+  if (pb.prec != P64) q.finv = false;  // the inverse spectra of a mixed problem are float
   // With u = tau C v (C the all-ones lower triangle), A_u = A_v (tau C)^-1, so
   // A_u^-T g = A_v^-T (tau C^T g): suffix sums of g, then the transposed difference-form
   // solve, done as time reversal + forward solve + reversal (J A_v^T J = A_v per mode).
@@ -676,7 +704,7 @@ ftoep_status ensure_level_ws(ftoep_plan pl, Ws& w) {
     ALLOC(w.z, pl->z_el * sizeof(double2));
     CK(cudaMemsetAsync(w.z, 0, pl->z_el * sizeof(double2), w.st));
   }
-  if (!w.scratch) ALLOC(w.scratch, pl->z_el * sizeof(double2));
+  if (!w.scratch) ALLOC(w.scratch, pl->scr_el * sizeof(double2));
   return FTOEP_OK;
 }
 
@@ -847,6 +875,39 @@ ftoep_status build_block_inverse(ftoep_plan pl, Ws& w, Prob& pb, Prec pr, void**
   return FTOEP_OK;
 }
 
+// Inverse-series solve set-up: h_m = T_m^-1 e_1 over [0, N) for every mode by the double
+// half-split solve of a unit impulse, then the packed spectra of the pairs (length 2 Np,
+// four-step order, solve precision), in chunks of pairs that fit the stream's scratch.
+ftoep_status build_full_inverse(ftoep_plan pl, Ws& w, Prob& pb) {
+  cudaStream_t st = w.st;
+  TRY(ensure_level_ws(pl, w));
+  if (!pb.c1_64) TRY(build_block_inverse(pl, w, pb, P64, (void**)&pb.c1_64, (void**)&pb.c2_64));
+  double2* z = (double2*)w.z;
+  LAUNCH(FTOEP_K_OTHER, launch_unit_impulse(z, pb.Np, pb.P, (int)pb.ncols, st));
+  Prob q = pb;
+  q.prec = P64;
+  q.finv = false;
+  q.c1 = pb.c1_64;
+  q.c2 = pb.c2_64;
+  TRY(solve_pairs(pl, w, q, P64, z, pb.spec64));
+  const int64_t n = 2 * pb.Np;
+  ALLOC(pb.cinv, (size_t)pb.P * n * velem(pb.prec));
+  const int64_t chunk = std::max<int64_t>(1, (int64_t)(pl->scr_el / (size_t)n));  // double2 scratch
+  for (int64_t p0 = 0; p0 < pb.P; p0 += chunk) {
+    FinvSpecArgs fs{};
+    fs.h = z + p0 * pb.Np;
+    fs.ld = pb.Np;
+    fs.N = pb.N;
+    fs.npairs = std::min<int64_t>(chunk, pb.P - p0);
+    fs.logn = pb.logNp + 1;
+    fs.scratch64 = (double2*)w.scratch;
+    fs.cs = (char*)pb.cinv + (size_t)p0 * n * velem(pb.prec);
+    fs.tw64 = pl->tw64;
+    LAUNCH(FTOEP_K_OTHER, launch_finv_spectrum(pb.prec, fs, st));
+  }
+  return FTOEP_OK;
+}
+
 ftoep_status setup_problem(ftoep_plan pl, Prob& pb) {
   const int64_t N = pb.N, Np = pb.Np;
   pb.h_a.resize(Np);
@@ -907,6 +968,7 @@ ftoep_status setup_problem(ftoep_plan pl, Prob& pb) {
     pb.c2_64 = (double2*)pb.c2;
   }
   if (pb.prec == P32) TRY(build_product_spectrum(pl, w, pb, pb.e, &pb.spec_res, PFF));
+  if (pb.finv) TRY(build_full_inverse(pl, w, pb));
   return FTOEP_OK;
 }
 
@@ -934,7 +996,7 @@ ftoep_status setup_chain(ftoep_plan pl) {
     int64_t scr = 0;
     bool any = false;
     for (auto& pb : pl->probs) {
-      if (pb.prec != pr) continue;
+      if (pb.prec != pr || pb.finv) continue;
       any = true;
       maxB = std::max(maxB, pb.B);
       for (int v = 1; v < pb.nblk; ++v) {
@@ -971,6 +1033,7 @@ ftoep_status setup_chain(ftoep_plan pl) {
   size_t gmax = 0;
   for (int i : order) {
     Prob& pb = pl->probs[i];
+    if (pb.finv) continue;  // solved on the internal streams, one convolution per pair
     const size_t b = (pair_bytes(pb) + 255) / 256 * 256;
     if (pl->groups.empty() || pl->groups.back().bytes + b > budget) pl->groups.emplace_back();
     ChainGroup& g = pl->groups.back();
@@ -980,8 +1043,10 @@ ftoep_status setup_chain(ftoep_plan pl) {
     g.probs.push_back(i);
     gmax = std::max(gmax, g.bytes);
   }
-  ALLOC(pl->gz, gmax);
-  CK(cudaMemset(pl->gz, 0, gmax));
+  if (gmax) {
+    ALLOC(pl->gz, gmax);
+    CK(cudaMemset(pl->gz, 0, gmax));
+  }
   pl->ncounters = 2 * (int)pl->groups.size();
   ALLOC(pl->counters, (size_t)pl->ncounters * sizeof(unsigned));
   for (auto& g : pl->groups) {
@@ -1096,6 +1161,23 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
   // problems longest first onto the least-loaded one
   const int want = (tune && tune->streams) ? tune->streams : kDefaultStreams;
   const int nstreams = nprob == 1 ? 1 : std::min(nprob, want);
+  // inverse-series solve, on request (FTOEP_SOLVER_INVERSE), for problems with more than
+  // one time block and a convolution length above the shared-memory one.  The library's
+  // choice is the half split: the inverse-series solve rounds once over the whole time axis,
+  // so the early, small levels of a growing solution carry the error of the late, large ones
+  // (measured: 4.7e-12 of a sub-diffusion problem's checked set in double, gamma 0.2,
+  // N = 127953; 4.6e-3 on the first 1024 levels of the mixed wave workload)
+  {
+    const int solver = tune ? tune->solver : (int)FTOEP_SOLVER_AUTO;
+    for (auto& pb : pl->probs) {
+      const int64_t n = 2 * pb.Np;
+      if (solver == FTOEP_SOLVER_INVERSE && pb.nblk >= 2 && n > nsmem_for(pb.prec)) pb.finv = true;
+    }
+    // the solve's four-step scratch holds one pair's 2 Np values at least
+    pl->scr_el = pl->z_el;
+    for (auto& pb : pl->probs)
+      if (pb.finv) pl->scr_el = std::max(pl->scr_el, (size_t)2 * pb.Np);
+  }
   pl->ws.resize(nstreams);
   for (int s = 0; s < nstreams; ++s) {
     Ws& w = pl->ws[s];
@@ -1165,7 +1247,7 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
       }
     }
     if (pl->sched == FTOEP_SCHED_LEVELS &&
-        (st = dalloc(pl, &w.scratch, pl->z_el * sizeof(double2))) != FTOEP_OK) return bail(st);
+        (st = dalloc(pl, &w.scratch, pl->scr_el * sizeof(double2))) != FTOEP_OK) return bail(st);
     if ((st = dalloc(pl, (void**)&w.zmv, pl->mv_el * sizeof(double2))) != FTOEP_OK) return bail(st);
     if ((st = dalloc(pl, (void**)&w.scratch_mv, 2 * pl->mv_el * sizeof(double2))) != FTOEP_OK) return bail(st);
     if ((st = dalloc(pl, (void**)&w.r, pl->r_el * sizeof(double))) != FTOEP_OK) return bail(st);
@@ -1182,6 +1264,13 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
     return bail(FTOEP_ECUDA);
   }
   *out = pl;
+  return FTOEP_OK;
+}
+
+ftoep_status ftoep_problem_solver(ftoep_plan pl, int iprob, int* solver) {
+  if (!pl) return fail(nullptr, FTOEP_EINVAL, "plan is NULL");
+  if (iprob < 0 || iprob >= (int)pl->probs.size() || !solver) return fail(pl, FTOEP_EINVAL, "iprob out of range or solver NULL");
+  *solver = pl->probs[iprob].finv ? FTOEP_SOLVER_INVERSE : FTOEP_SOLVER_HALFSPLIT;
   return FTOEP_OK;
 }
 
@@ -1210,36 +1299,42 @@ Ws ws_for(ftoep_plan pl, const Prob& pb) {
 
 // Every problem of the plan on its stream, per-level launches, forked from and joined back
 // to the caller's.
+// One problem with per-level launches on its internal stream and workspace (host
+// buffers through the stream's staging arrays).
+ftoep_status solve_on_stream(ftoep_plan pl, Prob& pb, const double* f, double* u, const double* u0,
+                             const double* phi, bool host) {
+  Ws& wr = pl->ws[pb.stream];
+  TRY(ensure_level_ws(pl, wr));
+  if (host) TRY(ensure_staging(pl, wr));
+  Ws w = ws_for(pl, pb);
+  cudaStream_t st = w.st;
+  const double* pf = f + pb.foff;
+  double* pu = u + pb.foff;
+  const double* pu0 = u0 ? u0 + pb.voff : nullptr;
+  const double* pphi = phi ? phi + pb.voff : nullptr;
+  if (host) {
+    const size_t bytes = (size_t)pb.M * pb.N * sizeof(double);
+    CK(cudaMemcpyAsync(w.stage_in, pf, bytes, cudaMemcpyDefault, st));
+    if (pu0) {
+      CK(cudaMemcpyAsync(w.stage_v0, pu0, pb.M * sizeof(double), cudaMemcpyDefault, st));
+      pu0 = w.stage_v0;
+    }
+    if (pphi) {
+      CK(cudaMemcpyAsync(w.stage_v1, pphi, pb.M * sizeof(double), cudaMemcpyDefault, st));
+      pphi = w.stage_v1;
+    }
+    TRY(solve_problem(pl, w, pb, w.stage_in, w.stage_out, pu0, pphi));
+    CK(cudaMemcpyAsync(pu, w.stage_out, bytes, cudaMemcpyDefault, st));
+  } else {
+    TRY(solve_problem(pl, w, pb, pf, pu, pu0, pphi));
+  }
+  return FTOEP_OK;
+}
+
 ftoep_status solve_all_levels(ftoep_plan pl, const double* f, double* u, const double* u0, const double* phi,
                               bool host) {
   TRY(fork_streams(pl));
-  for (auto& pb : pl->probs) {
-    Ws& wr = pl->ws[pb.stream];
-    TRY(ensure_level_ws(pl, wr));
-    if (host) TRY(ensure_staging(pl, wr));
-    Ws w = ws_for(pl, pb);
-    cudaStream_t st = w.st;
-    const double* pf = f + pb.foff;
-    double* pu = u + pb.foff;
-    const double* pu0 = u0 ? u0 + pb.voff : nullptr;
-    const double* pphi = phi ? phi + pb.voff : nullptr;
-    if (host) {
-      const size_t bytes = (size_t)pb.M * pb.N * sizeof(double);
-      CK(cudaMemcpyAsync(w.stage_in, pf, bytes, cudaMemcpyDefault, st));
-      if (pu0) {
-        CK(cudaMemcpyAsync(w.stage_v0, pu0, pb.M * sizeof(double), cudaMemcpyDefault, st));
-        pu0 = w.stage_v0;
-      }
-      if (pphi) {
-        CK(cudaMemcpyAsync(w.stage_v1, pphi, pb.M * sizeof(double), cudaMemcpyDefault, st));
-        pphi = w.stage_v1;
-      }
-      TRY(solve_problem(pl, w, pb, w.stage_in, w.stage_out, pu0, pphi));
-      CK(cudaMemcpyAsync(pu, w.stage_out, bytes, cudaMemcpyDefault, st));
-    } else {
-      TRY(solve_problem(pl, w, pb, pf, pu, pu0, pphi));
-    }
-  }
+  for (auto& pb : pl->probs) TRY(solve_on_stream(pl, pb, f, u, u0, phi, host));
   TRY(join_streams(pl));
   return FTOEP_OK;
 }
@@ -1304,6 +1399,15 @@ ftoep_status solve_all_chain(ftoep_plan pl, const double* f, double* u, const do
                              bool host) {
   if (host)
     for (auto& w : pl->ws) TRY(ensure_staging(pl, w));
+  // problems with the inverse-series solve: whole solves on the internal streams
+  bool any_finv = false;
+  for (auto& pb : pl->probs) any_finv |= pb.finv;
+  if (any_finv) {
+    TRY(fork_streams(pl));
+    for (auto& pb : pl->probs)
+      if (pb.finv) TRY(solve_on_stream(pl, pb, f, u, u0, phi, host));
+    TRY(join_streams(pl));
+  }
   for (size_t gi = 0; gi < pl->groups.size(); ++gi) {
     ChainGroup& g = pl->groups[gi];
     bool mixed = false;
@@ -1661,23 +1765,30 @@ ftoep_status ftoep_autotune(const ftoep_problem* probs, int nprob, void* cuda_st
   cudaEventCreate(&e1);
   std::vector<ftoep_tuning> cands;
   const int ns_list[] = {2, 4, 8};
-  for (int B : {1024, 2048, 4096})
-    for (int sch : {(int)FTOEP_SCHED_LEVELS, (int)FTOEP_SCHED_CHAIN}) {
-      if (sample.size() == 1) {
-        ftoep_tuning t{};
-        t.fft_tile = B;
-        t.scheduler = sch;
-        cands.push_back(t);
-        continue;
-      }
-      for (int ns : ns_list) {
-        ftoep_tuning t{};
-        t.fft_tile = B;
-        t.scheduler = sch;
-        t.streams = ns;
-        cands.push_back(t);
+  // the half-split solver only: the inverse-series solve trades accuracy for time (its
+  // error is normwise over the whole time axis), a choice the caller makes explicitly
+  for (int sv : {(int)FTOEP_SOLVER_HALFSPLIT}) {
+    for (int B : {1024, 2048, 4096}) {
+      for (int sch : {(int)FTOEP_SCHED_LEVELS, (int)FTOEP_SCHED_CHAIN}) {
+        if (sample.size() == 1) {
+          ftoep_tuning t{};
+          t.fft_tile = B;
+          t.scheduler = sch;
+          t.solver = sv;
+          cands.push_back(t);
+          continue;
+        }
+        for (int ns : ns_list) {
+          ftoep_tuning t{};
+          t.fft_tile = B;
+          t.scheduler = sch;
+          t.streams = ns;
+          t.solver = sv;
+          cands.push_back(t);
+        }
       }
     }
+  }
   float best_ms = -1.0f;
   ftoep_tuning best{};
   ftoep_status status = FTOEP_OK;
@@ -1712,6 +1823,244 @@ ftoep_status ftoep_autotune(const ftoep_problem* probs, int nprob, void* cuda_st
   if (status != FTOEP_OK) return status;
   *out = best;
   return FTOEP_OK;
+}
+
+// Restarted GMRES (Sec. 3.2) on the space-time system of problem iprob with zero initial
+// data: A u = f, A = I_M (x) T + K (x) I_N (the reordered Eq. 21; T the time operator's first
+// column a, K the spatial operator, for the Crank-Nicolson kind averaged over two levels).
+// Products: T by circulant embedding (product_lines), K by a stencil kernel.  Arnoldi with
+// classical Gram-Schmidt applied twice, Givens rotations on the host.
+ftoep_status ftoep_gmres(ftoep_plan pl, int iprob, const double* f, double* u, int restart, double tol, int maxit,
+                         int* iters, double* relres) {
+  if (!pl) return fail(nullptr, FTOEP_EINVAL, "plan is NULL");
+  if (iprob < 0 || iprob >= (int)pl->probs.size()) return fail(pl, FTOEP_EINVAL, "iprob out of range");
+  if (!f || !u) return fail(pl, FTOEP_EINVAL, "f and u must not be NULL");
+  if (restart < 1 || restart > kMaxBasis) return fail(pl, FTOEP_EINVAL, "restart must be in [1, %d]", kMaxBasis);
+  if (!(tol > 0.0) || maxit < 1) return fail(pl, FTOEP_EINVAL, "tol must be > 0 and maxit >= 1");
+  Prob& pb = pl->probs[iprob];
+  const int64_t M = pb.M, N = pb.N, L = M * N;
+  cudaStream_t st = pl->stream;
+  Ws w = pl->ws[0];
+  w.st = st;
+  TRY(build_product_spectrum(pl, w, pb, pb.a, (void**)&pb.spec_mv, P64));
+  const bool host = !is_device_ptr(f) || !is_device_ptr(u);
+  const int m = restart;
+  constexpr int nb = 256;
+  double *V = nullptr, *wv = nullptr, *fd = nullptr, *ud = nullptr, *partial = nullptr, *cdev = nullptr;
+  ftoep_status status = FTOEP_OK;
+  auto cleanup = [&]() {
+    release(pl, V);
+    release(pl, wv);
+    release(pl, fd);
+    release(pl, ud);
+    release(pl, partial);
+    release(pl, cdev);
+  };
+#define GTRY(expr)                 \
+  do {                             \
+    if ((status = (expr)) != FTOEP_OK) { \
+      cleanup();                   \
+      return status;               \
+    }                              \
+  } while (0)
+  GTRY(dalloc(pl, (void**)&V, (size_t)(m + 1) * L * sizeof(double)));
+  GTRY(dalloc(pl, (void**)&wv, (size_t)L * sizeof(double)));
+  GTRY(dalloc(pl, (void**)&partial, (size_t)(kMaxBasis + 1) * nb * sizeof(double)));
+  GTRY(dalloc(pl, (void**)&cdev, (size_t)(kMaxBasis + 1) * sizeof(double)));
+  const double* fin = f;
+  double* x = u;
+  if (host) {
+    GTRY(dalloc(pl, (void**)&fd, (size_t)L * sizeof(double)));
+    GTRY(dalloc(pl, (void**)&ud, (size_t)L * sizeof(double)));
+    if (cudaMemcpyAsync(fd, f, (size_t)L * sizeof(double), cudaMemcpyDefault, st) != cudaSuccess ||
+        cudaMemcpyAsync(ud, u, (size_t)L * sizeof(double), cudaMemcpyDefault, st) != cudaSuccess) {
+      cudaGetLastError();
+      cleanup();
+      return fail(pl, FTOEP_ECUDA, "gmres: staging copy failed");
+    }
+    fin = fd;
+    x = ud;
+  }
+  const double inv_h2 = 1.0 / (pb.h * pb.h);
+  auto Amul = [&](const double* xin, double* y) -> ftoep_status {
+    TRY(product_lines(pl, w, pb, P64, pb.spec_mv, xin, y, M, 0));
+    LAUNCH(FTOEP_K_OTHER, launch_space_add(y, xin, M, N, pb.d.space, inv_h2, pb.d.lambda, pb.sw, st));
+    return FTOEP_OK;
+  };
+  std::vector<double> hp((size_t)(kMaxBasis + 1) * nb);
+  auto dots = [&](const double* Vb, int k, const double* xin, double* out) -> ftoep_status {
+    LAUNCH(FTOEP_K_OTHER, launch_mdot(Vb, L, k, xin, L, partial, nb, st));
+    CK(cudaMemcpyAsync(hp.data(), partial, (size_t)k * nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int i = 0; i < k; ++i) {
+      double acc = 0.0;
+      for (int b = 0; b < nb; ++b) acc += hp[(size_t)i * nb + b];
+      out[i] = acc;
+    }
+    return FTOEP_OK;
+  };
+  auto norm = [&](const double* xin, double* out) -> ftoep_status {
+    double d = 0.0;
+    TRY(dots(xin, 1, xin, &d));
+    *out = std::sqrt(std::max(d, 0.0));
+    return FTOEP_OK;
+  };
+  auto Vc = [&](int i) { return V + (int64_t)i * L; };
+  double bnorm = 0.0, beta = 0.0;
+  GTRY(norm(fin, &bnorm));
+  std::vector<double> R((size_t)m * (m + 1), 0.0), cs(m), sn(m), g(m + 1), y(m), h(m + 1), c(m + 1);
+  int it = 0;
+  while (true) {
+    // true residual of the current iterate
+    GTRY(Amul(x, wv));
+    LAUNCH(FTOEP_K_OTHER, launch_lincomb(Vc(0), 1.0, fin, -1.0, wv, L, st));
+    GTRY(norm(Vc(0), &beta));
+    if (bnorm == 0.0 || beta <= tol * bnorm || it >= maxit) break;
+    LAUNCH(FTOEP_K_OTHER, launch_lincomb(Vc(0), 1.0 / beta, Vc(0), 0.0, nullptr, L, st));
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j = 0;
+    while (j < m && it < maxit) {
+      GTRY(Amul(Vc(j), wv));
+      std::fill(h.begin(), h.end(), 0.0);
+      for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+        GTRY(dots(V, j + 1, wv, c.data()));
+        for (int i = 0; i <= j; ++i) {
+          h[i] += c[i];
+          c[i] = -c[i];
+        }
+        CK(cudaMemcpyAsync(cdev, c.data(), (size_t)(j + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
+        LAUNCH(FTOEP_K_OTHER, launch_maxpy(wv, V, L, j + 1, cdev, L, st));
+      }
+      double hn = 0.0;
+      GTRY(norm(wv, &hn));
+      h[j + 1] = hn;
+      if (hn > 0.0) LAUNCH(FTOEP_K_OTHER, launch_lincomb(Vc(j + 1), 1.0 / hn, wv, 0.0, nullptr, L, st));
+      for (int i = 0; i < j; ++i) {  // earlier rotations on the new column
+        const double a = cs[i] * h[i] + sn[i] * h[i + 1];
+        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+        h[i] = a;
+      }
+      const double rr = std::hypot(h[j], h[j + 1]);
+      cs[j] = rr > 0.0 ? h[j] / rr : 1.0;
+      sn[j] = rr > 0.0 ? h[j + 1] / rr : 0.0;
+      h[j] = rr;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      for (int i = 0; i <= j; ++i) R[(size_t)i * m + j] = h[i];
+      ++j;
+      ++it;
+      if (std::fabs(g[j]) <= tol * bnorm || hn == 0.0) break;
+    }
+    for (int i = j - 1; i >= 0; --i) {  // R y = g, upper triangular
+      double acc = g[i];
+      for (int k = i + 1; k < j; ++k) acc -= R[(size_t)i * m + k] * y[k];
+      y[i] = R[(size_t)i * m + i] != 0.0 ? acc / R[(size_t)i * m + i] : 0.0;
+    }
+    CK(cudaMemcpyAsync(cdev, y.data(), (size_t)j * sizeof(double), cudaMemcpyHostToDevice, st));
+    LAUNCH(FTOEP_K_OTHER, launch_maxpy(x, V, L, j, cdev, L, st));
+  }
+  if (host && cudaMemcpyAsync(u, ud, (size_t)L * sizeof(double), cudaMemcpyDefault, st) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(pl, FTOEP_ECUDA, "gmres: copy out failed");
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(pl, FTOEP_ECUDA, "gmres: stream synchronize failed");
+  }
+#undef GTRY
+  cleanup();
+  if (iters) *iters = it;
+  if (relres) *relres = bnorm > 0.0 ? beta / bnorm : 0.0;
+  return FTOEP_OK;
+}
+
+// Advection sweeps of Sec. 3 (the fast procedure: space order, Figure 2): per node i = 1..M,
+// the lower-triangular Toeplitz system of one line, A-tilde U_i = B U_{i-1} + F_i, solved by
+// the library's own solve of one scalar problem with lambda = the diagonal shift:
+//   scheme 2: (c L1 + I/h) U_i = (I/h - c L1) U_{i-1} + F_i, c = mu/2 -- times 2, the scalar
+//             sub-diffusion problem (mu L1 + (2/h) I), with mu L1 U_{i-1} by the plan's
+//             circulant-embedded product;
+//   scheme 3: (c W + I/h) U_i = U_{i-1}/h + F_i -- the scalar hyperbolic problem, lambda = 1/h.
+// Initial data enter the right-hand side through the plan's initial-data weights (the
+// u-form rows, the solve itself with zero initial value).
+ftoep_status ftoep_advection_sweep(int scheme, double gamma, double T, double L, int64_t N, int64_t M,
+                                   const double* f, const double* u0, const double* phi, double* u, int precision,
+                                   void* cuda_stream) {
+  g_create_error.clear();
+  if (scheme != 2 && scheme != 3) return fail(nullptr, FTOEP_EINVAL, "advection sweep: scheme %d unknown", scheme);
+  if (scheme == 2 && !(gamma > 0.0 && gamma < 1.0))
+    return fail(nullptr, FTOEP_EINVAL, "advection sweep: scheme 2 needs gamma in (0,1), got %g", gamma);
+  if (scheme == 3 && !(gamma > 1.0 && gamma < 2.0))
+    return fail(nullptr, FTOEP_EINVAL, "advection sweep: scheme 3 needs gamma in (1,2), got %g", gamma);
+  if (N < 1 || M < 1 || !f || !u || !(T > 0.0) || !(L > 0.0) ||
+      (precision != FTOEP_FP64 && precision != FTOEP_MIXED))
+    return fail(nullptr, FTOEP_EINVAL, "advection sweep: N, M >= 1, f, u not NULL, T, L > 0, precision FP64/MIXED");
+  const double h = L / (double)M;
+  ftoep_problem d{};
+  d.kind = scheme == 2 ? FTOEP_L1_SUBDIFFUSION : FTOEP_L1_HYPERBOLIC;
+  d.space = FTOEP_SPACE_NONE;
+  d.precision = precision;
+  d.gamma = gamma;
+  d.T = T;
+  d.L = 1.0;
+  d.lambda = scheme == 2 ? 2.0 / h : 1.0 / h;
+  d.N = N;
+  d.M = 1;
+  ftoep_plan pl = nullptr;
+  TRY(ftoep_create(&pl, &d, 1, nullptr, cuda_stream));
+  ftoep_status status = FTOEP_OK;
+  {
+    Prob& pb = pl->probs[0];
+    Ws& w = pl->ws[0];
+    cudaStream_t st = w.st;
+    const int64_t LN = M * N;
+    const bool host = !is_device_ptr(f) || !is_device_ptr(u) || !is_device_ptr(u0) || !is_device_ptr(phi);
+    std::vector<double> hu0(u0 ? M : 0), hphi(phi ? M : 0);
+    double *fd = nullptr, *ud = nullptr, *g = nullptr, *t = nullptr;
+    auto run = [&]() -> ftoep_status {
+      if (u0) CK(cudaMemcpy(hu0.data(), u0, M * sizeof(double), cudaMemcpyDefault));
+      if (phi) CK(cudaMemcpy(hphi.data(), phi, M * sizeof(double), cudaMemcpyDefault));
+      TRY(ensure_level_ws(pl, w));
+      if (scheme == 2) TRY(build_product_spectrum(pl, w, pb, pb.a, (void**)&pb.spec_mv, P64));
+      ALLOC(g, N * sizeof(double));
+      ALLOC(t, N * sizeof(double));
+      const double* F = f;
+      double* U = u;
+      if (host) {
+        ALLOC(fd, LN * sizeof(double));
+        ALLOC(ud, LN * sizeof(double));
+        CK(cudaMemcpyAsync(fd, f, LN * sizeof(double), cudaMemcpyDefault, st));
+        F = fd;
+        U = ud;
+      }
+      for (int64_t i = 0; i < M; ++i) {
+        const double* up = i > 0 ? U + (i - 1) * N : nullptr;
+        if (scheme == 2) {
+          // g = 2 [ (1/h) U_{i-1} - (mu/2) L1 U_{i-1} + F_i ] + mu G_{n-1} (u0_i + u0_{i-1})
+          if (up) TRY(product_lines(pl, w, pb, P64, pb.spec_mv, up, t, 1, 0));
+          const double s0 = u0 ? hu0[i] + (i > 0 ? hu0[i - 1] : 0.0) : 0.0;
+          LAUNCH(FTOEP_K_OTHER, launch_sweep_rhs(g, up, up ? t : nullptr, F + i * N, u0 ? pb.wu0 : nullptr, nullptr, N,
+                                                 2.0 / h, -1.0, 2.0, s0, 0.0, st));
+        } else {
+          // g = U_{i-1}/h + F_i + (u0 and phi weights of Eq. 17)
+          LAUNCH(FTOEP_K_OTHER, launch_sweep_rhs(g, up, nullptr, F + i * N, u0 ? pb.wu0 : nullptr,
+                                                 phi ? pb.wphi : nullptr, N, 1.0 / h, 0.0, 1.0, u0 ? hu0[i] : 0.0,
+                                                 phi ? hphi[i] : 0.0, st));
+        }
+        TRY(solve_problem(pl, w, pb, g, U + i * N, nullptr, nullptr));
+      }
+      if (host) CK(cudaMemcpyAsync(u, ud, LN * sizeof(double), cudaMemcpyDefault, st));
+      CK(cudaStreamSynchronize(st));
+      return FTOEP_OK;
+    };
+    status = run();
+    if (status != FTOEP_OK) g_create_error = pl->err;
+  }
+  ftoep_destroy(pl);
+  return status;
 }
 
 ftoep_status ftoep_sync(ftoep_plan pl) {

@@ -129,11 +129,13 @@ __device__ __forceinline__ void conv_smem_body(Vt<T>* sm, const Vt<T>* __restric
 }
 
 // Four-step step A on columns c0 .. c0+C-1: zin is the pair's input half (row layout
-// j1*n2 + j2), sc the pair's scratch (n elements).  No barrier at the end.
+// j1*n2 + j2), sc the pair's scratch (n elements).  nvalid > 0: input entries at index
+// >= nvalid are read as zero (the padding of a row whose tail holds other data).  No
+// barrier at the end.
 template <typename T, int INF = 8, bool ASYNC = false>
 __device__ __forceinline__ void conv_col_fwd_body(Vt<T>* sm, const Vt<T>* __restrict__ zin_row,
                                                   Vt<T>* __restrict__ sc_row, int logn1, int logn2, int C, int c0,
-                                                  const Vt<T>* __restrict__ tw) {
+                                                  const Vt<T>* __restrict__ tw, int64_t nvalid = 0) {
   typedef Vt<T> V;
   const int n2 = 1 << logn2, logn = logn1 + logn2, n = 1 << logn;
   const V* __restrict__ zin = zin_row + c0;
@@ -141,17 +143,22 @@ __device__ __forceinline__ void conv_col_fwd_body(Vt<T>* sm, const Vt<T>* __rest
   const V* __restrict__ twn = tw + (n - 2);
   const SmLayout L = sm_layout<V>(logn1);
   const int np = fftr_npasses<V>(logn1);
+  const int64_t nv = nvalid > 0 ? nvalid - c0 : ((int64_t)1 << 62);  // relative to zin
   if constexpr (ASYNC) {  // input half: rows e < n1/2 of the C columns
     const int lc = 31 - __clz(C);
     for (int i = threadIdx.x; i < (C << (logn1 - 1)); i += blockDim.x) {
       const int t = i & (C - 1), e = i >> lc;
-      async_copy(&sm[sm_pos<V>(L, t, e)], zin + (int64_t)e * n2 + t);
+      const int64_t j = (int64_t)e * n2 + t;
+      if (j < nv) async_copy(&sm[sm_pos<V>(L, t, e)], zin + j);
+      else sm[sm_pos<V>(L, t, e)] = vzero<V>();
     }
     async_wait_all();
     fftr_pass<V, true, true>(0, logn1, C, tw, true, SmAt<V>{sm, L}, SmPut<V>{sm, L});
   } else {
-    fftr_pass<V, true, true, true, false, INF>(0, logn1, C, tw, true,
-                                               [&](int t, int e) { return zin[(int64_t)e * n2 + t]; }, SmPut<V>{sm, L});
+    fftr_pass<V, true, true, true, false, INF>(0, logn1, C, tw, true, [&](int t, int e) {
+      const int64_t j = (int64_t)e * n2 + t;
+      return j < nv ? zin[j] : vzero<V>();
+    }, SmPut<V>{sm, L});
   }
   __syncthreads();
   fftr_passes<V, true, true>(sm, logn1, C, tw, 1, np - 1, false);

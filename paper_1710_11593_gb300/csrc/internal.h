@@ -164,8 +164,59 @@ struct ConvArgs {
   const void* spec;
   const void* tw;
   void* scratch;    // [npairs][n] (four-step only)
+  int64_t nvalid;   // four-step step A: input entries at index >= nvalid read as zero (0: none)
 };
 int launch_conv(Prec prec, const ConvArgs& a, cudaStream_t st);
+// One column step of the four-step convolution alone (length n = 2^logn > nsmem):
+// inverse = 0: step A (zin -> scratch), 1: step C (scratch -> zout, mode as above).
+int launch_fourstep_cols(Prec prec, const ConvArgs& a, int inverse, cudaStream_t st);
+
+// Inverse-series solve of every pair: x = h * y over the padded length Np, as one cyclic
+// convolution of length n = 2 Np (exact for the first Np outputs) with the pair's packed
+// inverse spectrum -- two modes with different kernels in one complex FFT, so the
+// spectrum product pairs each frequency with its partner n - k (as the block inverse).
+// Four-step only (n above the shared-memory convolution length).
+struct FinvArgs {
+  void* z;           // pairs [npairs][ld]: right-hand side in, solution out (first Np entries)
+  int64_t ld;
+  int64_t N;         // right-hand side entries; entries N .. Np-1 are read as zero
+  int64_t npairs;
+  int logn;          // n = 2 Np
+  const void* cs;    // packed spectra [npairs][n], four-step storage order, scaled by 1/n
+  const void* tw;
+  void* scratch;     // [npairs][n]
+};
+int launch_full_inverse(Prec prec, const FinvArgs& a, cudaStream_t st);
+
+// Plan time: the packed spectra of the pairs' inverse columns h (double, first Np entries
+// of each pair row; zero-padded to n = 2 Np) in precision prec.
+struct FinvSpecArgs {
+  const double2* h;  // [npairs][ld]
+  int64_t ld;
+  int64_t N;         // entries of h used (the rest read as zero)
+  int64_t npairs;
+  int logn;
+  double2* scratch64;  // [npairs][n]
+  void* cs;            // [npairs][n]
+  const double2* tw64;
+};
+int launch_finv_spectrum(Prec prec, const FinvSpecArgs& a, cudaStream_t st);
+
+// Restarted GMRES vector kernels (gmres.cu), fields [M][N] double, L = M N.
+constexpr int kMaxBasis = 64;  // largest restart length
+int launch_space_add(double* y, const double* x, int64_t M, int64_t N, int space, double inv_h2, double lambda,
+                     double sw, cudaStream_t st);
+// partial[i * nblocks + b] = block b's part of <V_i, w>, i < k (V_i = V + i * ldv)
+int launch_mdot(const double* V, int64_t ldv, int k, const double* w, int64_t L, double* partial, int nblocks,
+                cudaStream_t st);
+// w += sum_{i<k} c_i V_i (c: k doubles in device memory, k <= kMaxBasis)
+int launch_maxpy(double* w, const double* V, int64_t ldv, int k, const double* c, int64_t L, cudaStream_t st);
+// advection sweep step: g = a up + b t + c F + s0 w0 + s1 w1 over N entries (up, t, w0, w1
+// nullable = 0)
+int launch_sweep_rhs(double* g, const double* up, const double* t, const double* F, const double* w0, const double* w1,
+                     int64_t N, double a, double b, double c, double s0, double s1, cudaStream_t st);
+// y = a x + b z (z unread when b = 0)
+int launch_lincomb(double* y, double a, const double* x, double b, const double* z, int64_t L, cudaStream_t st);
 
 // Solve the lower-triangular Toeplitz systems of every pair on one time block
 // [t0, t0 + B) in place (history from earlier blocks already subtracted).

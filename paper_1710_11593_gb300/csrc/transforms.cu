@@ -1130,7 +1130,7 @@ __global__ void __launch_bounds__(kThreads) conv_col_fwd_kernel(ConvArgs A, int 
   const int64_t p = blockIdx.y;
   const int64_t n = (int64_t)1 << (logn1 + logn2);
   conv_col_fwd_body<T>(reinterpret_cast<V*>(smraw), (const V*)A.zin + p * A.ld_in + A.in_off,
-                       (V*)A.scratch + p * n, logn1, logn2, C, (int)blockIdx.x * C, (const V*)A.tw);
+                       (V*)A.scratch + p * n, logn1, logn2, C, (int)blockIdx.x * C, (const V*)A.tw, A.nvalid);
 }
 
 template <typename T>
@@ -1277,6 +1277,30 @@ int launch_spectrum(Prec prec, const SpecArgs& a, cudaStream_t st) {
   else if (prec == P32) spectrum_launch<float>(a, st);
   else spectrum_launch<FF>(a, st);
   return (1 << a.logn) <= a.nsmem ? 1 : 2;
+}
+
+namespace {
+template <typename T>
+void fourstep_cols_launch(const ConvArgs& a, int inverse, cudaStream_t st) {
+  Split sp = split_of(a.logn);
+  const int C = fourstep_cols<T>(sp.logn1, sp.logn2);
+  const size_t smc = (size_t)C * ((size_t)1 << sp.logn1) * sizeof(Vt<T>);
+  dim3 gc((unsigned)((1 << sp.logn2) / C), (unsigned)a.npairs);
+  if (!inverse) {
+    set_smem((const void*)conv_col_fwd_kernel<T>, smc);
+    conv_col_fwd_kernel<T><<<gc, kThreads, smc, st>>>(a, sp.logn1, sp.logn2, C);
+  } else {
+    set_smem((const void*)conv_col_inv_kernel<T>, smc);
+    conv_col_inv_kernel<T><<<gc, kThreads, smc, st>>>(a, sp.logn1, sp.logn2, C);
+  }
+}
+}  // namespace
+
+int launch_fourstep_cols(Prec prec, const ConvArgs& a, int inverse, cudaStream_t st) {
+  if (prec == P64) fourstep_cols_launch<double>(a, inverse, st);
+  else if (prec == P32) fourstep_cols_launch<float>(a, inverse, st);
+  else fourstep_cols_launch<FF>(a, inverse, st);
+  return 1;
 }
 
 int launch_conv(Prec prec, const ConvArgs& a, cudaStream_t st) {

@@ -26,13 +26,14 @@ SPACE_NONE, SPACE_DIRICHLET_LAPLACIAN = 0, 1
 FP64, MIXED = 0, 1
 
 SCHED_AUTO, SCHED_LEVELS, SCHED_CHAIN = 0, 1, 2
+SOLVER_AUTO, SOLVER_HALFSPLIT, SOLVER_INVERSE = 0, 1, 2
 
 EXPORTS = ("ftoep_create", "ftoep_weights", "ftoep_solve", "ftoep_matvec", "ftoep_adjoint", "ftoep_profile",
            "ftoep_profile_read", "ftoep_matvec_noalloc", "ftoep_autotune", "ftoep_two_sided_cg", "ftoep_sync",
-           "ftoep_last_error", "ftoep_destroy")
-K_BLOCK_SOLVE, K_CONV_SMEM, K_CONV_FOURSTEP, K_SINE, K_OTHER, K_RESIDUAL, K_CHAIN = range(7)
+           "ftoep_last_error", "ftoep_destroy", "ftoep_problem_solver", "ftoep_gmres", "ftoep_advection_sweep")
+K_BLOCK_SOLVE, K_CONV_SMEM, K_CONV_FOURSTEP, K_SINE, K_OTHER, K_RESIDUAL, K_CHAIN, K_INVERSE = range(8)
 KERNEL_CLASSES = {K_BLOCK_SOLVE: "block_solve", K_CONV_SMEM: "conv_smem", K_CONV_FOURSTEP: "conv_fourstep",
-                  K_SINE: "sine", K_OTHER: "other", K_RESIDUAL: "residual", K_CHAIN: "chain"}
+                  K_SINE: "sine", K_OTHER: "other", K_RESIDUAL: "residual", K_CHAIN: "chain", K_INVERSE: "inverse"}
 
 
 class FtoepError(RuntimeError):
@@ -49,7 +50,7 @@ class ftoep_problem(ctypes.Structure):
 
 class ftoep_tuning(ctypes.Structure):
     _fields_ = [("leaf", ctypes.c_int), ("fft_tile", ctypes.c_int), ("gemm_max_level", ctypes.c_int),
-                ("scheduler", ctypes.c_int), ("streams", ctypes.c_int)]
+                ("scheduler", ctypes.c_int), ("streams", ctypes.c_int), ("solver", ctypes.c_int)]
 
 
 _lib = None
@@ -80,6 +81,11 @@ def load(path: Optional[str] = None):
     lib.ftoep_sync.argtypes = [vp]
     lib.ftoep_last_error.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.ftoep_destroy.argtypes = [vp]
+    lib.ftoep_problem_solver.argtypes = [vp, ci, ctypes.POINTER(ci)]
+    lib.ftoep_gmres.argtypes = [vp, ci, dp, dp, ci, ctypes.c_double, ci, ctypes.POINTER(ci),
+                                ctypes.POINTER(ctypes.c_double)]
+    lib.ftoep_advection_sweep.argtypes = [ci, ctypes.c_double, ctypes.c_double, ctypes.c_double, i64, i64, dp, dp,
+                                          dp, dp, ci, vp]
     lib.ftoep_matvec_noalloc.argtypes = [vp, i64, vp, vp, i64, ci, vp]
     lib.ftoep_two_sided_cg.argtypes = [ctypes.c_double, ctypes.c_double, i64, dp, dp, ctypes.c_double, ci,
                                        ctypes.POINTER(ci), ctypes.POINTER(ctypes.c_double), vp]
@@ -157,7 +163,7 @@ def ftoep_create(problems: Sequence[ProblemSpec], tuning: Optional[dict] = None,
     if tuning:
         tp = ctypes.pointer(ftoep_tuning(int(tuning.get("leaf", 0)), int(tuning.get("fft_tile", 0)),
                                          int(tuning.get("gemm_max_level", 0)), int(tuning.get("scheduler", 0)),
-                                         int(tuning.get("streams", 0))))
+                                         int(tuning.get("streams", 0)), int(tuning.get("solver", 0))))
     h = ctypes.c_void_p()
     st = current_stream_handle() if stream is None else stream
     rc = lib.ftoep_create(ctypes.byref(h), arr, len(problems), tp, ctypes.c_void_p(st))
@@ -231,7 +237,7 @@ def ftoep_destroy(plan: int):
 
 
 def ftoep_autotune(problems: Sequence[ProblemSpec], stream: Optional[int] = None) -> dict:
-    """Time the candidate tunings (block length, scheduler, internal streams) on the problems
+    """Time the candidate tunings (solver, block length, scheduler, internal streams) on the problems
     (C ABI ftoep_autotune) and return the fastest as a dict for Plan(..., tuning=...)."""
     lib = load()
     arr = (ftoep_problem * len(problems))(*[p.to_c() for p in problems])
@@ -240,7 +246,7 @@ def ftoep_autotune(problems: Sequence[ProblemSpec], stream: Optional[int] = None
     rc = lib.ftoep_autotune(arr, len(problems), ctypes.c_void_p(st), ctypes.byref(out))
     _check(rc, None)
     return {"leaf": out.leaf, "fft_tile": out.fft_tile, "gemm_max_level": out.gemm_max_level,
-            "scheduler": out.scheduler, "streams": out.streams}
+            "scheduler": out.scheduler, "streams": out.streams, "solver": out.solver}
 
 
 def tuning_key(problems: Sequence[ProblemSpec], device: str = "") -> str:
@@ -257,7 +263,7 @@ def tuning_key(problems: Sequence[ProblemSpec], device: str = "") -> str:
 
 
 SHIPPED_TUNING = os.path.join(HERE, "tuned_gb300.json")
-TUNING_FIELDS = ("leaf", "fft_tile", "gemm_max_level", "scheduler", "streams")
+TUNING_FIELDS = ("leaf", "fft_tile", "gemm_max_level", "scheduler", "streams", "solver")
 
 
 def _tuning_fields(entry: dict) -> dict:
@@ -337,6 +343,30 @@ class Plan:
     def __exit__(self, *exc):
         self.close()
 
+    def solver(self, iprob: int = 0) -> int:
+        """SOLVER_HALFSPLIT or SOLVER_INVERSE: the solver the plan uses for problem iprob."""
+        out = ctypes.c_int(0)
+        _check(load().ftoep_problem_solver(self.handle, iprob, ctypes.byref(out)), self.handle)
+        return out.value
+
+    def gmres(self, f, u=None, iprob: int = 0, restart: int = 30, tol: float = 1e-12, maxit: int = 10000):
+        """Restarted GMRES on problem iprob's space-time system (zero initial data), the
+        comparison path of Sec. 3.2; u holds the initial guess (zeros if None).  Returns
+        (u, Arnoldi steps, relative residual of u)."""
+        N, M = self.problems[iprob].N, self.problems[iprob].M
+        if _numel(f) != M * N:
+            raise FtoepError(FTOEP_EINVAL, f"f has {_numel(f)} elements, problem expects {M * N}")
+        if u is None:
+            if isinstance(f, np.ndarray):
+                u = np.zeros_like(f)
+            else:
+                import torch
+                u = torch.zeros_like(f)
+        it, rr = ctypes.c_int(0), ctypes.c_double(0.0)
+        _check(load().ftoep_gmres(self.handle, iprob, _ptr(f), _ptr(u), restart, tol, maxit, ctypes.byref(it),
+                                  ctypes.byref(rr)), self.handle)
+        return u, it.value, rr.value
+
     def weights(self, iprob: int = 0, with_dgamma: bool = False):
         N = self.problems[iprob].N
         a = np.empty(N)
@@ -390,6 +420,24 @@ class Plan:
     def profile_read(self):
         """{class name: (event ms, timed operations, kernels launched)} since profile()."""
         return {name: ftoep_profile_read(self.handle, k) for k, name in KERNEL_CLASSES.items()}
+
+
+def advection_sweep(scheme: int, f, gamma: float, T: float = 1.0, L: float = 1.0, u0=None, phi=None, u=None,
+                    precision: int = FP64, stream: Optional[int] = None):
+    """Schemes 2 and 3 of Sec. 3 (D^g u + u_x = f, inflow u(0, t) = 0) by the space-order sweep
+    (C ABI ftoep_advection_sweep).  f: [M][N] (row i-1 = node x_i = i L/M); returns u."""
+    M, N = (f.shape[0], f.shape[1]) if hasattr(f, "shape") and len(f.shape) == 2 else (1, _numel(f))
+    if u is None:
+        if isinstance(f, np.ndarray):
+            u = np.empty_like(f)
+        else:
+            import torch
+            u = torch.empty_like(f)
+    st = current_stream_handle() if stream is None else stream
+    rc = load().ftoep_advection_sweep(scheme, gamma, T, L, N, M, _ptr(f), _ptr(u0), _ptr(phi), _ptr(u), precision,
+                                      ctypes.c_void_p(st))
+    _check(rc, None)
+    return u
 
 
 def solve(f, gamma: float, kind: Optional[int] = None, precision: int = FP64, space: int = SPACE_DIRICHLET_LAPLACIAN,

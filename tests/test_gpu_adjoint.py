@@ -179,3 +179,23 @@ def test_autograd_backward_twice_and_plan_reuse(torch_ft):
     assert u2.grad_fn is not None and torch.equal(u2, u)
     assert len(ag._plans) == 1
     ag.clear_plan_cache()
+
+
+@pytest.mark.parametrize("kind,gamma", [(0, 0.45), (1, 1.5)])
+def test_adjoint_of_mixed_plan_runs_in_double(torch_ft, oracle, kind, gamma):
+    """A mixed-precision plan's adjoint solves in double (its own double block-inverse
+    spectra): the oracle's transposed march at 1e-12, several time blocks."""
+    torch, ftoep, _ = torch_ft
+    M, N = 31, 3000
+    rng = np.random.default_rng(21 + kind)
+    f = rng.standard_normal((M, N))
+    gg = rng.standard_normal((M, N))
+    with ftoep.Plan([ftoep.ProblemSpec(kind, gamma, N, M, 1, ftoep.MIXED)], {"fft_tile": 512}) as plan:
+        u = plan.solve(torch.from_numpy(f).cuda())
+        dldf, dg = plan.adjoint(torch.from_numpy(gg).cuda(), u)
+        plan.sync()
+        u, dldf = u.cpu().numpy(), dldf.cpu().numpy()
+    lam = oracle.adjoint_march(kind, 1, gamma, gg)
+    assert _rel(dldf, lam) < 1e-12
+    ref = oracle.gamma_gradient(kind, gamma, oracle.march(kind, 1, gamma, f), lam)
+    assert abs(dg[0] - ref) <= 1e-8 * abs(ref)

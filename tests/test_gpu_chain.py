@@ -43,7 +43,8 @@ def _check(a, b, tol, what):
 
 
 def _solve(ft, specs, f, sched, **kw):
-    with ft.Plan(specs, tuning={"scheduler": sched}) as plan:
+    # the half-split solver: the chain runs every pair's block solves and levels
+    with ft.Plan(specs, tuning={"scheduler": sched, "solver": ft.SOLVER_HALFSPLIT}) as plan:
         u = plan.solve(f, **kw)
         plan.sync()
     return u

@@ -18,7 +18,7 @@ from paper_1710_11593_gb300 import workloads as wl
 pytestmark = pytest.mark.gpu
 
 CN = 2
-SMALL_TUNE = {"leaf": 8, "fft_tile": 64, "gemm_max_level": 16}
+SMALL_TUNE = {"leaf": 8, "fft_tile": 64, "gemm_max_level": 16, "solver": 1}  # half-split
 
 
 @pytest.fixture(scope="module")
@@ -54,7 +54,9 @@ def _solve(ft, specs, f, tuning=None, u0=None, phi=None):
     (1.3, 40, 1500, 0, None),                      # M+1 = 41: chirp-z sine transform
     (1.8, 63, 3000, 1, {"fft_tile": 256}),         # mixed, 12 blocks
     (1.5, 100, 2000, 1, None),                     # mixed, M+1 = 101 (chirp-z)
-    (1.95, 7, 9000, 0, {"fft_tile": 512}),         # four-step levels, ragged N
+    (1.95, 7, 9000, 0, {"fft_tile": 512, "solver": 1}),  # half-split four-step levels, ragged N
+    (1.95, 7, 9000, 0, {"solver": 2}),             # inverse-series solve
+    (1.4, 30, 12000, 1, {"solver": 2}),            # inverse-series solve, mixed
 ])
 def test_cn_vs_oracle(ft, oracle, gamma, M, N, prec, tune):
     rng = np.random.default_rng(M * 7 + N)
@@ -87,7 +89,7 @@ def test_cn_in_chain_batch(ft, oracle, prec):
     specs = [ft.ProblemSpec(k, g, N, M, 1, prec) for k, g, M, N in cases]
     fs = [wl.random_field((M, N), seed=11 * i + M) for i, (_, _, M, N) in enumerate(cases)]
     f = np.concatenate([x.reshape(-1) for x in fs])
-    u = _solve(ft, specs, f, {"scheduler": ft.SCHED_CHAIN})
+    u = _solve(ft, specs, f, {"scheduler": ft.SCHED_CHAIN, "solver": ft.SOLVER_HALFSPLIT})
     off = 0
     for (k, g, M, N), fi in zip(cases, fs):
         ref = oracle.march(k, 1, g, fi)

@@ -43,7 +43,7 @@ def _solve_gpu(ft, kind, gamma, f, space=1, precision=0, lam=1.0, u0=None, phi=N
     return u.cpu().numpy()
 
 
-SMALL_TUNE = {"leaf": 8, "fft_tile": 64, "gemm_max_level": 16}
+SMALL_TUNE = {"leaf": 8, "fft_tile": 64, "gemm_max_level": 16, "solver": 1}  # half-split
 
 
 def test_config1_scalar(ft, oracle):
@@ -60,10 +60,10 @@ def test_config1_scalar(ft, oracle):
 @pytest.mark.parametrize("kind,gamma,M,N,tune", [
     (0, 0.7, 31, 600, None),
     (0, 0.7, 31, 600, SMALL_TUNE),
-    (0, 0.3, 15, 1000, {"leaf": 4, "fft_tile": 32, "gemm_max_level": 4}),
+    (0, 0.3, 15, 1000, {"leaf": 4, "fft_tile": 32, "gemm_max_level": 4, "solver": 1}),
     (1, 1.5, 31, 777, SMALL_TUNE),
     (1, 1.9, 63, 300, None),
-    (0, 0.95, 7, 2049, {"leaf": 16, "fft_tile": 128, "gemm_max_level": 32}),
+    (0, 0.95, 7, 2049, {"leaf": 16, "fft_tile": 128, "gemm_max_level": 32, "solver": 1}),
 ])
 def test_fp64_random_rhs(ft, oracle, kind, gamma, M, N, tune):
     f = wl.random_field((M, N), seed=M * 1000 + N)

@@ -48,6 +48,8 @@ def test_invalid_problem_rejected(kw, status, msg):
     ({"fft_tile": 8192}, "fft_tile"),
     ({"fft_tile": 100}, "fft_tile"),
     ({"gemm_max_level": 4096}, "gemm_max_level"),
+    ({"solver": 3}, "solver"),
+    ({"solver": -1}, "solver"),
 ])
 def test_invalid_tuning_rejected(tune, msg):
     with pytest.raises(ftoep.FtoepError) as ei:
@@ -80,7 +82,7 @@ def test_tuning_key_buckets_and_cache_roundtrip(tmp_path, monkeypatch):
     assert ftoep.tuning_key(a, "X") != ftoep.tuning_key(a, "Y")
     path = tmp_path / "t.json"
     key = ftoep.tuning_key(a, "")
-    want = {"leaf": 0, "fft_tile": 2048, "gemm_max_level": 0, "scheduler": 2, "streams": 8}
+    want = {"leaf": 0, "fft_tile": 2048, "gemm_max_level": 0, "scheduler": 2, "streams": 8, "solver": 2}
     path.write_text(json.dumps({key: want}))
     monkeypatch.setattr(ftoep, "ftoep_autotune", lambda *x, **k: (_ for _ in ()).throw(AssertionError("ran")))
     import sys
@@ -104,3 +106,29 @@ def test_two_sided_cg_validates_before_any_device_work(kw):
     rc = lib.ftoep_two_sided_cg(args["gamma"], args["T"], args["N"], f.ctypes.data, u.ctypes.data, args["tol"],
                                 args["maxit"], None, None, None)
     assert rc == ftoep.FTOEP_EINVAL
+
+
+@pytest.mark.parametrize("kw", [dict(scheme=1), dict(scheme=2, gamma=1.5), dict(scheme=3, gamma=0.5), dict(N=0),
+                                dict(M=0), dict(T=0.0), dict(L=-1.0), dict(precision=2)])
+def test_advection_sweep_validates_before_any_device_work(kw):
+    """Argument checks of ftoep_advection_sweep return FTOEP_EINVAL before touching CUDA."""
+    import numpy as np
+    from paper_1710_11593_gb300 import ftoep
+    args = dict(scheme=2, gamma=0.5, T=1.0, L=1.0, N=8, M=4, precision=0)
+    args.update(kw)
+    f = np.ones(max(1, args["M"] * args["N"]))
+    u = np.zeros_like(f)
+    lib = ftoep.load()
+    rc = lib.ftoep_advection_sweep(args["scheme"], args["gamma"], args["T"], args["L"], args["N"], args["M"],
+                                   f.ctypes.data, None, None, u.ctypes.data, args["precision"], None)
+    assert rc == ftoep.FTOEP_EINVAL
+
+
+def test_gmres_validates_its_arguments():
+    """ftoep_gmres without a plan returns FTOEP_EINVAL (no device work)."""
+    import numpy as np
+    from paper_1710_11593_gb300 import ftoep
+    f = np.ones(8)
+    u = np.zeros(8)
+    lib = ftoep.load()
+    assert lib.ftoep_gmres(None, 0, f.ctypes.data, u.ctypes.data, 10, 1e-10, 10, None, None) == ftoep.FTOEP_EINVAL
