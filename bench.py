@@ -43,7 +43,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["diffusion", "wave", "scalar", "batched", "twosided"])
+    ap.add_argument("--workload", default="batched",
+                    choices=["diffusion", "wave", "wave_cn", "scalar", "batched", "twosided", "advection", "gmres",
+                             "adjoint"])
     ap.add_argument("--nprob", type=int, default=512, help="batched workload: number of problems")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
                     help="default: fp64 for diffusion/scalar, mixed for wave")
@@ -72,6 +74,10 @@ def workload(name, nprob=512, M=None, N=None):
     if name == "wave":
         p = wl.config_wave(M=M or 4095, N=N or 262144)
         return p, f"wave_g1.5_M{p.M}_N{p.N}"
+    if name == "wave_cn":  # config 3's problem with the Crank-Nicolson average of the spatial term
+        p = wl.config_wave(M=M or 4095, N=N or 262144)
+        p.kind = 2
+        return p, f"wave_cn_g1.5_M{p.M}_N{p.N}"
     p = wl.config_scalar(N=N or 1024)
     return p, f"scalar_g0.5_N{p.N}"
 
@@ -165,7 +171,14 @@ def work_model(p, precision, solver=1):
     return flops, byts
 
 
-def chain_roofline(flops, byts, prof, precision):
+# DRAM bytes (read + write) of the float chain kernel per unknown it solves, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of a launch of the 32-problem batch of
+# the same generator (5.92e8 unknowns in one group: 42.6 GB per launch; profiles/
+# chain_solve_kernel.md); a launch's traffic grows with the unknowns it solves.
+CHAIN_FLOAT_DRAM_BYTES_PER_UNKNOWN = 42.66e9 / 591616893
+
+
+def chain_roofline(flops, byts, prof, precision, units=None):
     """Roofline of the persistent per-pair solve of a batched plan from its own event time:
     a chain launch runs alone on the GPU (every per-problem phase before it has joined, the
     ones after it wait for it), in the timed solves as in the instrumented one, so its
@@ -187,8 +200,14 @@ def chain_roofline(flops, byts, prof, precision):
                "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs)"}
     main, other = (alu_obj, hbm_obj) if alu_obj["frac"] >= hbm_obj["frac"] else (hbm_obj, alu_obj)
     out = dict(main)
+    traffic = None
+    if precision == "mixed" and units and launches:
+        # every unknown passes through two chain launches per step (first solve, correction)
+        traffic = CHAIN_FLOAT_DRAM_BYTES_PER_UNKNOWN * 2 * units / launches
     out.update({"kernel_class": "chain", "kernel": "chain_solve_kernel", "class_ms_per_step": ms,
-                "launches_per_step": launches, "per_launch_ms": ms / max(1, launches), "traffic": None,
+                "launches_per_step": launches, "per_launch_ms": ms / max(1, launches), "traffic": traffic,
+                "traffic_note": "dram bytes per launch: a 32-problem ncu capture scaled by the unknowns per launch"
+                if traffic else None,
                 "other_bound": other,
                 "note": "flops: 5 n log2 n per complex FFT of length n, 6 per complex product (block solves and "
                         "every cross-block level of both solves); bytes: compulsory HBM bytes of those steps; "
@@ -524,7 +543,7 @@ def run_batched(args):
         for k in f1:
             fl[k] = fl.get(k, 0.0) + f1[k]
             by[k] = by.get(k, 0.0) + b1[k]
-    roof = chain_roofline(fl, by, prof, precision) or roofline_of(fl, by, prof, ms, precision)
+    roof = chain_roofline(fl, by, prof, precision, units) or roofline_of(fl, by, prof, ms, precision)
     # end to end through host buffers (pinned), copies inside the call.  All ranks of a node
     # share its host memory: the pinned buffers of all ranks are kept within 3/4 of it, and
     # when the whole batch does not fit the end-to-end step covers a prefix of the problems
@@ -775,6 +794,164 @@ def run_twosided(args):
     return 0
 
 
+def run_advection(args):
+    """Schemes 2 and 3 of Sec. 3 by the space-order sweep (ftoep_advection_sweep), double:
+    Example 2 (Scheme 2, u = t sin pi x) and Example 3 (Scheme 3, u = t^3 x(1-x)) on M nodes
+    and N levels; one step = one sweep of each, f resident in HBM."""
+    import torch
+    from paper_1710_11593_gb300 import ftoep, workloads as wl
+    rk = Ranks()
+    torch.cuda.set_device(rk.local)
+    ftoep.load()
+    # Scheme 3 as printed loses stability on finer grids (h = tau = 1/1024 at gamma 1.5: the
+    # oracle's own error grows to 2.4e-2), so the default stays at M = 512 nodes
+    M, N = args.M or 512, args.N or 16384
+    h = 1.0 / M
+    g2, g3 = 0.5, 1.5
+    xm = (np.arange(1, M + 1) - 0.5) * h
+    x = np.arange(1, M + 1) * h
+    t, th = wl.time_points(0, N), wl.time_points(1, N)
+    f2 = np.outer(np.sin(np.pi * xm), t ** (1 - g2) / math.gamma(2 - g2)) + np.outer(np.pi * np.cos(np.pi * xm), t)
+    f3 = np.outer(x - x * x, 6 * th ** (3 - g3) / math.gamma(4 - g3)) + np.outer(1 - 2 * x, th ** 3)
+    d2, d3 = torch.from_numpy(f2).cuda(), torch.from_numpy(f3).cuda()
+    u2, u3 = torch.empty_like(d2), torch.empty_like(d3)
+    for _ in range(args.warmup):
+        ftoep.advection_sweep(2, d2, g2, u=u2)
+        ftoep.advection_sweep(3, d3, g3, u=u3)
+    torch.cuda.synchronize()
+    rk.barrier()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record()
+    for _ in range(args.steps):
+        ftoep.advection_sweep(2, d2, g2, u=u2)
+    e1.record()
+    for _ in range(args.steps):
+        ftoep.advection_sweep(3, d3, g3, u=u3)
+    e2.record()
+    torch.cuda.synchronize()
+    ms2, ms3 = rk.max(e0.elapsed_time(e1) / args.steps), rk.max(e1.elapsed_time(e2) / args.steps)
+    err2 = float(np.sqrt(h * np.sum((u2[:-1, -1].cpu().numpy() - np.sin(np.pi * x[:-1])) ** 2)))
+    err3 = float(np.sqrt(h * np.sum((u3[:-1, -1].cpu().numpy() - (x - x * x)[:-1]) ** 2)))
+    cpu = None
+    if rk.rank == 0 and not args.no_cpu_baseline:
+        from oracle import oracle as orc
+        n0 = 512  # the oracle's direct method on the first n0 levels (O(M n0^2))
+        c0 = time.perf_counter()
+        ref = orc.advection_march(2, g2, f2[:, :n0], T=n0 / N)
+        dt = time.perf_counter() - c0
+        rel = float(np.max(np.abs(u2[:, :n0].cpu().numpy() - ref)) / np.max(np.abs(ref)))
+        cpu = {"value": M * n0 / dt, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+               "sample": f"direct method of Scheme 2 on the first {n0} levels, all {M} nodes ({dt:.2f} s)",
+               "gpu_rel_err_on_sample": rel}
+    if rk.rank == 0:
+        print(json.dumps({"metric": "advection sweep unknowns/s (Scheme 2, Example 2; Scheme 3 beside)",
+                          "value": rk.world * M * N / (ms2 * 1e-3), "unit": "unknowns/s", "n_gpus": rk.world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms2, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": f"advection_example2_g{g2}_M{M}_N{N}"},
+                          "l2_error_vs_exact": err2,
+                          "scheme3": {"workload": f"advection_example3_g{g3}_M{M}_N{N}", "ms_per_step": ms3,
+                                      "value": M * N / (ms3 * 1e-3), "l2_error_vs_exact": err3},
+                          "cpu_baseline": cpu}))
+    rk.close()
+    return 0
+
+
+def run_adjoint(args):
+    """Config 5 (gamma 0.6, M 1023, N 65536, double): one step = the forward solve and the
+    adjoint (dL/df and dL/dgamma) of L = ||u(., T) - u_obs||^2, f resident in HBM; the gradient
+    in gamma checked against central differences of the GPU forward solve."""
+    import torch
+    from paper_1710_11593_gb300 import ftoep, workloads as wl
+    rk = Ranks()
+    torch.cuda.set_device(rk.local)
+    ftoep.load()
+    M, N, g = args.M or 1023, args.N or 65536, 0.6
+    p = wl.config_adjoint(M=M, N=N, gamma=g)
+    f = wl.materialize_torch(p.source, p.kind, N, M, device="cuda")
+    spec = ftoep.ProblemSpec(p.kind, g, N, M, p.space, ftoep.FP64)
+    with ftoep.Plan([ftoep.ProblemSpec(p.kind, 0.55, N, M, p.space, ftoep.FP64)]) as p55:
+        u_obs = p55.solve(f)[:, -1].clone() + torch.from_numpy(wl.noise(M, 1e-3, seed=2)).cuda()
+    with ftoep.Plan([spec]) as plan:
+        u = plan.solve(f)
+        gg = torch.zeros_like(u)
+
+        def step():
+            plan.solve(f, u)
+            gg[:, -1] = 2.0 * (u[:, -1] - u_obs)
+            return plan.adjoint(gg, u)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            dldf, dg = step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = rk.max(e0.elapsed_time(e1) / args.steps)
+        dg = float(dg[0])
+    fd = None
+    hstep = 1e-6
+    vals = []
+    for gm in (g - hstep, g + hstep):
+        with ftoep.Plan([ftoep.ProblemSpec(p.kind, gm, N, M, p.space, ftoep.FP64)]) as pp:
+            uu = pp.solve(f)
+            vals.append(float(torch.sum((uu[:, -1] - u_obs) ** 2)))
+    fd = (vals[1] - vals[0]) / (2 * hstep)
+    if rk.rank == 0:
+        print(json.dumps({"metric": "forward + adjoint unknowns/s (config 5, double)",
+                          "value": rk.world * M * N / (ms * 1e-3), "unit": "unknowns/s", "n_gpus": rk.world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": f"adjoint_g{g}_M{M}_N{N}"},
+                          "dldgamma": dg, "dldgamma_central_difference": fd,
+                          "rel_diff_vs_central_difference": abs(dg - fd) / abs(fd)}))
+    rk.close()
+    return 0
+
+
+def run_gmres(args):
+    """Restarted GMRES(40) of Sec. 3.2 against the direct solve on the config-2 family (double,
+    sub-diffusion): one step = one GMRES solve to relative residual 1e-12 from zero."""
+    import torch
+    from paper_1710_11593_gb300 import ftoep, workloads as wl
+    rk = Ranks()
+    torch.cuda.set_device(rk.local)
+    ftoep.load()
+    p = wl.config_diffusion(M=args.M or 255, N=args.N or 16384)
+    f = wl.materialize_torch(p.source, p.kind, p.N, p.M, device="cuda")
+    with ftoep.Plan([ftoep.ProblemSpec(p.kind, p.gamma, p.N, p.M, p.space, ftoep.FP64)]) as plan:
+        ud = plan.solve(f)
+        for _ in range(args.warmup):
+            u, it, rr = plan.gmres(f, restart=40, tol=1e-12, maxit=100000)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            u, it, rr = plan.gmres(f, restart=40, tol=1e-12, maxit=100000)
+        torch.cuda.synchronize()
+        sec = rk.max((time.perf_counter() - t0) / args.steps)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            plan.solve(f, ud)
+        e1.record()
+        torch.cuda.synchronize()
+        direct_ms = e0.elapsed_time(e1) / args.steps
+    rel = float(torch.linalg.norm(u - ud) / torch.linalg.norm(ud))
+    if rk.rank == 0:
+        print(json.dumps({"metric": "GMRES(40) unknowns/s on the config-2 family (direct solve beside)",
+                          "value": rk.world * p.M * p.N / sec, "unit": "unknowns/s", "n_gpus": rk.world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": {"workload": f"gmres_diffusion_g{p.gamma}_M{p.M}_N{p.N}",
+                                                          "restart": 40, "tol": 1e-12},
+                          "iterations": it, "relres": rr, "rel_diff_vs_direct_solve": rel,
+                          "direct_solve_ms": direct_ms}))
+    rk.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -783,6 +960,12 @@ def main():
         return run_batched(args)
     if args.workload == "twosided":
         return run_twosided(args)
+    if args.workload == "advection":
+        return run_advection(args)
+    if args.workload == "gmres":
+        return run_gmres(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     return run_ours(args)
 
 

@@ -301,9 +301,12 @@ ftoep_status ftoep_gmres(ftoep_plan p, int iprob, const double* f, double* u, in
  *     upwind difference at level n, f at (x_i, t_{n-1/2}): A-tilde U_i = U_{i-1}/h + F_i
  *     (A-tilde = c W + I/h).
  * Grid: tau = T/N, h = L/M, nodes x_i = i h (i = 1..M), inflow value u(0, t) = 0 (a = 1).
- * Each node's system is solved by the library's solve of one scalar problem (lambda = 2/h,
- * resp. 1/h; precision FTOEP_FP64 or FTOEP_MIXED), the product B U_{i-1} by circulant
- * embedding; M sequential steps.  f, u: [M][N] doubles (row i-1 = node x_i), u0: length M or
+ * The node systems share one operator, so U_i = G U_{i-1} + V_i with G = A-tilde^-1 B and
+ * V_i = A-tilde^-1 F_i (lower-triangular Toeplitz matrices commute): V for all nodes by one
+ * batched solve of the scalar problem (lambda = 2/h, resp. 1/h; precision FTOEP_FP64 or
+ * FTOEP_MIXED), the first column of G by one more, and the recursion over i as a scan of
+ * ceil(log2 M) rounds U_i += G^d U_{i-d} (d = 1, 2, 4, ...), each a batched circulant-
+ * embedded product in double.  f, u: [M][N] doubles (row i-1 = node x_i), u0: length M or
  * NULL, phi: length M or NULL (scheme 3 only); host or device memory.  The initial-data
  * weights are those of Eq. 4 (the u0 weight G_{n-1}) and Eq. 17.  Creates and destroys an
  * internal plan; ordered on cuda_stream and blocks until done.  Errors: FTOEP_EINVAL (scheme

@@ -1977,15 +1977,20 @@ ftoep_status ftoep_gmres(ftoep_plan pl, int iprob, const double* f, double* u, i
   return FTOEP_OK;
 }
 
-// Advection sweeps of Sec. 3 (the fast procedure: space order, Figure 2): per node i = 1..M,
-// the lower-triangular Toeplitz system of one line, A-tilde U_i = B U_{i-1} + F_i, solved by
-// the library's own solve of one scalar problem with lambda = the diagonal shift:
-//   scheme 2: (c L1 + I/h) U_i = (I/h - c L1) U_{i-1} + F_i, c = mu/2 -- times 2, the scalar
-//             sub-diffusion problem (mu L1 + (2/h) I), with mu L1 U_{i-1} by the plan's
-//             circulant-embedded product;
-//   scheme 3: (c W + I/h) U_i = U_{i-1}/h + F_i -- the scalar hyperbolic problem, lambda = 1/h.
-// Initial data enter the right-hand side through the plan's initial-data weights (the
-// u-form rows, the solve itself with zero initial value).
+// Advection sweeps of Sec. 3 (the fast procedure: space order, Figure 2).  Node i = 1..M solves
+// the lower-triangular Toeplitz system of one line, A-tilde U_i = B U_{i-1} + F_i:
+//   scheme 2: (c L1 + I/h) U_i = (I/h - c L1) U_{i-1} + F_i, c = mu/2; times 2, the scalar
+//             sub-diffusion operator A = mu L1 + (2/h) I and B = (2/h) I - mu L1;
+//   scheme 3: (c W + I/h) U_i = U_{i-1}/h + F_i: A = c W + (1/h) I, B = (1/h) I.
+// Lower-triangular Toeplitz matrices commute, so U_i = G U_{i-1} + V_i with G = A^-1 B (lower-
+// triangular Toeplitz, first column g = A^-1 b, b = B e_1) and V_i = A^-1 F_i.  The recursion
+// over i is a linear scan: after the rounds d = 1, 2, 4, ... < M of U_i += G^d U_{i-d} (every
+// i >= d at once, from the previous round's values) U_i = sum_{k<=i} G^{i-k} V_k.  So the sweep
+// is one batched solve of all M lines (the library's scalar solve, lambda = 2/h resp. 1/h),
+// the solve of b, and ceil(log2 M) rounds of a batched circulant-embedded product (Sec. 3.1)
+// with the first column of G^d (squared from round to round), instead of M dependent solves.
+// Initial data enter the right-hand sides through the plan's initial-data weights (the u-form
+// rows; the solves themselves with zero initial value).
 ftoep_status ftoep_advection_sweep(int scheme, double gamma, double T, double L, int64_t N, int64_t M,
                                    const double* f, const double* u0, const double* phi, double* u, int precision,
                                    void* cuda_stream) {
@@ -2008,7 +2013,7 @@ ftoep_status ftoep_advection_sweep(int scheme, double gamma, double T, double L,
   d.L = 1.0;
   d.lambda = scheme == 2 ? 2.0 / h : 1.0 / h;
   d.N = N;
-  d.M = 1;
+  d.M = M;  // M independent lines of the scalar problem
   ftoep_plan pl = nullptr;
   TRY(ftoep_create(&pl, &d, 1, nullptr, cuda_stream));
   ftoep_status status = FTOEP_OK;
@@ -2018,41 +2023,80 @@ ftoep_status ftoep_advection_sweep(int scheme, double gamma, double T, double L,
     cudaStream_t st = w.st;
     const int64_t LN = M * N;
     const bool host = !is_device_ptr(f) || !is_device_ptr(u) || !is_device_ptr(u0) || !is_device_ptr(phi);
-    std::vector<double> hu0(u0 ? M : 0), hphi(phi ? M : 0);
-    double *fd = nullptr, *ud = nullptr, *g = nullptr, *t = nullptr;
     auto run = [&]() -> ftoep_status {
+      std::vector<double> hu0(u0 ? M : 0), hphi(phi ? M : 0), s0(M, 0.0), s1(M, 0.0);
       if (u0) CK(cudaMemcpy(hu0.data(), u0, M * sizeof(double), cudaMemcpyDefault));
       if (phi) CK(cudaMemcpy(hphi.data(), phi, M * sizeof(double), cudaMemcpyDefault));
+      for (int64_t i = 0; i < M; ++i) {
+        if (u0) s0[i] = scheme == 2 ? hu0[i] + (i > 0 ? hu0[i - 1] : 0.0) : hu0[i];
+        if (phi && scheme == 3) s1[i] = hphi[i];
+      }
       TRY(ensure_level_ws(pl, w));
-      if (scheme == 2) TRY(build_product_spectrum(pl, w, pb, pb.a, (void**)&pb.spec_mv, P64));
-      ALLOC(g, N * sizeof(double));
-      ALLOC(t, N * sizeof(double));
+      double *fd = nullptr, *rhs = nullptr, *V = nullptr, *U0 = nullptr, *U1 = nullptr, *Tm = nullptr;
+      double *gcol = nullptr, *s0d = nullptr, *s1d = nullptr;
+      double2* spec = nullptr;
+      ALLOC(rhs, LN * sizeof(double));
+      ALLOC(V, LN * sizeof(double));
+      ALLOC(U0, LN * sizeof(double));
+      ALLOC(U1, LN * sizeof(double));
+      ALLOC(Tm, LN * sizeof(double));
+      ALLOC(gcol, 2 * N * sizeof(double));
+      ALLOC(s0d, M * sizeof(double));
+      ALLOC(s1d, M * sizeof(double));
+      ALLOC(spec, 2 * pb.Np * sizeof(double2));
+      CK(cudaMemcpyAsync(s0d, s0.data(), M * sizeof(double), cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(s1d, s1.data(), M * sizeof(double), cudaMemcpyHostToDevice, st));
       const double* F = f;
-      double* U = u;
       if (host) {
         ALLOC(fd, LN * sizeof(double));
-        ALLOC(ud, LN * sizeof(double));
         CK(cudaMemcpyAsync(fd, f, LN * sizeof(double), cudaMemcpyDefault, st));
         F = fd;
-        U = ud;
       }
-      for (int64_t i = 0; i < M; ++i) {
-        const double* up = i > 0 ? U + (i - 1) * N : nullptr;
-        if (scheme == 2) {
-          // g = 2 [ (1/h) U_{i-1} - (mu/2) L1 U_{i-1} + F_i ] + mu G_{n-1} (u0_i + u0_{i-1})
-          if (up) TRY(product_lines(pl, w, pb, P64, pb.spec_mv, up, t, 1, 0));
-          const double s0 = u0 ? hu0[i] + (i > 0 ? hu0[i - 1] : 0.0) : 0.0;
-          LAUNCH(FTOEP_K_OTHER, launch_sweep_rhs(g, up, up ? t : nullptr, F + i * N, u0 ? pb.wu0 : nullptr, nullptr, N,
-                                                 2.0 / h, -1.0, 2.0, s0, 0.0, st));
-        } else {
-          // g = U_{i-1}/h + F_i + (u0 and phi weights of Eq. 17)
-          LAUNCH(FTOEP_K_OTHER, launch_sweep_rhs(g, up, nullptr, F + i * N, u0 ? pb.wu0 : nullptr,
-                                                 phi ? pb.wphi : nullptr, N, 1.0 / h, 0.0, 1.0, u0 ? hu0[i] : 0.0,
-                                                 phi ? hphi[i] : 0.0, st));
+      // V = A^-1 (c F + initial-data terms), all nodes at once
+      LAUNCH(FTOEP_K_OTHER, launch_sweep_rhs_lines(rhs, F, u0 ? pb.wu0 : nullptr, s0d,
+                                                    (phi && scheme == 3) ? pb.wphi : nullptr, s1d, M, N,
+                                                    scheme == 2 ? 2.0 : 1.0, st));
+      TRY(solve_problem(pl, w, pb, rhs, V, nullptr, nullptr));
+      if (M > 1) {
+        // first column of G: A^-1 b on line 0 (the other lines zero)
+        std::vector<double> b(N, 0.0);
+        b[0] = scheme == 2 ? 2.0 / h : 1.0 / h;
+        if (scheme == 2)
+          for (int64_t n = 0; n < N; ++n) b[n] -= pb.h_a[n];
+        CK(cudaMemsetAsync(rhs, 0, LN * sizeof(double), st));
+        CK(cudaMemcpyAsync(rhs, b.data(), N * sizeof(double), cudaMemcpyHostToDevice, st));
+        TRY(solve_problem(pl, w, pb, rhs, Tm, nullptr, nullptr));
+        CK(cudaMemcpyAsync(gcol, Tm, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CK(cudaStreamSynchronize(st));  // b is host memory of this scope
+      }
+      // scan over the nodes: U_i += G^d U_{i-d}, d = 1, 2, 4, ...
+      double* cur = V;
+      double* nxt = U0;
+      double* spare = U1;
+      double* gd = gcol;
+      double* gn = gcol + N;
+      for (int64_t dd = 1; dd < M; dd *= 2) {
+        SpecArgs sa{};
+        sa.a = gd;
+        sa.lo = 0;
+        sa.hi = N;
+        sa.logn = pb.logNp + 1;
+        sa.nsmem = nsmem_for(P64);
+        sa.out = spec;
+        sa.tw64 = pl->tw64;
+        sa.scratch64 = w.scratch_mv;
+        LAUNCH(FTOEP_K_OTHER, launch_spectrum(P64, sa, st));
+        TRY(product_lines(pl, w, pb, P64, spec, cur, Tm, M - dd, 0));
+        LAUNCH(FTOEP_K_OTHER, launch_shift_add_lines(nxt, cur, Tm, M, N, dd, st));
+        if (2 * dd < M) {  // G^(2d) = G^d G^d
+          TRY(product_lines(pl, w, pb, P64, spec, gd, gn, 1, 0));
+          std::swap(gd, gn);
         }
-        TRY(solve_problem(pl, w, pb, g, U + i * N, nullptr, nullptr));
+        double* old = cur;
+        cur = nxt;
+        nxt = old == V ? spare : old;
       }
-      if (host) CK(cudaMemcpyAsync(u, ud, LN * sizeof(double), cudaMemcpyDefault, st));
+      CK(cudaMemcpyAsync(u, cur, LN * sizeof(double), cudaMemcpyDefault, st));
       CK(cudaStreamSynchronize(st));
       return FTOEP_OK;
     };

@@ -1,5 +1,5 @@
 // Vector kernels of the restarted GMRES method of Sec. 3.2 and of the advection sweeps of Sec. 3
-// (the right-hand side of one spatial step).
+// (the right-hand sides of all nodes, one round of the scan over the nodes).
 //
 // GMRES: the method of Sec. 3.2 (Saad and Schultz, as the paper
 // states it) on the space-time systems of the reordered schemes (Eq. 21: block rows A-hat on
@@ -75,19 +75,29 @@ __global__ void lincomb_kernel(double* y, double a, const double* x, double b, c
     y[e] = a * x[e] + (b != 0.0 ? b * z[e] : 0.0);
 }
 
-// Right-hand side of one step of the advection sweeps: g = a up + b t + c F + s0 w0 + s1 w1
-// (up, t may be NULL = 0; w0, w1 may be NULL).
-__global__ void sweep_rhs_kernel(double* __restrict__ g, const double* __restrict__ up, const double* __restrict__ t,
-                                 const double* __restrict__ F, const double* __restrict__ w0,
-                                 const double* __restrict__ w1, int64_t N, double a, double b, double c, double s0,
-                                 double s1) {
-  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
-    double v = c * F[n];
-    if (up) v = fma(a, up[n], v);
-    if (t) v = fma(b, t[n], v);
-    if (w0) v = fma(s0, w0[n], v);
-    if (w1) v = fma(s1, w1[n], v);
-    g[n] = v;
+// Right-hand sides of all nodes of an advection sweep: g[i][n] = c F[i][n] + s0[i] w0[n] +
+// s1[i] w1[n] (w0/s0, w1/s1 nullable).
+__global__ void sweep_rhs_lines_kernel(double* __restrict__ g, const double* __restrict__ F,
+                                       const double* __restrict__ w0, const double* __restrict__ s0,
+                                       const double* __restrict__ w1, const double* __restrict__ s1, int64_t M,
+                                       int64_t N, double c) {
+  const int64_t total = M * N;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / N, n = e % N;
+    double v = c * F[e];
+    if (w0) v = fma(s0[i], w0[n], v);
+    if (w1) v = fma(s1[i], w1[n], v);
+    g[e] = v;
+  }
+}
+
+// One round of the space scan: out[i] = in[i] + t[i - d] for i >= d, out[i] = in[i] below.
+__global__ void shift_add_lines_kernel(double* __restrict__ out, const double* __restrict__ in,
+                                       const double* __restrict__ t, int64_t M, int64_t N, int64_t d) {
+  const int64_t total = M * N;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / N;
+    out[e] = i >= d ? in[e] + t[e - d * N] : in[e];
   }
 }
 
@@ -115,9 +125,15 @@ int launch_maxpy(double* w, const double* V, int64_t ldv, int k, const double* c
   return 1;
 }
 
-int launch_sweep_rhs(double* g, const double* up, const double* t, const double* F, const double* w0, const double* w1,
-                     int64_t N, double a, double b, double c, double s0, double s1, cudaStream_t st) {
-  sweep_rhs_kernel<<<grid_for(N), kThreads, 0, st>>>(g, up, t, F, w0, w1, N, a, b, c, s0, s1);
+int launch_sweep_rhs_lines(double* g, const double* F, const double* w0, const double* s0, const double* w1,
+                           const double* s1, int64_t M, int64_t N, double c, cudaStream_t st) {
+  sweep_rhs_lines_kernel<<<grid_for(M * N), kThreads, 0, st>>>(g, F, w0, s0, w1, s1, M, N, c);
+  return 1;
+}
+
+int launch_shift_add_lines(double* out, const double* in, const double* t, int64_t M, int64_t N, int64_t d,
+                           cudaStream_t st) {
+  shift_add_lines_kernel<<<grid_for(M * N), kThreads, 0, st>>>(out, in, t, M, N, d);
   return 1;
 }
 

@@ -211,10 +211,12 @@ int launch_mdot(const double* V, int64_t ldv, int k, const double* w, int64_t L,
                 cudaStream_t st);
 // w += sum_{i<k} c_i V_i (c: k doubles in device memory, k <= kMaxBasis)
 int launch_maxpy(double* w, const double* V, int64_t ldv, int k, const double* c, int64_t L, cudaStream_t st);
-// advection sweep step: g = a up + b t + c F + s0 w0 + s1 w1 over N entries (up, t, w0, w1
-// nullable = 0)
-int launch_sweep_rhs(double* g, const double* up, const double* t, const double* F, const double* w0, const double* w1,
-                     int64_t N, double a, double b, double c, double s0, double s1, cudaStream_t st);
+// all nodes of a sweep: g[i][n] = c F[i][n] + s0[i] w0[n] + s1[i] w1[n] (w0/s0, w1/s1 nullable)
+int launch_sweep_rhs_lines(double* g, const double* F, const double* w0, const double* s0, const double* w1,
+                           const double* s1, int64_t M, int64_t N, double c, cudaStream_t st);
+// out[i] = in[i] + t[i - d] (i >= d), in[i] below; lines of N doubles
+int launch_shift_add_lines(double* out, const double* in, const double* t, int64_t M, int64_t N, int64_t d,
+                           cudaStream_t st);
 // y = a x + b z (z unread when b = 0)
 int launch_lincomb(double* y, double a, const double* x, double b, const double* z, int64_t L, cudaStream_t st);
 
