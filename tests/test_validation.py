@@ -132,3 +132,18 @@ def test_gmres_validates_its_arguments():
     u = np.zeros(8)
     lib = ftoep.load()
     assert lib.ftoep_gmres(None, 0, f.ctypes.data, u.ctypes.data, 10, 1e-10, 10, None, None) == ftoep.FTOEP_EINVAL
+
+
+def test_shipped_tuning_table_is_valid():
+    """The autotuner's table shipped with the package: every entry is a valid tuning for
+    ftoep_create and is keyed like tuning_key (device | buckets)."""
+    import json
+    from paper_1710_11593_gb300 import ftoep
+    with open(ftoep.SHIPPED_TUNING) as fh:
+        table = json.load(fh)
+    assert table
+    for key, entry in table.items():
+        assert "|" in key and key.split("|")[0]
+        t = {k: int(entry.get(k, 0)) for k in ftoep.TUNING_FIELDS}
+        assert t["fft_tile"] in (0, 1024, 2048, 4096) and t["scheduler"] in (0, 1, 2)
+        assert 0 <= t["streams"] <= 8 and t["solver"] in (0, 1)
