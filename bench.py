@@ -55,9 +55,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) leg (profiling runs)")
     ap.add_argument("--no-tune", action="store_true", help="batched: library default tuning instead of the autotuner's")
     ap.add_argument("--scheduler", type=int, default=0, choices=[0, 1, 2],
-                    help="single workloads: 0 library choice, 1 per-level launches, 2 persistent chain")
+                    help="0 library (or tuned) choice, 1 per-level launches, 2 persistent chain")
     ap.add_argument("--solver", type=int, default=0, choices=[0, 1, 2],
-                    help="single workloads: 0 library choice, 1 half-split, 2 inverse series")
+                    help="0 library (or tuned) choice, 1 half-split, 2 inverse series")
     ap.add_argument("--M", type=int, default=None, help="override the workload's interior points (profiling cases)")
     ap.add_argument("--N", type=int, default=None, help="override the workload's time steps (profiling cases)")
     return ap.parse_args()
@@ -529,6 +529,9 @@ def run_batched(args):
     # the autotuner's choice for this batch: the user's cache or the table shipped with the
     # package (written by paper_1710_11593_gb300/tune_table.py on a GB300), else a search
     tuning, cached = (None, None) if args.no_tune else ftoep.autotune_cached(specs)
+    if args.scheduler or args.solver:  # explicit choices over the tuned ones
+        tuning = dict(tuning or {})
+        tuning.update({k: v for k, v in (("scheduler", args.scheduler), ("solver", args.solver)) if v})
     plan = ftoep.Plan(specs, tuning=tuning)
     ms, launches, clk = timed(plan, f, u, args.steps, args.warmup, rk, local)
     prof = class_profile(plan, f, u)

@@ -742,21 +742,11 @@ ftoep_status join_streams(ftoep_plan pl) {
   return FTOEP_OK;
 }
 
-// Forward transform, in the bit-reversed order of the device decimation-in-frequency FFT
-// and divided by P, of b_m = conj(c_|m|) (|m| < L) wrapped to length P.  Host long double.
-std::vector<std::complex<long double>> chirp_kernel_spectrum(const std::vector<long double>& cr,
-                                                             const std::vector<long double>& ci, int64_t P) {
-  const int64_t L = (int64_t)cr.size();
+// Forward transform of (br, bi) (length P, a power of two), in the bit-reversed order of the
+// device decimation-in-frequency FFT and divided by P.  Host long double.
+std::vector<std::complex<long double>> dif_spectrum(std::vector<long double> br, std::vector<long double> bi) {
+  const int64_t P = (int64_t)br.size();
   const long double pi = 3.141592653589793238462643383279502884L;
-  std::vector<long double> br(P, 0.0L), bi(P, 0.0L);
-  for (int64_t m = 0; m < L; ++m) {
-    br[m] = cr[m];
-    bi[m] = -ci[m];
-    if (m > 0) {
-      br[P - m] = cr[m];
-      bi[P - m] = -ci[m];
-    }
-  }
   // radix-2 decimation in frequency, natural in, bit-reversed out (same permutation as fft_dif)
   for (int64_t len = P; len >= 2; len >>= 1) {
     const int64_t half = len / 2;
@@ -779,6 +769,22 @@ std::vector<std::complex<long double>> chirp_kernel_spectrum(const std::vector<l
   return out;
 }
 
+// dif_spectrum of b_m = conj(c_|m|) (|m| < L) wrapped to length P.
+std::vector<std::complex<long double>> chirp_kernel_spectrum(const std::vector<long double>& cr,
+                                                             const std::vector<long double>& ci, int64_t P) {
+  const int64_t L = (int64_t)cr.size();
+  std::vector<long double> br(P, 0.0L), bi(P, 0.0L);
+  for (int64_t m = 0; m < L; ++m) {
+    br[m] = cr[m];
+    bi[m] = -ci[m];
+    if (m > 0) {
+      br[P - m] = cr[m];
+      bi[P - m] = -ci[m];
+    }
+  }
+  return dif_spectrum(std::move(br), std::move(bi));
+}
+
 // Chirp c_n = exp(-i pi n^2 / L), n < L, with n^2 reduced mod 2L exactly.  Host long double.
 void chirp_of(int64_t L, std::vector<long double>& cr, std::vector<long double>& ci) {
   const long double pi = 3.141592653589793238462643383279502884L;
@@ -795,7 +801,13 @@ void chirp_of(int64_t L, std::vector<long double>& cr, std::vector<long double>&
 // Tables of the sine transform of a problem with K = M+1 not a power of two:
 //   double (folded half-length form, a DFT of length L = K): chirp, kernel spectrum of length
 //     P >= 2K - 1, fold factors sin(pi j/K), j <= K/2;
-//   float (odd extension, a DFT of length L = 2K): chirp, kernel spectrum of length P >= 4K - 1.
+//   float (the odd extension, a DFT of length L = 2K, at k = 1 .. K-1 as a convolution minus a
+//     correlation of length P >= 2K - 3): chirp, the two kernel spectra G1, G2 interleaved.
+//     With w_p = x_{p+1} c_{p+1} (p = 0 .. K-2) the sum over the odd extension is
+//       sum_p w_p conj(c_{k-1-p}) - sum_p w_p conj(c_{k+1+p}) = (w * g1)_k - (w~ * g2)_k,
+//     g1_m = conj(c_{m-1}), m in [-K+3, K-1];  g2_m = conj(c_{m+1}), m in [1, 2K-3];
+//     w~_q = w_{-q}, whose transform is W at -k.  Each range holds 2K - 3 values, so P >= 2K - 3
+//     keeps the outputs k = 1 .. K-1 free of wrap-around.
 ftoep_status build_bluestein(ftoep_plan pl, Prob& pb) {
   const int64_t K = pb.M + 1;
   const long double pi = 3.141592653589793238462643383279502884L;
@@ -819,19 +831,32 @@ ftoep_status build_bluestein(ftoep_plan pl, Prob& pb) {
     CK(cudaMemcpy(pb.bspec64, b64.data(), P * sizeof(double2), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(pb.sinv64, s64.data(), (Q + 1) * sizeof(double), cudaMemcpyHostToDevice));
   }
-  {  // float, odd extension
+  {  // float, odd extension by a convolution and a correlation
     const int64_t L = 2 * K;
-    pb.logP32 = ilog2(2 * L - 1);
+    pb.logP32 = std::max(4, ilog2(2 * K - 3));
     const int64_t P = int64_t(1) << pb.logP32;
     chirp_of(L, cr, ci);
-    const auto bs = chirp_kernel_spectrum(cr, ci, P);
-    std::vector<float2> c32(L), b32(P);
+    std::vector<long double> g1r(P, 0.0L), g1i(P, 0.0L), g2r(P, 0.0L), g2i(P, 0.0L);
+    for (int64_t m = 3 - K; m <= K - 1; ++m) {
+      const int64_t c = m >= 1 ? m - 1 : 1 - m, pos = m >= 0 ? m : P + m;
+      g1r[pos] = cr[c];
+      g1i[pos] = -ci[c];
+    }
+    for (int64_t m = 1; m <= 2 * K - 3; ++m) {
+      g2r[m % P] = cr[m + 1];
+      g2i[m % P] = -ci[m + 1];
+    }
+    const auto s1 = dif_spectrum(std::move(g1r), std::move(g1i));
+    const auto s2 = dif_spectrum(std::move(g2r), std::move(g2i));
+    std::vector<float2> c32(L);
+    std::vector<float4> g32(P);
     for (int64_t n = 0; n < L; ++n) c32[n] = make_float2((float)cr[n], (float)ci[n]);
-    for (int64_t k = 0; k < P; ++k) b32[k] = make_float2((float)bs[k].real(), (float)bs[k].imag());
+    for (int64_t k = 0; k < P; ++k)
+      g32[k] = make_float4((float)s1[k].real(), (float)s1[k].imag(), (float)s2[k].real(), (float)s2[k].imag());
     ALLOC(pb.chirp32, L * sizeof(float2));
-    ALLOC(pb.bspec32, P * sizeof(float2));
+    ALLOC(pb.bspec32, P * sizeof(float4));
     CK(cudaMemcpy(pb.chirp32, c32.data(), L * sizeof(float2), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(pb.bspec32, b32.data(), P * sizeof(float2), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(pb.bspec32, g32.data(), P * sizeof(float4), cudaMemcpyHostToDevice));
   }
   pb.bluestein = true;
   return FTOEP_OK;

@@ -566,31 +566,41 @@ __global__ void __launch_bounds__(kDstThreads) dst_bluestein_fold_kernel(DstArgs
   }
 }
 
-// Sine transform for any K = M+1 in float: the odd extension of length 2K by Bluestein.  With W = exp(-2 pi i / L),
-// L = 2K, and c_n = W^{n^2/2}: DFT(y)_k = c_k sum_n (y_n c_n) conj(c_{k-n}), a linear
-// convolution that a cyclic one of length P >= 2L-1 reproduces exactly.  One block
-// handles C time columns (C/2 complex column pairs, one P-buffer each); the product with
-// the chirp's spectrum runs fused between the forward and inverse FFT, and the DFT comes
-// out in natural order.
+// Sine transform for any K = M+1 in float: the DFT of the odd extension (length L = 2K) by
+// Bluestein, at the outputs k = 1 .. K-1 only.  With c_n = exp(-i pi n^2 / L) (period L,
+// c_{-n} = c_n) and the odd extension y_{-n} = -y_n,
+//     DFT(y)_k = c_k [ sum_{n=1}^{K-1} y_n c_n conj(c_{k-n}) - sum_{n=1}^{K-1} y_n c_n conj(c_{k+n}) ],
+// a convolution minus a correlation of w_p = y_{p+1} c_{p+1} (p = 0 .. K-2).  Both run as cyclic
+// convolutions of length P >= 2K - 3 (the plan's tables G1, G2 hold the two kernel spectra;
+// the correlation is a convolution with w~_q = w_{-q}, whose transform is W_{-k}):
+//     Z_k = W_k G1_k - W_{-k} G2_k,
+// one forward FFT, a product that visits each frequency with its partner -k, one inverse
+// FFT.  Against one convolution over the whole extension (P >= 4K - 1) the transforms are
+// half as long.  Two real columns share one complex sequence (y = a + i b, so that
+// DFT(y) = -2i S_a + 2 S_b).  One block handles C time columns (C/2 column pairs, one
+// P-buffer each).
 template <typename T>
-__global__ void __launch_bounds__(kDstThreads) dst_bluestein_odd_kernel(DstArgs A, int C, int fwd) {
+__global__ void __launch_bounds__(kDstThreads) dst_bluestein_split_kernel(DstArgs A, int C, int fwd) {
   typedef Vt<T> V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const int64_t col0 = (int64_t)blockIdx.x * C;
   const int64_t M = A.M;
-  const int K = A.K, Lq = 2 * K;
+  const int K = A.K;
   const int logP = A.logP, P = 1 << logP, H = P >> 1;
   const int CP = C >> 1, lcp = 31 - __clz(CP);
   const SmLayout Ls = sm_layout<V>(logP);
   const V* __restrict__ chirp = (const V*)A.chirp;
+  const float4* __restrict__ g12 = (const float4*)A.bspec;
   const V* __restrict__ tw = (const V*)A.tw;
-  // zero [0, P/2) of every buffer; the upper half is never read (half-zero input) unless
-  // the whole transform is a single pass
+  // zero [K-1, P/2) of every buffer (the inputs fill [0, K-1), K - 2 < P/2); the upper half
+  // is never read by the half-zero first pass unless the transform is a single pass
   const int np = fftr_npasses<V>(logP);
-  const int Z = np < 2 ? P : H;
-  for (int e = threadIdx.x; e < CP * Z; e += blockDim.x) sm[sm_pos<V>(Ls, e / Z, e % Z)] = vzero<V>();
-  __syncthreads();
+  const int lz = np < 2 ? logP : logP - 1;
+  for (int e = threadIdx.x; e < (CP << lz); e += blockDim.x) {
+    const int i = e & ((1 << lz) - 1);
+    if (i >= K - 1) sm[sm_pos<V>(Ls, e >> lz, i)] = vzero<V>();
+  }
   if (fwd) {
     const int tot = (int)M << lcp;
     for (int e0 = threadIdx.x; e0 < tot; e0 += 4 * (int)blockDim.x) {
@@ -609,9 +619,7 @@ __global__ void __launch_bounds__(kDstThreads) dst_bluestein_odd_kernel(DstArgs 
         const int e = e0 + q * (int)blockDim.x;
         if (e < tot) {
           const int j = (e >> lcp), t = (e & (CP - 1));
-          const V v = mkv(va[q], vb[q]);
-          sm[sm_pos<V>(Ls, t, j + 1)] = cmul(v, chirp[j + 1]);
-          sm[sm_pos<V>(Ls, t, Lq - j - 1)] = cmul(vneg(v), chirp[Lq - j - 1]);
+          sm[sm_pos<V>(Ls, t, j)] = cmul(mkv(va[q], vb[q]), chirp[j + 1]);
         }
       }
     }
@@ -635,23 +643,35 @@ __global__ void __launch_bounds__(kDstThreads) dst_bluestein_odd_kernel(DstArgs 
         if (e < tot) {
           const int a = (e >> lcp) + 1, t = (e & (CP - 1));
           const int b = K - a;
-          const V va = mkv(c0[q].x, c1[q].x);
-          sm[sm_pos<V>(Ls, t, a)] = cmul(va, chirp[a]);
-          sm[sm_pos<V>(Ls, t, Lq - a)] = cmul(vneg(va), chirp[Lq - a]);
-          if (b != a) {
-            const V vb = mkv(c0[q].y, c1[q].y);
-            sm[sm_pos<V>(Ls, t, b)] = cmul(vb, chirp[b]);
-            sm[sm_pos<V>(Ls, t, Lq - b)] = cmul(vneg(vb), chirp[Lq - b]);
-          }
+          sm[sm_pos<V>(Ls, t, a - 1)] = cmul(mkv(c0[q].x, c1[q].x), chirp[a]);
+          if (b != a) sm[sm_pos<V>(Ls, t, b - 1)] = cmul(mkv(c0[q].y, c1[q].y), chirp[b]);
         }
       }
     }
   }
   __syncthreads();
-  fftr_passes<V, true>(sm, logP, CP, tw, 0, np - 1, true);
-  fftr_middle<V>(sm, logP, CP, SpecMul<V>{(const V*)A.bspec});
+  fftr_passes<V, true>(sm, logP, CP, tw, 0, np, true);
+  // Z_k = W_k G1_k - W_{-k} G2_k, each frequency with its partner: item k < P/2 of transform
+  // t handles k and P - k (k = 0: the two self-partner frequencies 0 and P/2)
+  const int lh = logP - 1;
+  for (int e = threadIdx.x; e < (CP << lh); e += blockDim.x) {
+    const int t = e >> lh, k = e & (H - 1);
+    const int pos = (int)(__brev((unsigned)k) >> (32 - logP));
+    const int pk = k == 0 ? H : P - k;
+    const int pp = (int)(__brev((unsigned)pk) >> (32 - logP));
+    const int q1 = sm_pos<V>(Ls, t, pos), q2 = sm_pos<V>(Ls, t, pp);
+    const float4 ga = g12[pos], gb = g12[pp];
+    const V w1 = sm[q1], w2 = sm[q2];
+    if (k == 0) {
+      sm[q1] = cmul(w1, mkv((T)(ga.x - ga.z), (T)(ga.y - ga.w)));
+      sm[q2] = cmul(w2, mkv((T)(gb.x - gb.z), (T)(gb.y - gb.w)));
+    } else {
+      sm[q1] = csub(cmul(w1, mkv((T)ga.x, (T)ga.y)), cmul(w2, mkv((T)ga.z, (T)ga.w)));
+      sm[q2] = csub(cmul(w2, mkv((T)gb.x, (T)gb.y)), cmul(w1, mkv((T)gb.z, (T)gb.w)));
+    }
+  }
   __syncthreads();
-  fftr_passes<V, false>(sm, logP, CP, tw, 1, np, false);
+  fftr_passes<V, false>(sm, logP, CP, tw, 0, np, false);
   const T scale = (T)A.dst_scale;
   if (fwd) {
     V* z = (V*)A.z;
@@ -706,17 +726,18 @@ int dst_pairs_per_block(int logK2) {
 template <typename T>
 void dst_launch(const DstArgs& a, bool fwd, cudaStream_t st) {
   if (a.space && a.bluestein) {
-    // double: the folded half-length form; float: the odd extension (the folded form's odd
-    // coefficients are prefix sums of FFT outputs, whose rounding accumulates like a random
-    // walk across them -- harmless in double, too large against the float solve's correction)
+    // double: the folded half-length form; float: the odd extension as a convolution minus a
+    // correlation (the folded form's odd coefficients are prefix sums of FFT outputs, whose
+    // rounding accumulates like a random walk across them -- harmless in double, too large
+    // against the float solve's correction)
     const int C = dst_cols<T>(a.logP);
     const size_t smem = (size_t)(C / 2) * ((size_t)1 << a.logP) * sizeof(Vt<T>);
     const void* fn = std::is_same<T, double>::value ? (const void*)dst_bluestein_fold_kernel<T>
-                                                    : (const void*)dst_bluestein_odd_kernel<T>;
+                                                    : (const void*)dst_bluestein_split_kernel<T>;
     set_smem(fn, smem);
     const unsigned grid = (unsigned)((a.ncols + C - 1) / C);
     if (std::is_same<T, double>::value) dst_bluestein_fold_kernel<T><<<grid, kDstThreads, smem, st>>>(a, C, fwd ? 1 : 0);
-    else dst_bluestein_odd_kernel<T><<<grid, kDstThreads, smem, st>>>(a, C, fwd ? 1 : 0);
+    else dst_bluestein_split_kernel<T><<<grid, kDstThreads, smem, st>>>(a, C, fwd ? 1 : 0);
     return;
   }
   if (!a.space) {

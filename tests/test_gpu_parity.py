@@ -78,6 +78,12 @@ def test_fp64_random_rhs(ft, oracle, kind, gamma, M, N, tune):
     (0, 0.4, 2, 300, 0),      # M+1 = 3, smallest odd size
     (0, 0.8, 200, 1200, 1),   # mixed, M+1 = 201
     (1, 1.8, 2046, 150, 1),   # mixed, M+1 = 2047 = 23*89, P = 8192
+    # float chirp-z, a convolution minus a correlation of length P >= 2K - 3 (K = M+1)
+    (0, 0.6, 40, 900, 1),     # mixed, K = 41: P = 128
+    (1, 1.3, 682, 300, 1),    # mixed, K = 683: P = 2048
+    (0, 0.5, 1024, 200, 1),   # mixed, K = 1025: 2K - 3 = P - 1, the input fills [0, P/2)
+    (1, 1.4, 1025, 150, 1),   # mixed, K = 1026: P = 4096
+    (0, 0.9, 2, 60, 1),       # mixed, K = 3: the shortest transform, P = 16
 ])
 def test_sine_transform_any_size(ft, oracle, kind, gamma, M, N, prec):
     f = wl.random_field((M, N), seed=M + 7 * N)
@@ -198,6 +204,7 @@ def test_degenerate_sizes(ft, oracle, kind, gamma, M, N, prec):
     (0, 0.6, 4094, 30, 1),  # largest chirp-z M+1 = 4095, mixed
     (1, 1.6, 2046, 30, 0),  # chirp-z M+1 = 2047, double
     (0, 0.45, 4094, 24, 0),  # largest chirp-z M+1 = 4095, double (folded form): P = 8192
+    (1, 1.2, 2048, 30, 1),  # mixed chirp-z K = 2049: 2K - 3 = P - 1 at P = 4096
 ])
 def test_largest_sine_transforms(ft, oracle, kind, gamma, M, N, prec):
     f = wl.random_field((M, N), seed=M + N)
