@@ -501,4 +501,72 @@ __device__ __forceinline__ void fftr_middle(V* a, int logn, int cnt, Op op) {
   }
 }
 
+// Storage-order partner inside group 0 of the last pass: the frequency at position j of the
+// group is brev_r(j) * n/R, its partner n - that (mod n).
+__host__ __device__ constexpr int brev_c(int x, int bits) { return bits == 0 ? 0 : ((x & 1) << (bits - 1)) | brev_c(x >> 1, bits - 1); }
+__host__ __device__ constexpr int group0_partner(int j, int r) { return brev_c(((1 << r) - brev_c(j, r)) & ((1 << r) - 1), r); }
+
+// As fftr_middle, for a pointwise operation that pairs each frequency k with its partner
+// n - k.  Group g of the last pass (storage positions g R .. g R + R - 1, frequencies
+// brev(position)) pairs with group g ^ (2^h - 1), h its highest set bit, element j with
+// element R-1-j; groups 0 and 1 pair with themselves (group 0 by group0_partner, group 1
+// j with R-1-j).  Item u of a transform takes groups 0 and 1 (u = 0) or the pair with
+// g = u + 2^floor(log2 u), so consecutive threads read consecutive groups.
+// pair(t, pa, pb, wa, wb) gets the values at storage positions pa and pb (partners) and
+// replaces both; self(t, p, w) a self-partner frequency (0 or n/2).  No barrier.
+template <typename V, int r, class Pair, class Self>
+__device__ __forceinline__ void middle_partner_r(V* a, int logn, int cnt, Pair pair, Self self) {
+  constexpr int R = 1 << r;
+  const SmLayout L = sm_layout<V>(logn);
+  const int lu = logn - r;  // >= 1
+  const int lh = lu - 1;
+  for (int w = threadIdx.x; w < (cnt << lh); w += blockDim.x) {
+    const int t = w >> lh, u = w & ((1 << lh) - 1);
+    int g = 0, gp = 1;
+    if (u > 0) {
+      const int hb1 = 31 - __clz(u);
+      g = u + (1 << hb1);
+      gp = g ^ ((2 << hb1) - 1);
+    }
+    V xa[R], xb[R];
+    static_for<0, R>([&](auto JJ) {
+      constexpr int j = decltype(JJ)::value;
+      xa[j] = a[sm_pos<V>(L, t, (g << r) + j)];
+      xb[j] = a[sm_pos<V>(L, t, (gp << r) + j)];
+    });
+    dif_regs<V, r, false, false>(xa, nullptr, r, 0);
+    dif_regs<V, r, false, false>(xb, nullptr, r, 0);
+    if (u == 0) {
+      static_for<0, R>([&](auto JJ) {
+        constexpr int j = decltype(JJ)::value;
+        constexpr int jp = group0_partner(j, r);
+        if constexpr (jp == j) self(t, j, xa[j]);
+        else if constexpr (j < jp) pair(t, j, jp, xa[j], xa[jp]);
+      });
+      static_for<0, R / 2>([&](auto JJ) {
+        constexpr int j = decltype(JJ)::value;
+        pair(t, R + j, 2 * R - 1 - j, xb[j], xb[R - 1 - j]);
+      });
+    } else {
+      static_for<0, R>([&](auto JJ) {
+        constexpr int j = decltype(JJ)::value;
+        pair(t, (g << r) + j, (gp << r) + R - 1 - j, xa[j], xb[R - 1 - j]);
+      });
+    }
+    dit_regs<V, r, false>(xa, nullptr, r, 0);
+    dit_regs<V, r, false>(xb, nullptr, r, 0);
+    static_for<0, R>([&](auto JJ) {
+      constexpr int j = decltype(JJ)::value;
+      a[sm_pos<V>(L, t, (g << r) + j)] = xa[j];
+      a[sm_pos<V>(L, t, (gp << r) + j)] = xb[j];
+    });
+  }
+}
+
+// Runs DIF pass np-1 + the partner-paired operation + DIT pass 0 (np >= 2).
+template <typename V, class Pair, class Self>
+__device__ __forceinline__ void fftr_middle_partner(V* a, int logn, int cnt, Pair pair, Self self) {
+  middle_partner_r<V, EngineTraits<V>::RB>(a, logn, cnt, pair, self);  // the last pass has radix RB
+}
+
 }  // namespace ftoep

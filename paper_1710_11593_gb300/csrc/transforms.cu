@@ -574,11 +574,11 @@ __global__ void __launch_bounds__(kDstThreads) dst_bluestein_fold_kernel(DstArgs
 // convolutions of length P >= 2K - 3 (the plan's tables G1, G2 hold the two kernel spectra;
 // the correlation is a convolution with w~_q = w_{-q}, whose transform is W_{-k}):
 //     Z_k = W_k G1_k - W_{-k} G2_k,
-// one forward FFT, a product that visits each frequency with its partner -k, one inverse
-// FFT.  Against one convolution over the whole extension (P >= 4K - 1) the transforms are
-// half as long.  Two real columns share one complex sequence (y = a + i b, so that
-// DFT(y) = -2i S_a + 2 S_b).  One block handles C time columns (C/2 column pairs, one
-// P-buffer each).
+// one forward FFT, a product that visits each frequency with its partner -k (fused in
+// registers with the last forward and the first inverse pass), one inverse FFT.  Against
+// one convolution over the whole extension (P >= 4K - 1) the transforms are half as long.
+// Two real columns share one complex sequence (y = a + i b, so that DFT(y) = -2i S_a +
+// 2 S_b).  One block handles C time columns (C/2 column pairs, one P-buffer each).
 template <typename T>
 __global__ void __launch_bounds__(kDstThreads) dst_bluestein_split_kernel(DstArgs A, int C, int fwd) {
   typedef Vt<T> V;
@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(kDstThreads) dst_bluestein_split_kernel(DstArg
   const int64_t col0 = (int64_t)blockIdx.x * C;
   const int64_t M = A.M;
   const int K = A.K;
-  const int logP = A.logP, P = 1 << logP, H = P >> 1;
+  const int logP = A.logP;
   const int CP = C >> 1, lcp = 31 - __clz(CP);
   const SmLayout Ls = sm_layout<V>(logP);
   const V* __restrict__ chirp = (const V*)A.chirp;
@@ -650,28 +650,22 @@ __global__ void __launch_bounds__(kDstThreads) dst_bluestein_split_kernel(DstArg
     }
   }
   __syncthreads();
-  fftr_passes<V, true>(sm, logP, CP, tw, 0, np, true);
-  // Z_k = W_k G1_k - W_{-k} G2_k, each frequency with its partner: item k < P/2 of transform
-  // t handles k and P - k (k = 0: the two self-partner frequencies 0 and P/2)
-  const int lh = logP - 1;
-  for (int e = threadIdx.x; e < (CP << lh); e += blockDim.x) {
-    const int t = e >> lh, k = e & (H - 1);
-    const int pos = (int)(__brev((unsigned)k) >> (32 - logP));
-    const int pk = k == 0 ? H : P - k;
-    const int pp = (int)(__brev((unsigned)pk) >> (32 - logP));
-    const int q1 = sm_pos<V>(Ls, t, pos), q2 = sm_pos<V>(Ls, t, pp);
-    const float4 ga = g12[pos], gb = g12[pp];
-    const V w1 = sm[q1], w2 = sm[q2];
-    if (k == 0) {
-      sm[q1] = cmul(w1, mkv((T)(ga.x - ga.z), (T)(ga.y - ga.w)));
-      sm[q2] = cmul(w2, mkv((T)(gb.x - gb.z), (T)(gb.y - gb.w)));
-    } else {
-      sm[q1] = csub(cmul(w1, mkv((T)ga.x, (T)ga.y)), cmul(w2, mkv((T)ga.z, (T)ga.w)));
-      sm[q2] = csub(cmul(w2, mkv((T)gb.x, (T)gb.y)), cmul(w1, mkv((T)gb.z, (T)gb.w)));
-    }
-  }
+  fftr_passes<V, true>(sm, logP, CP, tw, 0, np - 1, true);
+  // Z_k = W_k G1_k - W_{-k} G2_k, fused with the last forward and first inverse pass
+  fftr_middle_partner<V>(
+      sm, logP, CP,
+      [&](int, int pa, int pb, V& wa, V& wb) {
+        const float4 ga = g12[pa], gb = g12[pb];
+        const V za = csub(cmul(wa, mkv((T)ga.x, (T)ga.y)), cmul(wb, mkv((T)ga.z, (T)ga.w)));
+        wb = csub(cmul(wb, mkv((T)gb.x, (T)gb.y)), cmul(wa, mkv((T)gb.z, (T)gb.w)));
+        wa = za;
+      },
+      [&](int, int p, V& w) {
+        const float4 g = g12[p];
+        w = cmul(w, mkv((T)(g.x - g.z), (T)(g.y - g.w)));
+      });
   __syncthreads();
-  fftr_passes<V, false>(sm, logP, CP, tw, 0, np, false);
+  fftr_passes<V, false>(sm, logP, CP, tw, 1, np, false);
   const T scale = (T)A.dst_scale;
   if (fwd) {
     V* z = (V*)A.z;
