@@ -551,6 +551,7 @@ def run_batched(args):
     # share its host memory: the pinned buffers of all ranks are kept within 3/4 of it, and
     # when the whole batch does not fit the end-to-end step covers a prefix of the problems
     e2e = None
+    fh, freed = None, False
     try:
         if args.no_e2e:
             raise ValueError("skipped (--no-e2e)")
@@ -562,9 +563,14 @@ def run_batched(args):
         if k < len(probs):  # free the full plan's workspace before the sample's
             plan.close()
             plan = None
-        eplan = plan if plan is not None else ftoep.Plan(specs[:k])
         fh = f[:e_units].cpu().pin_memory()
         uh = torch.empty_like(fh).pin_memory()
+        # the host-buffer solve needs no device copy of the caller's fields: free them, so
+        # that the plan can keep its own device copies (f in once, u out once per solve)
+        del f, u
+        freed = True
+        torch.cuda.empty_cache()
+        eplan = plan if plan is not None else ftoep.Plan(specs[:k])
         eplan.solve(fh, uh)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -576,11 +582,16 @@ def run_batched(args):
         if k < len(probs):
             e2e["sample"] = f"first {k} of {len(probs)} problems ({e_units} unknowns): host-memory budget"
             eplan.close()
-        del fh, uh
+        del uh
     except (RuntimeError, ValueError, OSError) as exc:  # host memory
         e2e = {"unavailable": str(exc)[:200]}
-    if plan is not None:
+    if plan is not None:  # (with its device copies of the fields)
         plan.close()
+        plan = None
+    if freed:  # the device fields again, for the legs below
+        f = fh.cuda() if fh is not None and fh.numel() == units else batch_field(probs)
+        u = torch.empty_like(f)
+    fh = None
     # the library's default tuning on the same batch, for comparison with the tuned step
     default = None
     if tuning is not None:

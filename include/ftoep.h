@@ -44,7 +44,13 @@
  *
  * Pointers: field pointers may be device memory or host memory (pinned or pageable);
  * the library detects which.  Host buffers are staged through the plan's device
- * workspace inside the call.  The caller keeps ownership of every buffer it passes.
+ * workspace inside the call.  On the chain schedule (FTOEP_SCHED_CHAIN) the first
+ * host-buffer solve also allocates device copies of the fields of the plan's largest
+ * group when they fit in the free device memory with 1 GiB to spare: f then crosses the
+ * host link once and u once per solve; otherwise (or with FTOEP_HOST_STAGED=1 in the
+ * environment at plan creation) each problem passes through the staging arrays, f twice
+ * and, for a mixed problem, u out twice and in once.  The caller keeps ownership of every
+ * buffer it passes.
  *
  * Streams and errors: every call is ordered on the CUDA stream given to ftoep_create
  * and may return before the GPU work has finished.  Errors are returned as status

@@ -215,6 +215,11 @@ struct ftoep_plan_s {
   std::vector<SolveGraph> graphs;  // most recently used last
   cudaStream_t gstream = nullptr;  // root stream the graphs are captured and replayed on
   cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+  // host-buffer solves on the chain schedule: device copies of one group's f and u (when
+  // they fit), so that f crosses the host link once and u once per solve
+  double* res_f = nullptr;
+  double* res_u = nullptr;
+  bool res_tried = false;
 };
 
 namespace {
@@ -724,6 +729,39 @@ ftoep_status sync_plan(ftoep_plan pl) {
   return FTOEP_OK;
 }
 
+// Device copies of the fields of the largest chain group, for host-buffer solves: allocated
+// on the first such solve if they fit in the free device memory with 1 GiB to spare, else
+// never (the solves then pass each problem through its stream's staging arrays).
+bool ensure_resident(ftoep_plan pl) {
+  if (pl->res_f) return true;
+  if (pl->res_tried) return false;
+  pl->res_tried = true;
+  int64_t need = 0;
+  for (const auto& g : pl->groups) {
+    int64_t n = 0;
+    for (int i : g.probs) n += pl->probs[i].M * pl->probs[i].N;
+    need = std::max(need, n);
+  }
+  const size_t bytes = (size_t)need * sizeof(double);
+  size_t free_b = 0, total_b = 0;
+  if (need == 0 || cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (2 * bytes + (size_t(1) << 30) > free_b) return false;
+  void *a = nullptr, *b = nullptr;
+  if (cudaMalloc(&a, bytes) != cudaSuccess || cudaMalloc(&b, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    if (a) cudaFree(a);
+    return false;
+  }
+  pl->allocs.push_back(a);
+  pl->allocs.push_back(b);
+  pl->res_f = (double*)a;
+  pl->res_u = (double*)b;
+  return true;
+}
+
 // Make the internal streams wait for the caller's stream.
 ftoep_status fork_streams(ftoep_plan pl) {
   if (pl->ws.size() == 1 && !pl->ws[0].own) return FTOEP_OK;
@@ -1120,6 +1158,10 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
     const char* fa = getenv("FTOEP_FAIL_ALLOC_AFTER");
     pl->fail_after = (fa && *fa) ? atol(fa) : -1;
   }
+  {  // host-buffer solves always through the staging arrays (no device copies of the fields)
+    const char* hs = getenv("FTOEP_HOST_STAGED");
+    if (hs && *hs && atol(hs) != 0) pl->res_tried = true;
+  }
   ftoep_status st = FTOEP_OK;
   auto bail = [&](ftoep_status s) {
     g_create_error = pl->err;
@@ -1393,11 +1435,14 @@ struct Staged {
   const double *f = nullptr, *u0 = nullptr, *phi = nullptr;
   double* u = nullptr;
 };
+// (f NULL: only the initial-data vectors.)
 ftoep_status stage_inputs(ftoep_plan pl, Ws& w, const Prob& pb, const double* f, const double* u0,
                           const double* phi, Staged* out) {
   cudaStream_t st = w.st;
-  CK(cudaMemcpyAsync(w.stage_in, f, (size_t)pb.M * pb.N * sizeof(double), cudaMemcpyDefault, st));
-  out->f = w.stage_in;
+  if (f) {
+    CK(cudaMemcpyAsync(w.stage_in, f, (size_t)pb.M * pb.N * sizeof(double), cudaMemcpyDefault, st));
+    out->f = w.stage_in;
+  }
   out->u = w.stage_out;
   if (u0) {
     CK(cudaMemcpyAsync(w.stage_v0, u0, pb.M * sizeof(double), cudaMemcpyDefault, st));
@@ -1418,12 +1463,15 @@ ftoep_status stage_inputs(ftoep_plan pl, Ws& w, const Prob& pb, const double* f,
 //      its forward transform;
 //   4. mixed: one chain launch solves the correction of every pair;
 //   5. mixed: inverse transform, u += tau cumsum.
-// Host buffers go through the streams' staging arrays one problem at a time: f is copied
-// in for steps 1 and 3, u is copied out after step 3 and again, updated, after step 5.
+// Host buffers: when the group's fields fit on the device (ensure_resident), f is copied in
+// once in step 1 and u out once after its last step, and the steps run on the device
+// copies; otherwise every problem goes through its stream's staging arrays one at a time (f
+// copied in for steps 1 and 3, u copied out after step 3 and again, updated, after step 5).
 ftoep_status solve_all_chain(ftoep_plan pl, const double* f, double* u, const double* u0, const double* phi,
                              bool host) {
   if (host)
     for (auto& w : pl->ws) TRY(ensure_staging(pl, w));
+  const bool res = host && ensure_resident(pl);
   // problems with the inverse-series solve: whole solves on the internal streams
   bool any_finv = false;
   for (auto& pb : pl->probs) any_finv |= pb.finv;
@@ -1436,15 +1484,28 @@ ftoep_status solve_all_chain(ftoep_plan pl, const double* f, double* u, const do
   for (size_t gi = 0; gi < pl->groups.size(); ++gi) {
     ChainGroup& g = pl->groups[gi];
     bool mixed = false;
-    TRY(fork_streams(pl));
+    // offsets of the group's problems in the device copies of the fields
+    std::vector<int64_t> roff;
+    int64_t ro = 0;
     for (int i : g.probs) {
-      Prob& pb = pl->probs[i];
+      roff.push_back(ro);
+      ro += pl->probs[i].M * pl->probs[i].N;
+    }
+    TRY(fork_streams(pl));
+    for (size_t k = 0; k < g.probs.size(); ++k) {
+      Prob& pb = pl->probs[g.probs[k]];
       Ws w = ws_for(pl, pb);
       void* z = (char*)pl->gz + pb.zbyte;
       const double* pu0 = u0 ? u0 + pb.voff : nullptr;
       const double* pphi = phi ? phi + pb.voff : nullptr;
       mixed |= pb.prec != P64;
-      if (host) {
+      if (res) {
+        Staged sg;
+        TRY(stage_inputs(pl, w, pb, nullptr, pu0, pphi, &sg));
+        double* rf = pl->res_f + roff[k];
+        CK(cudaMemcpyAsync(rf, f + pb.foff, (size_t)pb.M * pb.N * sizeof(double), cudaMemcpyDefault, w.st));
+        TRY(rhs_forward(pl, w, pb, z, rf, sg.u0, sg.phi));
+      } else if (host) {
         Staged sg;
         TRY(stage_inputs(pl, w, pb, f + pb.foff, pu0, pphi, &sg));
         TRY(rhs_forward(pl, w, pb, z, sg.f, sg.u0, sg.phi));
@@ -1455,13 +1516,20 @@ ftoep_status solve_all_chain(ftoep_plan pl, const double* f, double* u, const do
     TRY(join_streams(pl));
     for (int pi = 0; pi < 2; ++pi) TRY(chain_launch(pl, (int)gi, pi, 0));
     TRY(fork_streams(pl));
-    for (int i : g.probs) {
-      Prob& pb = pl->probs[i];
+    for (size_t k = 0; k < g.probs.size(); ++k) {
+      Prob& pb = pl->probs[g.probs[k]];
       Ws w = ws_for(pl, pb);
       void* z = (char*)pl->gz + pb.zbyte;
       const double* pu0 = u0 ? u0 + pb.voff : nullptr;
       const double* pphi = phi ? phi + pb.voff : nullptr;
-      if (host) {
+      if (res) {
+        Staged sg;
+        TRY(stage_inputs(pl, w, pb, nullptr, pu0, pphi, &sg));
+        double* ru = pl->res_u + roff[k];
+        TRY(after_first_solve(pl, w, pb, z, pl->res_f + roff[k], ru, sg.u0, sg.phi));
+        if (pb.prec == P64)
+          CK(cudaMemcpyAsync(u + pb.foff, ru, (size_t)pb.M * pb.N * sizeof(double), cudaMemcpyDefault, w.st));
+      } else if (host) {
         Staged sg;
         TRY(stage_inputs(pl, w, pb, f + pb.foff, pu0, pphi, &sg));
         TRY(after_first_solve(pl, w, pb, z, sg.f, sg.u, sg.u0, sg.phi));
@@ -1474,12 +1542,16 @@ ftoep_status solve_all_chain(ftoep_plan pl, const double* f, double* u, const do
     if (!mixed) continue;
     TRY(chain_launch(pl, (int)gi, 1, 1));
     TRY(fork_streams(pl));
-    for (int i : g.probs) {
-      Prob& pb = pl->probs[i];
+    for (size_t k = 0; k < g.probs.size(); ++k) {
+      Prob& pb = pl->probs[g.probs[k]];
       if (pb.prec == P64) continue;
       Ws w = ws_for(pl, pb);
       void* z = (char*)pl->gz + pb.zbyte;
-      if (host) {
+      if (res) {
+        double* ru = pl->res_u + roff[k];
+        TRY(after_correction(pl, w, pb, z, ru));
+        CK(cudaMemcpyAsync(u + pb.foff, ru, (size_t)pb.M * pb.N * sizeof(double), cudaMemcpyDefault, w.st));
+      } else if (host) {
         const size_t bytes = (size_t)pb.M * pb.N * sizeof(double);
         CK(cudaMemcpyAsync(w.stage_out, u + pb.foff, bytes, cudaMemcpyDefault, w.st));
         TRY(after_correction(pl, w, pb, z, w.stage_out));

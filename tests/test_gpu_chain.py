@@ -7,8 +7,9 @@ through the whole recursion, so the two agree to rounding (the bodies compile se
 so the last bits may differ).  Sizes reach the four-step levels inside the chain (2s above
 the shared-memory length: N = 40000 has levels up to 2s = 65536), the chirp-z sine
 transform (M+1 not a power of two), both kinds and both precisions; batches check every
-problem against the oracle, also with host buffers (staged one problem at a time around the
-chain launches), with initial data, and split into several groups by a small memory budget.
+problem against the oracle, also with host buffers (through the plan's device copies of the
+fields, and staged one problem at a time around the chain launches), with initial data, and
+split into several groups by a small memory budget.
 """
 import os
 
@@ -75,9 +76,14 @@ def _batch(probs):
     return f
 
 
-@pytest.mark.parametrize("prec,tol,host", [(0, 1e-12, False), (1, 1e-6, False), (0, 1e-12, True), (1, 1e-6, True)])
-def test_chain_batch_vs_oracle(ft, oracle, prec, tol, host):
+@pytest.mark.parametrize("prec,tol,host", [(0, 1e-12, False), (1, 1e-6, False), (0, 1e-12, True), (1, 1e-6, True),
+                                           (0, 1e-12, "staged"), (1, 1e-6, "staged")])
+def test_chain_batch_vs_oracle(ft, oracle, monkeypatch, prec, tol, host):
+    """Device buffers; host buffers with the plan's device copies of the fields (f in once,
+    u out once); host buffers through the staging arrays (FTOEP_HOST_STAGED)."""
     import torch
+    if host == "staged":
+        monkeypatch.setenv("FTOEP_HOST_STAGED", "1")
     probs = wl.config_batched(nprob=9, seed=31, n_range=(300, 12000), m_range=(3, 40))
     fh = _batch(probs)
     specs = [ft.ProblemSpec(p.kind, p.gamma, p.N, p.M, p.space, prec) for p in probs]
