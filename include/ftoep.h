@@ -136,7 +136,7 @@ typedef enum {
   FTOEP_SOLVER_HALFSPLIT = 1, /* time blocks of B levels solved by the block inverse, then the
                                  recursive half-split updates between blocks (Sec. 3: the
                                  fast direct method of the reordered systems)                 */
-  FTOEP_SOLVER_INVERSE = 2    /* the inverse-series solve: x = h_m * y over the whole padded
+  FTOEP_SOLVER_INVERSE = 2,   /* the inverse-series solve: x = h_m * y over the whole padded
                                  length, h_m = T_m^-1 e_1 computed once per plan (by the
                                  half-split solve of a unit impulse, in double); each solve is
                                  one causal convolution of length 2 Np per mode pair.  Its
@@ -146,6 +146,17 @@ typedef enum {
                                  with the size of each block's own values -- for a growing
                                  hyperbolic or mixed-precision solution the early levels lose
                                  relative accuracy                                           */
+  FTOEP_SOLVER_INVERSE_MIXED_SUBDIFFUSION = 3
+                              /* INVERSE for the mixed-precision sub-diffusion problems
+                                 (FTOEP_L1_SUBDIFFUSION, FTOEP_MIXED), HALFSPLIT for the rest.
+                                 In the mixed path the correction sweep removes the first
+                                 solve's error; what remains is the correction's own normwise
+                                 rounding, a float rounding of a correction of about the
+                                 first solve's error, which the sub-diffusion inverse (positive
+                                 and decreasing) keeps well inside the mixed bar.  The
+                                 hyperbolic inverse oscillates and its float error can exceed
+                                 what one correction removes.  The inverse spectra take 8 B
+                                 per unknown x 2 Np/N of device memory beside the plan.       */
 } ftoep_solver;
 
 /* Optional tuning (NULL or 0 fields = library choice; ftoep_autotune picks fft_tile,
@@ -323,12 +334,13 @@ ftoep_status ftoep_advection_sweep(int scheme, double gamma, double T, double L,
                                    void* cuda_stream);
 
 /* The solver a plan uses for problem iprob (FTOEP_SOLVER_HALFSPLIT or
- * FTOEP_SOLVER_INVERSE), after the library's choice.  Errors: FTOEP_EINVAL. */
+ * FTOEP_SOLVER_INVERSE), after the library's choice and the tuning's rule.  Errors: FTOEP_EINVAL. */
 ftoep_status ftoep_problem_solver(ftoep_plan p, int iprob, int* solver);
 
 /* Autotuner (no counterpart in the paper).  Times ftoep_solve on synthetic fields for
  * every candidate tuning -- time-block length fft_tile in {1024, 2048, 4096} of the
- * half-split solver (the inverse-series solve is the caller's accuracy choice) x scheduler in {levels, chain} x internal streams in
+ * half-split solver (the inverse-series solves are the caller's choice: they trade accuracy
+ * or device memory for time) x scheduler in {levels, chain} x internal streams in
  * {2, 4, 8} (streams only for plans of several problems; a single problem runs on the
  * caller's stream) -- with a plan per candidate,
  * one warm-up solve, one captured solve and two timed replays (CUDA events on

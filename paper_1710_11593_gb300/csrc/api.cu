@@ -366,7 +366,7 @@ ftoep_status validate(const ftoep_problem& d, int i, const ftoep_tuning* tune) {
       return fail(pl, FTOEP_EINVAL, "tuning: gemm_max_level must be a power of two <= 2048");
     if (tune->streams < 0 || tune->streams > kMaxStreams)
       return fail(pl, FTOEP_EINVAL, "tuning: streams must be in [0, %d]", kMaxStreams);
-    if (tune->solver < 0 || tune->solver > FTOEP_SOLVER_INVERSE)
+    if (tune->solver < 0 || tune->solver > FTOEP_SOLVER_INVERSE_MIXED_SUBDIFFUSION)
       return fail(pl, FTOEP_EINVAL, "tuning: solver %d unknown", tune->solver);
     if (tune->scheduler < 0 || tune->scheduler > FTOEP_SCHED_CHAIN)
       return fail(pl, FTOEP_EINVAL, "tuning: scheduler must be 0 (library choice), 1 (levels) or 2 (chain)");
@@ -1238,7 +1238,9 @@ ftoep_status ftoep_create(ftoep_plan* out, const ftoep_problem* probs, int nprob
     const int solver = tune ? tune->solver : (int)FTOEP_SOLVER_AUTO;
     for (auto& pb : pl->probs) {
       const int64_t n = 2 * pb.Np;
-      if (solver == FTOEP_SOLVER_INVERSE && pb.nblk >= 2 && n > nsmem_for(pb.prec)) pb.finv = true;
+      const bool want = solver == FTOEP_SOLVER_INVERSE ||
+                        (solver == FTOEP_SOLVER_INVERSE_MIXED_SUBDIFFUSION && pb.prec != P64 && pb.tk == 0);
+      if (want && pb.nblk >= 2 && n > nsmem_for(pb.prec)) pb.finv = true;
     }
     // the solve's four-step scratch holds one pair's 2 Np values at least
     pl->scr_el = pl->z_el;
@@ -1862,8 +1864,9 @@ ftoep_status ftoep_autotune(const ftoep_problem* probs, int nprob, void* cuda_st
   cudaEventCreate(&e1);
   std::vector<ftoep_tuning> cands;
   const int ns_list[] = {2, 4, 8};
-  // the half-split solver only: the inverse-series solve trades accuracy for time (its
-  // error is normwise over the whole time axis), a choice the caller makes explicitly
+  // the half-split solver only: the inverse-series solves trade accuracy (INVERSE) or device
+  // memory (their spectra: 8-16 B per unknown x 2 Np/N, which a sample does not show) for
+  // time, a choice the caller makes explicitly
   for (int sv : {(int)FTOEP_SOLVER_HALFSPLIT}) {
     for (int B : {1024, 2048, 4096}) {
       for (int sch : {(int)FTOEP_SCHED_LEVELS, (int)FTOEP_SCHED_CHAIN}) {

@@ -26,7 +26,7 @@ SPACE_NONE, SPACE_DIRICHLET_LAPLACIAN = 0, 1
 FP64, MIXED = 0, 1
 
 SCHED_AUTO, SCHED_LEVELS, SCHED_CHAIN = 0, 1, 2
-SOLVER_AUTO, SOLVER_HALFSPLIT, SOLVER_INVERSE = 0, 1, 2
+SOLVER_AUTO, SOLVER_HALFSPLIT, SOLVER_INVERSE, SOLVER_INVERSE_MIXED_SUBDIFFUSION = 0, 1, 2, 3
 
 EXPORTS = ("ftoep_create", "ftoep_weights", "ftoep_solve", "ftoep_matvec", "ftoep_adjoint", "ftoep_profile",
            "ftoep_profile_read", "ftoep_matvec_noalloc", "ftoep_autotune", "ftoep_two_sided_cg", "ftoep_sync",

@@ -148,13 +148,20 @@ def config4_reference(oracle):
     return probs, picks, res
 
 
-@pytest.mark.parametrize("prec,tol", [(1, 1e-6), (0, 1e-12)])
-def test_config4_batch_sampled(ft, config4_reference, prec, tol):
+@pytest.mark.parametrize("prec,tol,solver", [(1, 1e-6, 0), (0, 1e-12, 0), (1, 1e-6, 3)])
+def test_config4_batch_sampled(ft, config4_reference, prec, tol, solver):
+    """solver 3: the inverse-series solve for the mixed sub-diffusion problems, the half
+    split for the hyperbolic ones."""
     import torch
     probs, picks, res = config4_reference
     f = _batch_fields(probs)
     specs = [ft.ProblemSpec(p.kind, p.gamma, p.N, p.M, p.space, prec) for p in probs]
-    with ft.Plan(specs) as plan:
+    with ft.Plan(specs, {"solver": solver} if solver else None) as plan:
+        if solver:
+            got = [plan.solver(i) for i in picks]
+            want = [ft.SOLVER_INVERSE if probs[i].kind == 0 and probs[i].N > 4096 else ft.SOLVER_HALFSPLIT
+                    for i in picks]
+            assert got == want, (got, want)
         u = plan.solve(f)
         plan.sync()
     del f

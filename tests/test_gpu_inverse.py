@@ -6,8 +6,10 @@ Cases: both kinds and the Crank-Nicolson kind, power-of-two and chirp-z sine siz
 ragged N (the padding of the pair rows read as zero), four-step splits with n1 < n2 and
 n1 = n2, nonzero u0 and phi, the scalar problem, double and mixed paths, host buffers,
 batches where some problems take the inverse-series solve and the rest the half split
-(chain and per-level schedules), and the adjoint of double and mixed plans.  The library's
-own choice stays the half split (test_library_choice_is_the_half_split).
+(chain and per-level schedules), the adjoint of double and mixed plans, and the rule that
+takes the inverse series for the mixed sub-diffusion problems only
+(FTOEP_SOLVER_INVERSE_MIXED_SUBDIFFUSION).  The library's own choice stays the half split
+(test_library_choice_is_the_half_split).
 
 Tolerances: the inverse-series solve rounds once over the whole time axis (one FFT of
 length 2 Np), so its error is normwise -- about eps log2(2 Np) |h| |y| against the largest
@@ -177,3 +179,26 @@ def test_inverse_plan_adjoint(ft, oracle, prec):
     assert _err(dldf, lam) < (1e-12 if prec == 0 else 5e-12)
     ref = oracle.gamma_gradient(0, g, oracle.march(0, 1, g, f), lam)
     assert abs(dg[0] - ref) <= (1e-10 if prec == 0 else 1e-8) * abs(ref)
+
+
+def test_mixed_subdiffusion_rule(ft, oracle):
+    """FTOEP_SOLVER_INVERSE_MIXED_SUBDIFFUSION: the inverse series for the mixed sub-diffusion
+    problems of more than one block, the half split for the hyperbolic, the double and the
+    one-block ones; the mixed sub-diffusion solution matches the oracle at 1e-6 over the
+    whole field and on its first 2048 levels against their own size."""
+    import torch
+    cases = [(0, 0.4, 15, 20000, 1), (1, 1.5, 15, 20000, 1), (0, 0.4, 15, 20000, 0), (0, 0.6, 15, 3000, 1)]
+    specs = [ft.ProblemSpec(k, g, N, M, 1, pr) for k, g, M, N, pr in cases]
+    with ft.Plan(specs, {"solver": ft.SOLVER_INVERSE_MIXED_SUBDIFFUSION}) as plan:
+        assert [plan.solver(i) for i in range(4)] == [ft.SOLVER_INVERSE, ft.SOLVER_HALFSPLIT,
+                                                      ft.SOLVER_HALFSPLIT, ft.SOLVER_HALFSPLIT]
+    k, g, M, N, pr = cases[0]
+    p = wl.config_diffusion(M=M, N=N, gamma=g)
+    f = wl.materialize(p.source, p.kind, N, M) + 1e-3 * wl.random_field((M, N), seed=11)
+    u, solvers = _plan_solve(ft, specs[:1], f, {"solver": ft.SOLVER_INVERSE_MIXED_SUBDIFFUSION})
+    assert solvers == [ft.SOLVER_INVERSE]
+    ref = oracle.march(0, 1, g, f)
+    assert _err(u, ref) < 1e-6
+    n0 = 2048
+    d = u[:, :n0] - ref[:, :n0]
+    assert np.linalg.norm(d) / np.linalg.norm(ref[:, :n0]) < 1e-6

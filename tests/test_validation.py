@@ -48,7 +48,7 @@ def test_invalid_problem_rejected(kw, status, msg):
     ({"fft_tile": 8192}, "fft_tile"),
     ({"fft_tile": 100}, "fft_tile"),
     ({"gemm_max_level": 4096}, "gemm_max_level"),
-    ({"solver": 3}, "solver"),
+    ({"solver": 4}, "solver"),
     ({"solver": -1}, "solver"),
 ])
 def test_invalid_tuning_rejected(tune, msg):
@@ -146,4 +146,4 @@ def test_shipped_tuning_table_is_valid():
         assert "|" in key and key.split("|")[0]
         t = {k: int(entry.get(k, 0)) for k in ftoep.TUNING_FIELDS}
         assert t["fft_tile"] in (0, 1024, 2048, 4096) and t["scheduler"] in (0, 1, 2)
-        assert 0 <= t["streams"] <= 8 and t["solver"] in (0, 1)
+        assert 0 <= t["streams"] <= 8 and t["solver"] in (0, 1, 3)
