@@ -132,7 +132,8 @@ constexpr int kDstThreads = 256;
 // Block shape of the float chirp-z transform: threads and shared-memory budget per block.
 // Small blocks (128 threads, at most 32 KB: one or two column pairs) keep more independent
 // blocks per SM between the barriers of the FFT passes; on the 512-problem batch the step
-// took 2415 ms against 2523 ms with 256 threads and 64 KB (256 threads and 32 KB: 2438 ms).
+// took 2415 ms against 2523 ms with 256 threads and 64 KB (256 threads and 32 KB: 2438 ms;
+// 128 threads and 16 KB: 2446 ms; 64 threads and 16 KB: 2558 ms).
 #ifndef FTOEP_SPLIT_THREADS
 #define FTOEP_SPLIT_THREADS 128
 #endif
